@@ -1,0 +1,382 @@
+"""Throughput of the VQ-NNF hot path on one GB300 (or N replicas, one per GPU).
+
+One step = the whole hot path on one synthetic template-query pair of the headline
+workload: k-means codebook of the template (10 Lloyd steps), template NNF, template filter
+responses, query NNF, query integral image + filter responses + Eq. 2 heatmap + argmax.
+Metric: query Mpixel/s (query pixels / step time); the template side is inside the step.
+
+Default workload: 2048 x 2048 query, D = 512, k = 128, 128 x 128 template (rotated, scaled,
+occluded, noisy resample of the query), F = 10 (full window + 3 x 3 sub-windows).
+Inputs are generated on the device from fixed seeds and stay resident (8 GiB of features,
+larger than L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32] [--impl reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on bounded
+samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HEADLINE = dict(H=2048, W=2048, D=512, k=128, th=128, tw=128, grid=3, iters=10, M=128,
+                n_sp=20000, q_seed=1001, t_seed=2001, fit_seed=3001)
+METRIC = "query Mpix/s at 2048^2, D=512, k=128: BF16 vs FP32 path, % of roofline"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_workload(dev, cfg):
+    import synth
+    q = synth.query_map(cfg["H"], cfg["W"], cfg["D"], M=cfg["M"], n_sp=cfg["n_sp"],
+                        seed=cfg["q_seed"], device=dev)
+    T, info = synth.warped_template(q, cfg["th"], cfg["tw"], seed=cfg["t_seed"])
+    bank = synth.grid_bank(cfg["th"], cfg["tw"], cfg["grid"])
+    return q, T, info, bank
+
+
+class Pipeline:
+    """The hot path with every buffer allocated once (so a step can be graph-captured)."""
+
+    def __init__(self, vq, X, T, cfg, bank, prec, stream):
+        import torch
+        self.vq, self.X, self.T, self.cfg, self.prec, self.s = vq, X, T, cfg, prec, stream
+        self.bank = vq.Bank(bank)
+        H, W, D, k = cfg["H"], cfg["W"], cfg["D"], cfg["k"]
+        th, tw = cfg["th"], cfg["tw"]
+        dev = X.device
+        self.ws_fit = vq.Workspace(vq.vqnnf_workspace_bytes(0, th, tw, D, k, prec=prec), dev)
+        self.ws_a = vq.Workspace(vq.vqnnf_workspace_bytes(1, H, W, D, k, prec=prec), dev)
+        self.ws_s = vq.Workspace(vq.vqnnf_workspace_bytes(3, H, W, 0, k, th, tw, self.bank.F), dev)
+        self.C = torch.empty((k, D), device=dev)
+        self.tl = torch.empty((th, tw), dtype=torch.uint8, device=dev)
+        self.ql = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        self.tc = torch.empty((self.bank.F, k), dtype=torch.int32, device=dev)
+        self.heat = torch.empty((H - th + 1, W - tw + 1), device=dev)
+        self.am = torch.empty(2, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(4, dtype=torch.int64, device=dev)
+
+    def step(self, ev=None):
+        vq, c, s = self.vq, self.cfg, self.s
+        if ev is not None:
+            ev[0].record(s)
+        vq.vqnnf_fit_codebook(self.T, c["k"], c["iters"], c["fit_seed"], self.prec, C=self.C,
+                              ws=self.ws_fit, stream=s)
+        vq.vqnnf_assign(self.T, self.C, self.prec, labels=self.tl, ws=self.ws_a, stream=s)
+        vq.vqnnf_filter_responses(self.tl, c["k"], self.bank, counts=self.tc, stream=s)
+        if ev is not None:
+            ev[1].record(s)
+        vq.vqnnf_assign(self.X, self.C, self.prec, labels=self.ql, stats=self.stats,
+                        ws=self.ws_a, stream=s)
+        if ev is not None:
+            ev[2].record(s)
+        vq.vqnnf_score(self.ql, c["k"], c["th"], c["tw"], self.bank, self.tc, heatmap=self.heat,
+                       argmax_yx=self.am, ws=self.ws_s, stream=s)
+        if ev is not None:
+            ev[3].record(s)
+
+
+def kernels_per_step(cfg, prec):
+    """Kernels of this library launched by one step (counted from the launch sequence)."""
+    k = cfg["k"]
+    assign = 2 + 1 + 1 + 1          # prep mean + prep centroids, contraction, rescore, stats
+    fit = 1 + cfg["iters"] * (assign - 1 + 2)   # gather; per step: assign (no stats) + sort + update
+    tpl = (assign - 1) + 1          # template NNF, template responses
+    score = 2 + 1 + 1               # row carry + sweep, score, argmax
+    return fit + tpl + assign + score
+
+
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2306_15010_gb300 as vq
+    from paper_2306_15010_gb300 import build as _b
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if local == 0:
+        _b.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    cfg = dict(HEADLINE)
+    q, T, info, bank = make_workload(dev, cfg)
+    X = q.X
+    s = torch.cuda.Stream(device=dev)
+    pipe = Pipeline(vq, X, T, cfg, bank, args.prec, s)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pipe.step()
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        start.record(s)
+        with torch.cuda.stream(s):
+            for i in range(K):
+                pipe.step(evs[i])
+        stop.record(s)
+        torch.cuda.synchronize()
+    ms = start.elapsed_time(stop) / K
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    seg = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
+                    for e in evs]).mean(0)
+    stats = pipe.stats.cpu().tolist()
+    am = pipe.am.cpu().tolist()
+    clocks = clk.summary()
+
+    # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
+    e2e = run_e2e(vq, pipe, X, T, cfg, args, s, dev)
+
+    if rank != 0:
+        return None
+    L = cfg["H"] * cfg["W"]
+    value = world * L / (ms * 1e-3) / 1e6
+    peaks, peak_src = _peaks()
+    roof = roofline(cfg, args.prec, seg[1], peaks, peak_src)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
+                               "(full + 3x3), 10 Lloyd steps; whole hot path per step",
+                   "prec": args.prec, "query_px": L, "l2": "inputs larger than L2 (8 GiB features)",
+                   "parallelism": f"replicas x{world}"},
+        "segments_ms": {"template_side": round(seg[0], 4), "query_assign": round(seg[1], 4),
+                        "query_score": round(seg[2], 4)},
+        "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
+        "argmax_yx": am, "planted_top_left": list(info["top_left"]),
+        "roofline": roof, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": kernels_per_step(cfg, args.prec) * K,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget)
+    return line
+
+
+def roofline(cfg, prec, assign_ms, peaks, src):
+    L, D, k = cfg["H"] * cfg["W"], cfg["D"], cfg["k"]
+    if prec == "bf16":
+        # HBM-bound: the contraction must read every FP32 feature once and write a label
+        bytes_ = L * (D * 4 + 1)
+        ach = bytes_ / (assign_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "query assign (contraction + re-scoring)", "peak_source": src}
+    # FP32 SIMT: bound by the FP32 FMA pipes, 152 SMs x 128 lanes x 2 flop x max SM clock
+    flops = 2.0 * L * D * k
+    ach = flops / (assign_ms * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4), "traffic": None,
+            "kernel": "query assign (FP32 SIMT contraction + re-scoring)",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+
+
+def run_e2e(vq, pipe, X, T, cfg, args, s, dev):
+    import torch
+    try:
+        hX = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
+        hT = torch.empty(T.shape, dtype=T.dtype, pin_memory=True)
+        hX.copy_(X.cpu())
+        hT.copy_(T.cpu())
+        hheat = torch.empty(pipe.heat.shape, dtype=torch.float32, pin_memory=True)
+        ham = torch.empty(2, dtype=torch.int32, pin_memory=True)
+    except Exception as exc:  # pragma: no cover
+        return {"value": None, "unit": "Mpix/s", "error": str(exc)}
+    n = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s):
+        for _ in range(n):
+            pipe.X.copy_(hX, non_blocking=True)
+            pipe.T.copy_(hT, non_blocking=True)
+            pipe.step()
+            hheat.copy_(pipe.heat, non_blocking=True)
+            ham.copy_(pipe.am, non_blocking=True)
+    s.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    L = cfg["H"] * cfg["W"]
+    return {"value": round(L / dt / 1e6, 3), "unit": "Mpix/s",
+            "h2d_bytes_per_step": hX.numel() * 4 + hT.numel() * 4,
+            "d2h_bytes_per_step": hheat.numel() * 4 + 8, "steps": n}
+
+
+def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1):
+    """The FP64 oracle timed on bounded samples of the same workload, scaled to one step."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    Xh = q.X[: 8].cpu().numpy()                   # 8 query rows = 16384 pixels
+    Th = T.cpu().numpy()
+    k, D = cfg["k"], cfg["D"]
+    L = cfg["H"] * cfg["W"]
+    th, tw = cfg["th"], cfg["tw"]
+    HO, WO = cfg["H"] - th + 1, cfg["W"] - tw + 1
+    t0 = time.perf_counter()
+    C = oracle.fit_codebook(Th, k, 1, cfg["fit_seed"])       # one Lloyd step
+    t_fit1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lab = oracle.assign(Xh, C)
+    t_asg = time.perf_counter() - t0
+    px_asg = Xh.shape[0] * Xh.shape[1]
+    # score sample: windows of a synthetic label field of the same size (labels for the
+    # whole query would need the full assignment)
+    ql = (q.sp_id.cpu().numpy() * 7 % k).astype(np.int32)
+    tl = ql[:th, :tw]
+    tc = oracle.filter_counts(tl, k, bank)
+    rng = np.random.default_rng(0)
+    nwin = 64
+    win = np.stack([rng.integers(0, HO, nwin), rng.integers(0, WO, nwin)], 1)
+    t0 = time.perf_counter()
+    oracle.score_at(ql, k, bank, tc, win)
+    t_sc = time.perf_counter() - t0
+    t_step = (t_fit1 * cfg["iters"] + t_asg * (L + th * tw) / px_asg
+              + t_sc * HO * WO / nwin)
+    return {"value": round(L / t_step / 1e6, 6), "unit": "Mpix/s",
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"1 Lloyd step (x{cfg['iters']}), {px_asg} query pixels assigned, "
+                       f"{nwin} windows scored; scaled to one full step"),
+            "step_s_estimate": round(t_step, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+    cfg = dict(HEADLINE)
+    gen_dev = "cuda" if torch.cuda.is_available() else "cpu"   # input generation only
+    q, T, info, bank = make_workload(gen_dev, cfg)
+    for _ in range(args.warmup):
+        cpu_baseline(q, T, cfg, bank)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(q, T, cfg, bank))
+    wall = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * vals[-1]["step_s_estimate"], 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
+                                   "(full + 3x3), 10 Lloyd steps; whole hot path per step",
+                       "sampled": True, "wall_s": round(wall, 1), "torch_threads": torch.get_num_threads()},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", choices=["bf16", "fp32"], default="fp32")
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if args.warmup < 3 and args.impl == "gpu":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_gpu(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * vqnnf.h -- C ABI of the GB300 VQ-NNF template-matching hot path.
+ *
+ * The calls follow the problem statement of Gupta & Sintorn, "Efficient High-Resolution
+ * Template Matching with Vector Quantized Nearest Neighbour Fields" (Sec. 3): a template
+ * tau of w x h x c features and a query I of W x H x c features; a k-vector codebook of
+ * the template (Sec. 3.1); the nearest-neighbour field of both images over that codebook
+ * (Algorithm 1); coarse-filter responses on the integral image of the one-hot field
+ * (Sec. 3.2, Eq. 1, Algorithm 2); and the similarity score of every query sub-window
+ * (Sec. 3.3, Eq. 2) with its maximum (Sec. 4, "Target Localization").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Memory.    Every pointer named *device* is CUDA device memory owned by the caller; the
+ *            library never allocates, frees or retains memory.  Scratch space is passed in
+ *            as `ws` (device, at least vqnnf_workspace_bytes(...) bytes, 256-byte aligned);
+ *            its contents on entry are ignored.  Filter banks are host memory, read during
+ *            the call only.
+ * Layout.    Feature maps are HWC row-major float32: element (y, x, i) of an H x W x D map
+ *            is at [(y * W + x) * D + i].  Label images are row-major uint8 (k <= 256).
+ *            Codebooks are k x D row-major float32.
+ * Streams.   `stream` is a cudaStream_t (NULL = legacy default stream).  Calls only
+ *            enqueue work on it and return; none synchronises the host, so a call can be
+ *            captured into a CUDA graph.  Results are valid once the stream reaches them.
+ * Errors.    Argument errors are detected on the host and returned before anything is
+ *            enqueued (VQNNF_EINVAL, VQNNF_ENOMEM for a workspace that is too small,
+ *            VQNNF_EUNSUPPORTED for shapes outside the supported range).  A failed launch
+ *            returns VQNNF_ECUDA.  Bounded device-side waits that give up record
+ *            VQNNF_ETIMEOUT in a device error word that vqnnf_last_device_error() reads.
+ *            No call aborts the process or traps on the device.
+ * Threads.   The library keeps no host state: calls from several host threads on
+ *            different streams are independent.
+ * Ties.      Nearest-neighbour ties go to the lowest centroid index; the heatmap maximum
+ *            goes to the lowest row-major (y, then x) window.
+ */
+#ifndef VQNNF_H
+#define VQNNF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vqnnf_status {
+    VQNNF_OK = 0,
+    VQNNF_EINVAL = 1,        /* bad pointer, size or filter bank                         */
+    VQNNF_ENOMEM = 2,        /* workspace smaller than vqnnf_workspace_bytes(...)          */
+    VQNNF_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed               */
+    VQNNF_ETIMEOUT = 4,      /* a bounded device wait gave up (see last_device_error)     */
+    VQNNF_EUNSUPPORTED = 5   /* valid request outside the implemented range              */
+} vqnnf_status;
+
+/* Arithmetic of the nearest-neighbour distance contraction (Sec. 4.2: exact L2 NN). */
+typedef enum vqnnf_prec {
+    VQNNF_PREC_FP32 = 0,     /* FP32 SIMT dot products                                   */
+    VQNNF_PREC_BF16 = 1      /* BF16 tensor cores (tcgen05), FP32 accumulation            */
+} vqnnf_prec;
+/* Both precisions return the exact nearest neighbour of the FP32 inputs: every pixel
+ * whose two best distances are closer than a proven bound on the contraction's error is
+ * re-scored in compensated FP32 over its candidate centroids.  Labels therefore equal
+ * an exact (FP64) evaluation except where that evaluation's own relative gap between
+ * the two best distances is below about 1e-11. */
+
+/* A rectangle of a coarse filter, relative to the window's top-left corner, half-open:
+ * columns [x0, x1), rows [y0, y1), 0 <= x0 < x1 <= tw, 0 <= y0 < y1 <= th.  Its
+ * response for cluster j is weight * (number of pixels labelled j inside it). */
+typedef struct vqnnf_rect {
+    int32_t x0, y0, x1, y1;
+    int32_t weight;
+} vqnnf_rect;
+
+/* A filter f: the sum of its rectangles' responses (the integral-image form of a coarse
+ * filter, Algorithm 2), its score weight w_f (Eq. 2) and its normaliser A_f (the
+ * receptive-field area of Eq. 1).  The score uses w_f / A_f. */
+typedef struct vqnnf_filter {
+    int32_t n_rects;
+    const vqnnf_rect *rects;
+    float w_f;
+    float area;
+} vqnnf_filter;
+
+/* Counters of the near-tie re-scoring, accumulated on the device by vqnnf_assign. */
+typedef struct vqnnf_assign_stats {
+    unsigned long long n_flagged;     /* pixels whose contraction result was ambiguous      */
+    unsigned long long n_candidates;  /* candidate centroids re-scored over those pixels    */
+    unsigned long long n_deep;        /* pixels that needed the double-float second stage   */
+    unsigned long long reserved;
+} vqnnf_assign_stats;
+
+/* Operation codes for vqnnf_workspace_bytes. */
+enum {
+    VQNNF_OP_FIT = 0,
+    VQNNF_OP_ASSIGN = 1,
+    VQNNF_OP_FILTER_RESPONSES = 2,
+    VQNNF_OP_SCORE = 3
+};
+
+/* Scratch bytes needed by one call.  Arguments not used by `op` are ignored:
+ *   FIT:              H x W = template h x w, D, k, prec
+ *   ASSIGN:           H x W pixels, D, k, prec
+ *   FILTER_RESPONSES: nothing (returns a small constant)
+ *   SCORE:            H x W query, k, th x tw template, F filters
+ * Returns 0 for arguments that are out of range. */
+size_t vqnnf_workspace_bytes(int op, int H, int W, int D, int k, int th, int tw, int F,
+                             int prec);
+
+/* k-means codebook of the template (Sec. 3.1; Sec. 4.2 uses plain k-means).
+ *   T      device, h x w x D float32 template features
+ *   k      1 <= k <= min(256, h*w) clusters;  iters >= 0 Lloyd steps (no early stop)
+ *   seed   seeds the initial centroids: k distinct template pixels, the first k slots of
+ *          a Fisher-Yates shuffle of 0..h*w-1 in which slot i swaps with slot
+ *          i + (r mod (h*w - i)), r the i-th output of SplitMix64 started at `seed`
+ *   C      device, k x D float32, written
+ * Each Lloyd step assigns every template pixel to its exact nearest centroid (lowest
+ * index on ties), then replaces each non-empty cluster's centroid by the FP64 mean of its
+ * members, summed in pixel order and rounded to float32; an empty cluster keeps its
+ * centroid.  D % 4 == 0.  `prec` selects the arithmetic of the assignment steps. */
+vqnnf_status vqnnf_fit_codebook(const float *T, int h, int w, int D, int k, int iters,
+                                uint64_t seed, vqnnf_prec prec, float *C,
+                                void *ws, size_t ws_bytes, void *stream);
+
+/* Nearest-neighbour field (Algorithm 1): labels[p] = argmin_j ||X[p] - C[j]||^2.
+ *   X       device, H x W x D float32 features (query or template)
+ *   C       device, k x D float32 codebook, 1 <= k <= 256
+ *   prec    VQNNF_PREC_FP32 (D % 4 == 0) or VQNNF_PREC_BF16 (D % 16 == 0)
+ *   labels  device, H x W uint8, written
+ *   stats   device vqnnf_assign_stats, overwritten; may be NULL */
+vqnnf_status vqnnf_assign(const float *X, int H, int W, int D, const float *C, int k,
+                          vqnnf_prec prec, uint8_t *labels, vqnnf_assign_stats *stats,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* Template representation vectors (Sec. 3.3, R(tau)): for every filter f and cluster j,
+ *   counts[f * k + j] = sum over rects of weight * #{pixels labelled j in the rect}
+ * with the window placed at the template's origin.
+ *   labels  device, h x w uint8 template NNF;  bank: host, F >= 1 filters
+ *   counts  device, F x k int32, written */
+vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,
+                                    const vqnnf_filter *bank, int F, int32_t *counts,
+                                    void *ws, size_t ws_bytes, void *stream);
+
+/* Similarity heatmap (Eq. 2, |.| read as the L1 norm over clusters):
+ *   heat[y][x] = - sum_f (w_f / A_f) * sum_j | t_counts[f][j] - q_f(y, x)[j] |
+ * for every valid window top-left (y, x), 0 <= y <= H - th, 0 <= x <= W - tw, where
+ * q_f(y, x) are the filter's counts over the query NNF with the window at (y, x), taken
+ * from the per-cluster integral image of the one-hot query NNF.  The inner sums are exact
+ * integers; the outer sum is float32 in bank order.
+ *   q_labels  device, H x W uint8;  t_counts: device, F x k int32 (vqnnf_filter_responses)
+ *   heatmap   device, (H - th + 1) x (W - tw + 1) float32, written
+ *   argmax_yx device int32[2] (y, x) of the maximum, lowest row-major index on ties;
+ *             may be NULL */
+vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, int tw,
+                         const vqnnf_filter *bank, int F, const int32_t *t_counts,
+                         float *heatmap, int32_t *argmax_yx,
+                         void *ws, size_t ws_bytes, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *vqnnf_status_str(vqnnf_status s);
+
+/* Synchronises `stream`, then returns and clears the device error word of the current
+ * device: VQNNF_OK, or VQNNF_ETIMEOUT when a bounded device wait gave up since the last
+ * call. */
+vqnnf_status vqnnf_last_device_error(void *stream);
+
+/* ABI version of this header (major * 100 + minor). */
+int vqnnf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VQNNF_H */

@@ -1,0 +1,19 @@
+"""GB300-native VQ-NNF template matching (Gupta & Sintorn, arXiv 2306.15010).
+
+The hot path -- k-means codebook, nearest-neighbour field, integral-image filter
+responses and the Eq. 2 similarity heatmap -- runs in the hand-written CUDA kernels of
+``libvqnnf.so``; this package only marshals torch tensors (device memory and the current
+stream) into the C ABI of ``include/vqnnf.h``.
+"""
+from .api import (  # noqa: F401
+    vqnnf_assign,
+    vqnnf_fit_codebook,
+    vqnnf_filter_responses,
+    vqnnf_last_device_error,
+    vqnnf_score,
+    vqnnf_version,
+    vqnnf_workspace_bytes,
+    Bank,
+    Workspace,
+)
+from ._lib import VqnnfError  # noqa: F401

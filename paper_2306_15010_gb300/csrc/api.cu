@@ -1,0 +1,400 @@
+// C ABI of the VQ-NNF hot path (include/vqnnf.h): argument checks, workspace layout and
+// the launch sequence of every call.  All work is enqueued on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "score_spec.cuh"
+
+using namespace vqnnf;
+
+namespace {
+
+constexpr int kVersion = 100;
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ----------------------------------------------------------------------------------
+// Workspace layouts (the same code computes sizes with a null base).
+// ----------------------------------------------------------------------------------
+struct AssignWs {
+    CodebookPrep prep;
+    FlagList fl;
+};
+
+AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
+{
+    AssignWs w;
+    w.prep.mean = c.take<float>((size_t)D);
+    w.prep.cc = c.take<float>((size_t)k * D);
+    w.prep.chi = c.take<uint16_t>((size_t)k * D);
+    w.prep.clo = c.take<uint16_t>((size_t)k * D);
+    w.prep.nrm = c.take<float>((size_t)k);
+    w.prep.a = c.take<float>((size_t)k);
+    w.prep.v = c.take<float>((size_t)k);
+    w.prep.b = c.take<float>((size_t)k);
+    w.fl.count = c.take<unsigned int>(64);     // count + stats share one memset
+    w.fl.stats = c.base ? reinterpret_cast<unsigned long long *>(w.fl.count + 16) : nullptr;
+    w.fl.pix = c.take<unsigned int>((size_t)n);
+    w.fl.mask = c.take<unsigned int>((size_t)n * kMaskWords);
+    return w;
+}
+
+struct FitWs {
+    AssignWs as;
+    uint8_t *lab;
+    int *cnt, *off, *members;
+};
+
+FitWs carve_fit(WsCursor &c, long long l, int D, int k)
+{
+    FitWs w;
+    w.as = carve_assign(c, l, D, k);
+    w.lab = c.take<uint8_t>((size_t)l);
+    w.cnt = c.take<int>((size_t)k);
+    w.off = c.take<int>((size_t)k + 1);
+    w.members = c.take<int>((size_t)l);
+    return w;
+}
+
+struct ScoreWs {
+    int *S;
+    int *carry;
+    unsigned long long *amax;
+};
+
+ScoreWs carve_score(WsCursor &c, int H, int W, int k)
+{
+    ScoreWs w;
+    w.S = c.take<int>((size_t)(H + 1) * k * sat_pitch(W));
+    w.carry = c.take<int>((size_t)H * sat_strips(W) * k);
+    w.amax = c.take<unsigned long long>(1);
+    return w;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+vqnnf_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return VQNNF_OK;
+    if (e == cudaErrorNotSupported) return VQNNF_EUNSUPPORTED;
+    return VQNNF_ECUDA;
+}
+
+bool check_prec(int prec, int D)
+{
+    if (prec == VQNNF_PREC_FP32) return D % 4 == 0;
+    if (prec == VQNNF_PREC_BF16) return D % 16 == 0;
+    return false;
+}
+
+// Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).
+vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
+                        uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.fl.count, 0, 64 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_prep_codebook(C, k, D, prec, w.prep, s);
+    if (e == cudaSuccess) {
+        if (prec == VQNNF_PREC_BF16)
+            e = launch_assign_bf16(X, n, D, k, w.prep, labels, w.fl, s);
+        else
+            e = launch_assign_fp32(X, n, D, k, w.prep, labels, w.fl, s);
+    }
+    if (e == cudaSuccess) e = launch_rescore(X, n, D, C, k, labels, w.fl, s);
+    if (e == cudaSuccess && stats) e = launch_finish_stats(w.fl, stats, s);
+    return from_cuda(e);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) and the partial Fisher-Yates initial indices,
+// with the swapped slots kept in a small table instead of an l-element permutation.
+uint64_t splitmix64(uint64_t &st)
+{
+    st += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void kmeans_init_indices(long long l, int k, uint64_t seed, int32_t *out)
+{
+    long long key[2 * kMaxK];
+    long long val[2 * kMaxK];
+    int nmap = 0;
+    auto get = [&](long long p) {
+        for (int q = 0; q < nmap; ++q)
+            if (key[q] == p) return val[q];
+        return p;
+    };
+    auto set = [&](long long p, long long v) {
+        for (int q = 0; q < nmap; ++q)
+            if (key[q] == p) { val[q] = v; return; }
+        key[nmap] = p;
+        val[nmap] = v;
+        ++nmap;
+    };
+    uint64_t st = seed;
+    for (int i = 0; i < k; ++i) {
+        const uint64_t r = splitmix64(st);
+        const long long j = (long long)i + (long long)(r % (uint64_t)(l - i));
+        const long long vi = get(i), vj = get(j);
+        set(i, vj);
+        set(j, vi);
+        out[i] = (int32_t)vj;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Filter banks.
+// ----------------------------------------------------------------------------------
+vqnnf_status compile_bank(const vqnnf_filter *bank, int F, int th, int tw, BankSpec &bs,
+                          GridSpec &gs)
+{
+    if (!bank || F < 1) return VQNNF_EINVAL;
+    if (F > kMaxFilters) return VQNNF_EUNSUPPORTED;
+    memset(&bs, 0, sizeof(bs));
+    memset(&gs, 0, sizeof(gs));
+    int nr = 0;
+    int rows[kMaxRows];
+    int nrect = 0;
+    for (int f = 0; f < F; ++f) {
+        const vqnnf_filter &fl = bank[f];
+        if (fl.n_rects < 1 || !fl.rects || !(fl.area > 0.f) || !std::isfinite(fl.area) ||
+            !std::isfinite(fl.w_f))
+            return VQNNF_EINVAL;
+        if (nrect + fl.n_rects > kMaxRects) return VQNNF_EUNSUPPORTED;
+        bs.rect_begin[f] = nrect;
+        for (int r = 0; r < fl.n_rects; ++r) {
+            const vqnnf_rect &rc = fl.rects[r];
+            if (rc.x0 < 0 || rc.y0 < 0 || rc.x1 > tw || rc.y1 > th || rc.x0 >= rc.x1 ||
+                rc.y0 >= rc.y1)
+                return VQNNF_EINVAL;
+            RectSpec &o = bs.rect[nrect++];
+            o.x0 = rc.x0; o.y0 = rc.y0; o.x1 = rc.x1; o.y1 = rc.y1; o.weight = rc.weight;
+            for (int yy : {rc.y0, rc.y1}) {
+                bool seen = false;
+                for (int q = 0; q < nr; ++q) seen |= rows[q] == yy;
+                if (!seen) rows[nr++] = yy;
+            }
+        }
+        bs.coef[f] = (float)((double)fl.w_f / (double)fl.area);
+    }
+    bs.rect_begin[F] = nrect;
+    bs.F = F;
+    std::sort(rows, rows + nr);
+    bs.nrow = nr;
+    for (int q = 0; q < nr; ++q) bs.roff[q] = rows[q];
+    for (int r = 0; r < nrect; ++r) {
+        RectSpec &o = bs.rect[r];
+        o.ry0 = int(std::lower_bound(rows, rows + nr, o.y0) - rows);
+        o.ry1 = int(std::lower_bound(rows, rows + nr, o.y1) - rows);
+    }
+    bs.ncol = score_ncol(tw);
+
+    // grid detection: single unit-weight rectangles forming a G x G cell grid (+ full)
+    bool single = true;
+    for (int f = 0; f < F; ++f)
+        single &= bank[f].n_rects == 1 && bank[f].rects[0].weight == 1;
+    if (!single) return VQNNF_OK;
+    int xs[kMaxRects * 2], ys[kMaxRects * 2], nx = 0, ny = 0;
+    int full_f = -1;
+    for (int f = 0; f < F; ++f) {
+        const vqnnf_rect &rc = bank[f].rects[0];
+        if (rc.x0 == 0 && rc.y0 == 0 && rc.x1 == tw && rc.y1 == th && full_f < 0 && F > 1) {
+            full_f = f;
+            continue;
+        }
+        xs[nx++] = rc.x0; xs[nx++] = rc.x1;
+        ys[ny++] = rc.y0; ys[ny++] = rc.y1;
+    }
+    std::sort(xs, xs + nx);
+    nx = int(std::unique(xs, xs + nx) - xs);
+    std::sort(ys, ys + ny);
+    ny = int(std::unique(ys, ys + ny) - ys);
+    const int G = nx - 1;
+    if (G < 1 || G > 4 || ny - 1 != G || xs[0] != 0 || xs[G] != tw || ys[0] != 0 || ys[G] != th)
+        return VQNNF_OK;
+    const int ncell = F - (full_f >= 0 ? 1 : 0);
+    if (ncell != G * G) return VQNNF_OK;
+    int seen[16] = {0};
+    GridSpec g;
+    memset(&g, 0, sizeof(g));
+    for (int f = 0; f < F; ++f) {
+        if (f == full_f) {
+            g.filter_slot[f] = G * G;
+            g.slot_filter[G * G] = f;
+            continue;
+        }
+        const vqnnf_rect &rc = bank[f].rects[0];
+        const int c = int(std::lower_bound(xs, xs + nx, rc.x0) - xs);
+        const int r = int(std::lower_bound(ys, ys + ny, rc.y0) - ys);
+        if (xs[c + 1] != rc.x1 || ys[r + 1] != rc.y1 || seen[r * G + c]) return VQNNF_OK;
+        seen[r * G + c] = 1;
+        g.filter_slot[f] = r * G + c;
+        g.slot_filter[r * G + c] = f;
+    }
+    g.G = G;
+    g.full = full_f >= 0;
+    g.F = F;
+    g.ncol = bs.ncol;
+    for (int q = 0; q <= G; ++q) {
+        g.bx[q] = xs[q];
+        g.by[q] = ys[q];
+    }
+    for (int f = 0; f < F; ++f) g.coef[f] = bs.coef[f];
+    gs = g;
+    return VQNNF_OK;
+}
+
+int device_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return 0;
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vqnnf_version(void) { return kVersion; }
+
+const char *vqnnf_status_str(vqnnf_status s)
+{
+    switch (s) {
+    case VQNNF_OK: return "ok";
+    case VQNNF_EINVAL: return "invalid argument";
+    case VQNNF_ENOMEM: return "workspace too small";
+    case VQNNF_ECUDA: return "CUDA error";
+    case VQNNF_ETIMEOUT: return "device wait timed out";
+    case VQNNF_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+size_t vqnnf_workspace_bytes(int op, int H, int W, int D, int k, int th, int tw, int F, int prec)
+{
+    (void)th; (void)tw; (void)F; (void)prec;
+    WsCursor c{nullptr, 0};
+    switch (op) {
+    case VQNNF_OP_FIT:
+        if (H < 1 || W < 1 || D < 1 || k < 1 || k > kMaxK) return 0;
+        carve_fit(c, (long long)H * W, D, k);
+        break;
+    case VQNNF_OP_ASSIGN:
+        if (H < 1 || W < 1 || D < 1 || k < 1 || k > kMaxK) return 0;
+        carve_assign(c, (long long)H * W, D, k);
+        break;
+    case VQNNF_OP_FILTER_RESPONSES:
+        return 256;
+    case VQNNF_OP_SCORE:
+        if (H < 1 || W < 1 || k < 1 || k > kMaxK) return 0;
+        carve_score(c, H, W, k);
+        break;
+    default:
+        return 0;
+    }
+    return (c.off + 255) & ~size_t(255);
+}
+
+vqnnf_status vqnnf_assign(const float *X, int H, int W, int D, const float *C, int k,
+                          vqnnf_prec prec, uint8_t *labels, vqnnf_assign_stats *stats, void *ws,
+                          size_t ws_bytes, void *stream)
+{
+    if (!X || !C || !labels || !ws || H < 1 || W < 1 || D < 1 || k < 1) return VQNNF_EINVAL;
+    if (!aligned(X, 16) || !aligned(C, 16) || !aligned(ws, 256)) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    const long long n = (long long)H * W;
+    if (n >= (1ll << 32)) return VQNNF_EUNSUPPORTED;
+    if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_ASSIGN, H, W, D, k, 0, 0, 0, prec))
+        return VQNNF_ENOMEM;
+    WsCursor c{static_cast<char *>(ws), 0};
+    AssignWs w = carve_assign(c, n, D, k);
+    return run_assign(X, n, D, C, k, prec, labels, stats, w, as_stream(stream));
+}
+
+vqnnf_status vqnnf_fit_codebook(const float *T, int h, int w, int D, int k, int iters,
+                                uint64_t seed, vqnnf_prec prec, float *C, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    if (!T || !C || !ws || h < 1 || w < 1 || D < 1 || k < 1 || iters < 0) return VQNNF_EINVAL;
+    if (!aligned(T, 16) || !aligned(C, 16) || !aligned(ws, 256)) return VQNNF_EINVAL;
+    const long long l = (long long)h * w;
+    if (k > l) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (l > (1ll << 30)) return VQNNF_EUNSUPPORTED;
+    if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_FIT, h, w, D, k, 0, 0, 0, prec))
+        return VQNNF_ENOMEM;
+    cudaStream_t s = as_stream(stream);
+    WsCursor c{static_cast<char *>(ws), 0};
+    FitWs fw = carve_fit(c, l, D, k);
+    InitIdx ii;
+    memset(&ii, 0, sizeof(ii));
+    kmeans_init_indices(l, k, seed, ii.idx);
+    cudaError_t e = launch_gather_init(T, D, k, ii, C, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int it = 0; it < iters; ++it) {
+        vqnnf_status st = run_assign(T, l, D, C, k, prec, fw.lab, nullptr, fw.as, s);
+        if (st != VQNNF_OK) return st;
+        e = launch_lloyd_update(T, (int)l, D, k, fw.lab, fw.cnt, fw.off, fw.members, C, s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return VQNNF_OK;
+}
+
+vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,
+                                    const vqnnf_filter *bank, int F, int32_t *counts, void *ws,
+                                    size_t ws_bytes, void *stream)
+{
+    (void)ws; (void)ws_bytes;
+    if (!labels || !counts || h < 1 || w < 1 || k < 1) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    BankSpec bs;
+    GridSpec gs;
+    vqnnf_status st = compile_bank(bank, F, h, w, bs, gs);
+    if (st != VQNNF_OK) return st;
+    return from_cuda(launch_filter_responses(labels, h, w, k, bs, counts, as_stream(stream)));
+}
+
+vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, int tw,
+                         const vqnnf_filter *bank, int F, const int32_t *t_counts, float *heatmap,
+                         int32_t *argmax_yx, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!q_labels || !t_counts || !heatmap || !ws || H < 1 || W < 1 || k < 1 || th < 1 ||
+        tw < 1 || th > H || tw > W)
+        return VQNNF_EINVAL;
+    if (!aligned(ws, 256)) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    if ((long long)(H + 1) * (W + 1) >= (1ll << 31)) return VQNNF_EUNSUPPORTED;
+    if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_SCORE, H, W, 0, k, th, tw, F, 0))
+        return VQNNF_ENOMEM;
+    BankSpec bs;
+    GridSpec gs;
+    vqnnf_status st = compile_bank(bank, F, th, tw, bs, gs);
+    if (st != VQNNF_OK) return st;
+    const size_t smem = score_smem_bytes(bs, gs, k);
+    if (smem > (size_t)device_smem_optin()) return VQNNF_EUNSUPPORTED;
+    cudaStream_t s = as_stream(stream);
+    WsCursor c{static_cast<char *>(ws), 0};
+    ScoreWs sw = carve_score(c, H, W, k);
+    cudaError_t e = launch_sat(q_labels, H, W, k, sw.carry, sw.S, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    const int HO = H - th + 1, WO = W - tw + 1;
+    return from_cuda(launch_score(sw.S, W, k, HO, WO, bs, gs, t_counts, heatmap, sw.amax,
+                                  argmax_yx, s));
+}
+
+vqnnf_status vqnnf_last_device_error(void *stream)
+{
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return VQNNF_ECUDA;
+    int err = 0;
+    if (read_and_clear_tc_error(&err) != cudaSuccess) return VQNNF_ECUDA;
+    return err ? VQNNF_ETIMEOUT : VQNNF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,468 @@
+// Nearest-neighbour field (Algorithm 1) -- codebook preparation, the FP32 SIMT distance
+// contraction with bound-driven near-tie flagging, and the compensated re-scoring stage
+// shared by both precisions.
+//
+// Distances.  For a pixel x and centroid c_j the contraction computes
+//     s_j = ||c_j - m||^2 - 2 (x - m) . (c_j - m)  =  ||x - c_j||^2 - ||x - m||^2
+// with m the FP32 mean of the codebook (centring shrinks the norms that scale the
+// rounding error; the argmin over j is unchanged).  A proven per-pixel bound B_j on
+// |s_j - exact| gives an interval for every distance; the pixel's label is decided when
+// exactly one interval reaches below the smallest upper end, otherwise the pixel and its
+// candidate set go to the re-scoring stage, which decides them from the uncentred FP32
+// inputs in compensated arithmetic.
+//
+// Bound (u = 2^-24, X = ||x'|| with x' = fl(x - m), Delta = ||x' - A-operand||):
+//     B_j = X a_j + (Delta + u (X + Delta)(1 + 4u)) v_j + b_j + 4u |s_j|,  inflated by 2^-8
+// with per-centroid a_j, v_j, b_j written by prep_codebook (derivation in the design
+// notes: contraction accumulation error, rounding of the centred codebook and of x').
+#include <cuda_bf16.h>
+
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace vqnnf {
+namespace {
+
+constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
+
+// ----------------------------------------------------------------------------------
+// Codebook preparation (FP64): reference point, centred copies and bound terms.
+// ----------------------------------------------------------------------------------
+__global__ void prep_mean_kernel(const float *__restrict__ C, int k, int D, float *mean)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += (double)C[(size_t)j * D + i];
+    mean[i] = (float)(s / (double)k);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h)
+{
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+
+// One block per centroid.  Sums are reduced in a fixed tree order (deterministic).
+__global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restrict__ C, int k,
+                                                            int D, int prec, CodebookPrep p)
+{
+    const int j = blockIdx.x;
+    __shared__ double red[6][256];
+    double s_c2 = 0, s_cc2 = 0, s_d32 = 0, s_hi2 = 0, s_lo2 = 0, s_d16 = 0;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        double cs = (double)C[(size_t)j * D + i] - (double)p.mean[i];   // exact in FP64
+        float cf = (float)cs;
+        p.cc[(size_t)j * D + i] = cf;
+        __nv_bfloat16 hi = __double2bfloat16(cs);
+        double r = cs - (double)__bfloat162float(hi);
+        __nv_bfloat16 lo = __double2bfloat16(r);
+        double d16 = r - (double)__bfloat162float(lo);
+        p.chi[(size_t)j * D + i] = bf16_bits(hi);
+        p.clo[(size_t)j * D + i] = bf16_bits(lo);
+        double hif = (double)__bfloat162float(hi), lof = (double)__bfloat162float(lo);
+        double d32 = cs - (double)cf;
+        s_c2 += cs * cs;
+        s_cc2 += (double)cf * (double)cf;
+        s_d32 += d32 * d32;
+        s_hi2 += hif * hif;
+        s_lo2 += lof * lof;
+        s_d16 += d16 * d16;
+    }
+    red[0][threadIdx.x] = s_c2;
+    red[1][threadIdx.x] = s_cc2;
+    red[2][threadIdx.x] = s_d32;
+    red[3][threadIdx.x] = s_hi2;
+    red[4][threadIdx.x] = s_lo2;
+    red[5][threadIdx.x] = s_d16;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double u = kU32;
+        const double g64 = (double)(D + 2) * 1.1102230246251565e-16;  // FP64 sum error
+        const double c2 = red[0][0];
+        const float n32 = (float)c2;
+        const double en = fabs((double)n32 - c2) + c2 * g64;
+        const double margin = 1.0 + 1e-6;
+        const double nc = sqrt(red[0][0]) * margin;      // ||c*||
+        const double ncc = sqrt(red[1][0]) * margin;     // ||fl32(c*)||
+        const double nd32 = sqrt(red[2][0]) * margin;    // ||c* - fl32(c*)||
+        const double nhi = sqrt(red[3][0]) * margin;
+        const double nlo = sqrt(red[4][0]) * margin;
+        const double nd16 = sqrt(red[5][0]) * margin;
+        double a, v;
+        if (prec == VQNNF_PREC_FP32) {
+            const double gD = (double)D * u / (1.0 - (double)D * u);
+            a = 2.0 * gD * ncc + 2.0 * (1.0 + 2.0 * u) * nd32;
+            v = 2.0 * (ncc > nc ? ncc : nc);
+        } else {
+            // tensor-core accumulation order and rounding are not documented: take four
+            // times the sequential FP32 bound
+            const double gacc = (double)D * 4.0 * u;
+            a = 2.0 * gacc * (nhi + nlo) + 2.0 * nd16;
+            v = 2.0 * nc;
+        }
+        p.nrm[j] = n32;
+        p.a[j] = __double2float_ru(a);
+        p.v[j] = __double2float_ru(v);
+        p.b[j] = __double2float_ru(en);
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// FP32 SIMT contraction: 128 pixels x 128 centroids per pass, 8 x 8 outputs per thread,
+// sequential FMA accumulation over D (so the per-dot error is <= gamma_D sum |x c|).
+// ----------------------------------------------------------------------------------
+constexpr int BM = 128, BN = 128, BK = 16, NT = 256;
+
+__device__ __forceinline__ void push_flag(bool flagged, unsigned int pix, const unsigned *mask,
+                                          FlagList fl)
+{
+    const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+    if (!ballot) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(fl.count, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flagged) {
+        const unsigned slot = base + __popc(ballot & ((1u << lane) - 1u));
+        fl.pix[slot] = pix;
+#pragma unroll
+        for (int w = 0; w < kMaskWords; ++w) fl.mask[(size_t)slot * kMaskWords + w] = mask[w];
+    }
+}
+
+// Epilogue shared with the tensor-core path: decide or flag one pixel from its row of
+// scores s_j (strided by `stride` floats), X = ||A-side vector||, Dl = rounding residual.
+__device__ __forceinline__ int decide_pixel(const float *srow, int stride, int k, float X, float Dl,
+                                            const float *ca, const float *cv, const float *cb,
+                                            unsigned *mask, int *ncand)
+{
+    const float u = (float)kU32;
+    const float Y = Dl + u * (X + Dl) * (1.0f + 4.0f * u);
+    const float infl = 1.0f + 0.00390625f;
+    float U = FLT_MAX, smin = FLT_MAX;
+    int amin = 0;
+    for (int j = 0; j < k; ++j) {
+        const float s = srow[j * stride];
+        const float B = fmaf(X, ca[j], fmaf(Y, cv[j], cb[j] + 4.0f * u * fabsf(s))) * infl;
+        U = fminf(U, s + B);
+        if (s < smin) { smin = s; amin = j; }
+    }
+#pragma unroll
+    for (int w = 0; w < kMaskWords; ++w) mask[w] = 0u;
+    int cnt = 0, last = amin;
+    for (int j = 0; j < k; ++j) {
+        const float s = srow[j * stride];
+        const float B = fmaf(X, ca[j], fmaf(Y, cv[j], cb[j] + 4.0f * u * fabsf(s))) * infl;
+        if (s - B <= U) {
+            ++cnt;
+            last = j;
+            mask[j >> 5] |= 1u << (j & 31);
+        }
+    }
+    *ncand = cnt;
+    return cnt == 1 ? last : amin;
+}
+
+__global__ void __launch_bounds__(NT) assign_fp32_kernel(const float *__restrict__ X, long long n,
+                                                         int D, int k, CodebookPrep p,
+                                                         uint8_t *__restrict__ labels, FlagList fl)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int kp = (k + BN - 1) / BN * BN;
+    const int sp = kp + 1;
+    float *As = smem;                  // [2][BK][BM]
+    float *Bs = As + 2 * BK * BM;      // [2][BK][BN]
+    float *Sc = Bs + 2 * BK * BN;      // [BM][sp]
+    float *ca = Sc + BM * sp;          // [kp]
+    float *cv = ca + kp;
+    float *cb = cv + kp;
+    float *cn = cb + kp;
+    float *xn = cn + kp;               // [2][BM]
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const long long p0 = (long long)blockIdx.x * BM;
+    for (int j = tid; j < kp; j += NT) {
+        const bool ok = j < k;
+        ca[j] = ok ? p.a[j] : 0.f;
+        cv[j] = ok ? p.v[j] : 0.f;
+        cb[j] = ok ? p.b[j] : 0.f;
+        cn[j] = ok ? p.nrm[j] : 0.f;
+    }
+    // loader mapping: row lp (pixel or centroid), dims lh*8 .. lh*8+7 of the k-step
+    const int lp = tid >> 1, lh = tid & 1;
+    const long long prow = p0 + lp;
+    const bool prow_ok = prow < n;
+    const float *xrow = X + (prow_ok ? prow : 0) * (long long)D;
+    float xsq = 0.f;
+
+    for (int nc = 0; nc < kp; nc += BN) {
+        const int crow = nc + lp;
+        const bool crow_ok = crow < k;
+        const float *crw = p.cc + (size_t)(crow_ok ? crow : 0) * D;
+        float acc[8][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+        float ra[8], rb[8];
+        auto gload = [&](int d0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int d = d0 + lh * 8 + q * 4;
+                float4 xa = make_float4(0, 0, 0, 0), cbv = make_float4(0, 0, 0, 0);
+                if (d < D) {
+                    if (prow_ok) {
+                        xa = __ldg(reinterpret_cast<const float4 *>(xrow + d));
+                        const float4 mm = __ldg(reinterpret_cast<const float4 *>(p.mean + d));
+                        xa.x -= mm.x; xa.y -= mm.y; xa.z -= mm.z; xa.w -= mm.w;
+                    }
+                    if (crow_ok) cbv = __ldg(reinterpret_cast<const float4 *>(crw + d));
+                }
+                ra[q * 4 + 0] = xa.x; ra[q * 4 + 1] = xa.y; ra[q * 4 + 2] = xa.z; ra[q * 4 + 3] = xa.w;
+                rb[q * 4 + 0] = cbv.x; rb[q * 4 + 1] = cbv.y; rb[q * 4 + 2] = cbv.z; rb[q * 4 + 3] = cbv.w;
+            }
+        };
+        auto sstore = [&](int buf) {
+            float *a = As + buf * BK * BM;
+            float *b = Bs + buf * BK * BN;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                a[(lh * 8 + q) * BM + lp] = ra[q];
+                b[(lh * 8 + q) * BN + lp] = rb[q];
+            }
+        };
+        gload(0);
+        if (nc == 0)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xsq = fmaf(ra[q], ra[q], xsq);
+        sstore(0);
+        __syncthreads();
+        int buf = 0;
+        for (int d0 = 0; d0 < D; d0 += BK) {
+            const bool more = d0 + BK < D;
+            if (more) gload(d0 + BK);
+            const float *a = As + buf * BK * BM;
+            const float *b = Bs + buf * BK * BN;
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4 *>(a + kk * BM + ty * 4);
+                const float4 a1 = *reinterpret_cast<const float4 *>(a + kk * BM + 64 + ty * 4);
+                const float4 b0 = *reinterpret_cast<const float4 *>(b + kk * BN + tx * 4);
+                const float4 b1 = *reinterpret_cast<const float4 *>(b + kk * BN + 64 + tx * 4);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) acc[i][jj] = fmaf(av[i], bv[jj], acc[i][jj]);
+            }
+            if (more) {
+                if (nc == 0)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) xsq = fmaf(ra[q], ra[q], xsq);
+                sstore(buf ^ 1);
+            }
+            __syncthreads();
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+                const int c = nc + ((jj < 4) ? tx * 4 + jj : 64 + tx * 4 + (jj - 4));
+                Sc[r * sp + c] = fmaf(-2.0f, acc[i][jj], cn[c]);
+            }
+        }
+    }
+    xn[lh * BM + lp] = xsq;
+    __syncthreads();
+    if (tid < BM) {
+        const long long pix = p0 + tid;
+        const bool valid = pix < n;
+        const float xs = xn[tid] + xn[BM + tid];
+        const float X = sqrtf(xs) * (1.0f + (float)(D + 8) * (float)kU32);
+        unsigned mask[kMaskWords];
+        int ncand = 1;
+        int lab = 0;
+        if (valid) lab = decide_pixel(Sc + tid * sp, 1, k, X, 0.0f, ca, cv, cb, mask, &ncand);
+        if (valid) labels[pix] = (uint8_t)lab;
+        push_flag(valid && ncand > 1, (unsigned)pix, mask, fl);
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Re-scoring of flagged pixels: one warp per pixel, uncentred FP32 inputs.
+// Stage 1: plain FP32 direct form sum (x_i - c_i)^2, lane-sequential then a fixed
+//          butterfly; every term is non-negative, so the relative error is at most
+//          rho = (ceil(D/32) + 8) u.  Decided when the two smallest intervals separate.
+// Stage 2: double-float direct form -- exact differences (TwoSum), exact squares
+//          (FMA), compensated accumulation -- relative error about D u^2; ties between
+//          equal values go to the lowest index.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void df_warp_sum(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+    float s, e;
+    two_sum(hi, lo, s, e);   // renormalise
+    hi = s;
+    lo = e;
+}
+
+__global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ X, int D,
+                                                      const float *__restrict__ C, int k,
+                                                      uint8_t *__restrict__ labels, FlagList fl)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    const unsigned n_entries = *fl.count;
+    const float u = (float)kU32;
+    const float rho = ((float)((D + 31) / 32) + 8.0f) * u * 1.01f + 4.0f * u;
+    unsigned long long my_cand = 0, my_deep = 0;
+    for (unsigned e = wid; e < n_entries; e += nw) {
+        const unsigned pix = fl.pix[e];
+        unsigned mw = lane < kMaskWords ? fl.mask[(size_t)e * kMaskWords + lane] : 0u;
+        const float *x = X + (size_t)pix * D;
+        float r1 = FLT_MAX, r2 = FLT_MAX;
+        int a = 0, nc = 0;
+        for (int w = 0; w < kMaskWords; ++w) {
+            unsigned bits = __shfl_sync(0xffffffffu, mw, w);
+            while (bits) {
+                const int j = w * 32 + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const float *c = C + (size_t)j * D;
+                float acc = 0.f;
+                for (int i = lane; i < D; i += 32) {
+                    const float d = x[i] - c[i];
+                    acc = fmaf(d, d, acc);
+                }
+                const float r = warp_sum(acc);
+                ++nc;
+                if (r < r1) { r2 = r1; r1 = r; a = j; }
+                else if (r < r2) { r2 = r; }
+            }
+        }
+        const bool decided = r2 * (1.0f - rho) > r1 * (1.0f + rho);
+        if (!decided) {
+            float bh = FLT_MAX, bl = 0.f;
+            int best = 0;
+            for (int w = 0; w < kMaskWords; ++w) {
+                unsigned bits = __shfl_sync(0xffffffffu, mw, w);
+                while (bits) {
+                    const int j = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float *c = C + (size_t)j * D;
+                    float S = 0.f, E = 0.f;
+                    for (int i = lane; i < D; i += 32) {
+                        const float xi = x[i], ci = c[i];
+                        float h, l;
+                        two_sum(xi, -ci, h, l);          // xi - ci = h + l exactly
+                        const float p2 = h * h;
+                        const float pe = fmaf(h, h, -p2);  // h^2 = p2 + pe exactly
+                        float t, te;
+                        two_sum(S, p2, t, te);
+                        S = t;
+                        E += te + pe + fmaf(2.0f * h, l, l * l);
+                    }
+                    df_warp_sum(S, E);
+                    if (S < bh || (S == bh && E < bl)) { bh = S; bl = E; best = j; }
+                }
+            }
+            a = best;
+            ++my_deep;
+        }
+        my_cand += (unsigned long long)nc;
+        if (lane == 0) labels[pix] = (uint8_t)a;
+    }
+    if (lane == 0 && (my_cand | my_deep)) {
+        atomicAdd(&fl.stats[1], my_cand);
+        if (my_deep) atomicAdd(&fl.stats[2], my_deep);
+    }
+}
+
+__global__ void finish_stats_kernel(FlagList fl, vqnnf_assign_stats *out)
+{
+    out->n_flagged = *fl.count;
+    out->n_candidates = fl.stats[1];
+    out->n_deep = fl.stats[2];
+    out->reserved = 0;
+}
+
+}  // namespace
+
+cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
+                                 cudaStream_t s)
+{
+    prep_mean_kernel<<<(D + 255) / 256, 256, 0, s>>>(C, k, D, p.mean);
+    prep_centroid_kernel<<<k, 256, 0, s>>>(C, k, D, prec, p);
+    return cudaGetLastError();
+}
+
+static size_t fp32_smem_bytes(int k)
+{
+    const int kp = (k + BN - 1) / BN * BN;
+    return sizeof(float) * (size_t)(2 * BK * BM + 2 * BK * BN + BM * (kp + 1) + 4 * kp + 2 * BM);
+}
+
+cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k, const CodebookPrep &p,
+                               uint8_t *labels, FlagList fl, cudaStream_t s)
+{
+    const size_t smem = fp32_smem_bytes(k);
+    cudaError_t e = cudaFuncSetAttribute(assign_fp32_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (n + BM - 1) / BM;
+    assign_fp32_kernel<<<(unsigned)blocks, NT, smem, s>>>(X, n, D, k, p, labels, fl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
+                           uint8_t *labels, FlagList fl, cudaStream_t s)
+{
+    (void)n;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    rescore_kernel<<<sms * 8, 256, 0, s>>>(X, D, C, k, labels, fl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s)
+{
+    finish_stats_kernel<<<1, 1, 0, s>>>(fl, out);
+    return cudaGetLastError();
+}
+
+}  // namespace vqnnf

@@ -1,0 +1,73 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vqnnf.h"
+
+namespace vqnnf {
+
+constexpr int kMaxK = 256;          // labels are uint8
+constexpr int kMaskWords = kMaxK / 32;
+
+// Per-centroid terms of the assignment error bound and the centred codebook, written by
+// prep_codebook (assign_fp32.cu) into the workspace.
+struct CodebookPrep {
+    float *mean;      // D       reference point m (the FP32 codebook mean)
+    float *cc;        // k x D   FP32 rounding of c_j - m
+    uint16_t *chi;    // k x D   BF16 rounding of c_j - m              (BF16 path)
+    uint16_t *clo;    // k x D   BF16 rounding of the remainder        (BF16 path)
+    float *nrm;       // k       FP32 rounding of ||c_j - m||^2
+    float *a;         // k       bound coefficient of ||x'||
+    float *v;         // k       bound coefficient of the per-pixel rounding residual
+    float *b;         // k       bound constant (error of nrm)
+};
+
+// List of pixels whose contraction result is ambiguous, with their candidate sets.
+struct FlagList {
+    unsigned int *count;      // device counter
+    unsigned int *pix;        // capacity entries
+    unsigned int *mask;       // capacity x kMaskWords candidate bit sets
+    unsigned long long *stats;  // [n_flagged, n_candidates, n_deep, reserved]
+};
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
+                                 cudaStream_t s);
+cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k,
+                               const CodebookPrep &p, uint8_t *labels, FlagList fl,
+                               cudaStream_t s);
+cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k,
+                               const CodebookPrep &p, uint8_t *labels, FlagList fl,
+                               cudaStream_t s);
+cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
+                           uint8_t *labels, FlagList fl, cudaStream_t s);
+cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s);
+
+// Device error word of the tensor-core translation unit (bounded waits).
+cudaError_t read_and_clear_tc_error(int *out);
+
+// Initial centroid indices of the k-means (kernel parameter).
+struct InitIdx {
+    int32_t idx[kMaxK];
+};
+cudaError_t launch_gather_init(const float *T, int D, int k, const InitIdx &ii, float *C,
+                               cudaStream_t s);
+cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8_t *lab, int *cnt,
+                                int *off, int *members, float *C, cudaStream_t s);
+
+}  // namespace vqnnf
+
+// Bump allocator over a caller-provided workspace (256-byte alignment).
+struct WsCursor {
+    char *base;
+    size_t off;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};

@@ -1,0 +1,108 @@
+// k-means codebook of the template (Sec. 3.1): seeded initial centroids, then Lloyd
+// steps whose assignment is the exact nearest-neighbour field of assign_fp32.cu /
+// assign_tc.cu and whose update sums every cluster's members in FP64 in pixel order.
+//
+// Determinism: the members of each cluster are listed in pixel order by a stable counting
+// sort, and thread (j, i) adds member features one after another in that order, so every
+// FP64 sum is the same sequence of additions as a plain loop over pixels -- the centroids
+// do not depend on scheduling.
+#include "common.cuh"
+
+namespace vqnnf {
+
+namespace {
+
+__global__ void gather_init_kernel(const float *__restrict__ T, int D, int k, InitIdx ii,
+                                   float *__restrict__ C)
+{
+    const int j = blockIdx.x;
+    const float *src = T + (size_t)ii.idx[j] * D;
+    for (int i = threadIdx.x; i < D; i += blockDim.x) C[(size_t)j * D + i] = src[i];
+}
+
+// Stable counting sort of the labels by cluster (one block of 1024 threads).
+//   cnt[k], off[k+1], members[l] (pixel indices in increasing order within a cluster)
+__global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__restrict__ lab,
+                                                           int l, int k, int *cnt, int *off,
+                                                           int *members)
+{
+    __shared__ int hist[kMaxK];
+    __shared__ int base[kMaxK];
+    __shared__ int wc[32][kMaxK];   // per-warp counts of the current chunk
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int j = t; j < k; j += blockDim.x) hist[j] = 0;
+    __syncthreads();
+    for (int p = t; p < l; p += blockDim.x) atomicAdd(&hist[lab[p]], 1);
+    __syncthreads();
+    if (t == 0) {
+        int s = 0;
+        for (int j = 0; j < k; ++j) {
+            base[j] = s;
+            off[j] = s;
+            cnt[j] = hist[j];
+            s += hist[j];
+        }
+        off[k] = s;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < l; c0 += blockDim.x) {
+        for (int q = t; q < 32 * kMaxK; q += blockDim.x) (&wc[0][0])[q] = 0;
+        __syncthreads();
+        const int p = c0 + t;
+        const bool ok = p < l;
+        const int lb = ok ? (int)lab[p] : -1 - lane;     // unique dummies never match
+        const unsigned same = __match_any_sync(0xffffffffu, lb);
+        const int rank = __popc(same & ((1u << lane) - 1u));
+        if (ok && rank == 0) wc[w][lb] = __popc(same);
+        __syncthreads();
+        // exclusive prefix over warps for every cluster; base advances by the chunk total
+        for (int j = t; j < k; j += blockDim.x) {
+            int s = base[j];
+            for (int q = 0; q < 32; ++q) {
+                const int c = wc[q][j];
+                wc[q][j] = s;
+                s += c;
+            }
+            base[j] = s;
+        }
+        __syncthreads();
+        if (ok) members[wc[w][lb] + rank] = p;
+        __syncthreads();
+    }
+}
+
+// c_j[i] = fl32( (sum over members, pixel order, FP64) / count ); empty clusters keep c_j.
+__global__ void update_kernel(const float *__restrict__ T, int D, int k,
+                              const int *__restrict__ cnt, const int *__restrict__ off,
+                              const int *__restrict__ members, float *__restrict__ C)
+{
+    const int j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    const int c = cnt[j];
+    if (c == 0) return;
+    const int *m = members + off[j];
+    double s = 0.0;
+    for (int q = 0; q < c; ++q) s += (double)T[(size_t)m[q] * D + i];
+    C[(size_t)j * D + i] = (float)(s / (double)c);
+}
+
+}  // namespace
+
+cudaError_t launch_gather_init(const float *T, int D, int k, const InitIdx &ii, float *C,
+                               cudaStream_t s)
+{
+    gather_init_kernel<<<k, 128, 0, s>>>(T, D, k, ii, C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8_t *lab, int *cnt,
+                                int *off, int *members, float *C, cudaStream_t s)
+{
+    stable_sort_kernel<<<1, 1024, 0, s>>>(lab, l, k, cnt, off, members);
+    dim3 g((D + 127) / 128, k);
+    update_kernel<<<g, 128, 0, s>>>(T, D, k, cnt, off, members, C);
+    return cudaGetLastError();
+}
+
+}  // namespace vqnnf

@@ -1,0 +1,56 @@
+// Filter-bank descriptions passed to the score kernels by value (kernel parameters).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vqnnf {
+
+constexpr int kMaxFilters = 32;
+constexpr int kMaxRects = 64;
+constexpr int kMaxRows = 2 * kMaxRects;
+
+// One weighted half-open rectangle; ry0 / ry1 index the bank's distinct row offsets.
+struct RectSpec {
+    int x0, y0, x1, y1, weight;
+    int ry0, ry1;
+};
+
+// Any bank: F filters, rectangles of filter f are rect[rect_begin[f] .. rect_begin[f+1]).
+struct BankSpec {
+    int F;
+    int nrow;                     // distinct row offsets staged per window row
+    int ncol;                     // staged columns per row (256 windows + template width)
+    int roff[kMaxRows];           // the distinct row offsets, ascending
+    int rect_begin[kMaxFilters + 1];
+    RectSpec rect[kMaxRects];
+    float coef[kMaxFilters];      // w_f / A_f
+};
+
+// Grid bank: the window cut by column boundaries bx[0..G] and row boundaries by[0..G]
+// into G x G cells (slot r * G + c), optionally with the full window (slot G * G).  Every
+// filter is one cell or the full window with weight 1.
+struct GridSpec {
+    int G;                        // 0 = not a grid bank
+    int full;
+    int F;
+    int ncol;
+    int bx[5];
+    int by[5];
+    int slot_filter[17];          // slot -> filter index
+    int filter_slot[kMaxFilters]; // filter index -> slot
+    float coef[kMaxFilters];
+};
+
+size_t score_smem_bytes(const BankSpec &bs, const GridSpec &gs, int k);
+int sat_pitch(int W);
+int sat_strips(int W);
+int score_ncol(int tw);
+cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, int *carry, int *S, cudaStream_t s);
+cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, const BankSpec &bs,
+                                    int32_t *counts, cudaStream_t s);
+cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankSpec &bs,
+                         const GridSpec &gs, const int32_t *tc, float *heat,
+                         unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s);
+
+}  // namespace vqnnf

@@ -1,0 +1,130 @@
+"""The C ABI library: it loads, exports every entry point the header declares, and checks
+its arguments on the host (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vqnnf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_15010_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vqnnf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["vqnnf_fit_codebook", "vqnnf_assign", "vqnnf_filter_responses", "vqnnf_score",
+                 "vqnnf_workspace_bytes", "vqnnf_status_str", "vqnnf_last_device_error"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2306_15010_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_version_and_status_strings(lib):
+    assert lib.vqnnf_version() == 100
+    assert lib.vqnnf_status_str(0) == b"ok"
+    assert lib.vqnnf_status_str(2) == b"workspace too small"
+    assert lib.vqnnf_status_str(99) == b"unknown status"
+
+
+def test_workspace_sizes(lib):
+    from paper_2306_15010_gb300 import _lib
+    a = lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 2048, 2048, 512, 128, 0, 0, 0, 1)
+    assert a % 256 == 0 and a > 2048 * 2048 * 36
+    assert lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 2048, 2048, 512, 257, 0, 0, 0, 1) == 0
+    s = lib.vqnnf_workspace_bytes(_lib.OP_SCORE, 256, 256, 0, 16, 32, 32, 5, 0)
+    assert s >= 257 * 16 * 260 * 4
+    assert lib.vqnnf_workspace_bytes(99, 1, 1, 1, 1, 1, 1, 1, 0) == 0
+    f = lib.vqnnf_workspace_bytes(_lib.OP_FIT, 128, 128, 512, 128, 0, 0, 0, 0)
+    assert f > lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 128, 128, 512, 128, 0, 0, 0, 0)
+
+
+FAKE = 1 << 20          # a non-null, 256-aligned pointer value never dereferenced
+
+
+def test_assign_argument_errors(lib):
+    from paper_2306_15010_gb300 import _lib
+    ws = lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 4, 4, 16, 3, 0, 0, 0, 0)
+    call = lambda **kw: lib.vqnnf_assign(*[kw.get(n, d) for n, d in [
+        ("X", FAKE), ("H", 4), ("W", 4), ("D", 16), ("C", FAKE), ("k", 3), ("prec", 0),
+        ("labels", FAKE), ("stats", None), ("ws", FAKE), ("ws_bytes", ws), ("stream", None)]])
+    assert call(X=None) == _lib.EINVAL
+    assert call(labels=None) == _lib.EINVAL
+    assert call(H=0) == _lib.EINVAL
+    assert call(k=0) == _lib.EINVAL
+    assert call(k=300) == _lib.EUNSUPPORTED
+    assert call(X=FAKE + 4) == _lib.EINVAL           # misaligned features
+    assert call(prec=7) == _lib.EINVAL
+    assert call(D=18, prec=0) == _lib.EUNSUPPORTED    # FP32 path wants D % 4 == 0
+    assert call(D=20, prec=1) == _lib.EUNSUPPORTED    # tensor path wants D % 16 == 0
+    assert call(ws_bytes=ws - 1) == _lib.ENOMEM
+
+
+def test_fit_argument_errors(lib):
+    from paper_2306_15010_gb300 import _lib
+    ws = lib.vqnnf_workspace_bytes(_lib.OP_FIT, 4, 4, 8, 3, 0, 0, 0, 0)
+    def call(**kw):
+        a = dict(T=FAKE, h=4, w=4, D=8, k=3, iters=2, seed=ctypes.c_uint64(1), prec=0, C=FAKE,
+                 ws=FAKE, ws_bytes=ws, stream=None)
+        a.update(kw)
+        return lib.vqnnf_fit_codebook(*a.values())
+    assert call(k=17) == _lib.EINVAL                  # more clusters than pixels
+    assert call(iters=-1) == _lib.EINVAL
+    assert call(C=None) == _lib.EINVAL
+    assert call(ws_bytes=16) == _lib.ENOMEM
+
+
+def _bank(rects, w_f=1.0, area=None):
+    from paper_2306_15010_gb300 import Bank
+    area = area if area is not None else float(sum((r[2] - r[0]) * (r[3] - r[1]) for r in rects))
+    return Bank([{"rects": rects, "w_f": w_f, "area": area}])
+
+
+def test_score_rejects_bad_banks_and_shapes(lib):
+    from paper_2306_15010_gb300 import _lib
+    ws = lib.vqnnf_workspace_bytes(_lib.OP_SCORE, 16, 16, 0, 4, 4, 4, 1, 0)
+    def call(bank, **kw):
+        a = dict(q=FAKE, H=16, W=16, k=4, th=4, tw=4, bank=bank.ptr, F=bank.F, tc=FAKE,
+                 heat=FAKE, am=None, ws=FAKE, ws_bytes=ws, stream=None)
+        a.update(kw)
+        return lib.vqnnf_score(*a.values())
+    good = _bank([(0, 0, 4, 4, 1)])
+    assert call(good, th=17) == _lib.EINVAL           # template taller than the query
+    assert call(good, F=0) == _lib.EINVAL
+    assert call(good, ws_bytes=100) == _lib.ENOMEM
+    assert call(_bank([(0, 0, 5, 4, 1)])) == _lib.EINVAL    # rectangle outside the window
+    assert call(_bank([(2, 0, 2, 4, 1)])) == _lib.EINVAL    # empty rectangle
+    assert call(_bank([(0, 0, 4, 4, 1)], area=0.0)) == _lib.EINVAL
+    assert call(_bank([(0, 0, 4, 4, 1)], w_f=float("nan"))) == _lib.EINVAL
+
+
+def test_filter_responses_rejects_bad_banks(lib):
+    from paper_2306_15010_gb300 import _lib
+    b = _bank([(0, 0, 9, 4, 1)])
+    assert lib.vqnnf_filter_responses(FAKE, 4, 8, 4, b.ptr, 1, FAKE, None, 0, None) == _lib.EINVAL
+    assert lib.vqnnf_filter_responses(None, 4, 8, 4, b.ptr, 1, FAKE, None, 0, None) == _lib.EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2306_15010_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        _lib.load()

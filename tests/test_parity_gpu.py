@@ -1,0 +1,245 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the arithmetic, see the design notes):
+* labels: equal to the oracle's wherever the oracle's own relative gap between the two best
+  distances is >= 1e-6 (the near-tie band); duplicate centroids must give the lowest index;
+* codebook: bit-identical (same FP64 additions in the same order, same roundings);
+* counts: exact integers;
+* heatmap from identical labels: |H_gpu - H_ref| <= 1e-5 * max|H_ref| (F float32 terms);
+  heatmap of the whole path: <= 1e-4 * max|H_ref|.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vq():
+    from paper_2306_15010_gb300 import build
+    build.build()
+    import paper_2306_15010_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _dev(a):
+    return torch.as_tensor(a).cuda()
+
+
+def _labels_ok(gpu, ref, d1, d2):
+    band = oracle.relative_gap(d1, d2) < 1e-6
+    bad = (gpu.astype(np.int32) != ref) & ~band
+    return int(bad.sum()), int(band.sum())
+
+
+def _codebook_case(H, W, D, k, seed, th=None, tw=None, iters=3):
+    q = synth.query_map(H, W, D, M=max(4, k // 2 + 3), n_sp=max(8, H * W // 200), seed=seed)
+    th = th or max(4, H // 4)
+    tw = tw or max(4, W // 4)
+    T, _ = synth.crop_template(q, th, tw, seed=seed + 1000)
+    C = oracle.fit_codebook(T.numpy(), k, iters, seed)
+    return q, T, C
+
+
+PRECS = ["fp32"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("H,W,D,k", [
+    (256, 256, 64, 16),      # config-1 query
+    (129, 67, 64, 16),       # ragged tail of the 128-pixel tile
+    (33, 50, 512, 128),      # headline depth and codebook size
+    (40, 41, 16, 8),
+    (17, 19, 32, 256),       # largest k (two 128-centroid passes)
+    (9, 7, 4, 3),            # D = 4, partial k tile
+    (1, 1, 64, 5),           # a single pixel
+])
+def test_assign_parity(vq, prec, H, W, D, k):
+    q, _, C = _codebook_case(H, W, D, k, seed=H * 7 + W)
+    ref, d1, d2 = oracle.assign(q.X.numpy(), C, return_dist=True)
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    lab = vq.vqnnf_assign(_dev(q.X), _dev(C), prec, stats=stats).cpu().numpy()
+    bad, inband = _labels_ok(lab, ref, d1, d2)
+    assert bad == 0, f"{bad} labels differ outside the near-tie band ({inband} in band)"
+    n_flag, n_cand, n_deep, _ = stats.cpu().tolist()
+    assert 0 <= n_flag <= H * W and n_cand >= 2 * n_flag and n_deep <= n_flag
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_assign_k1_and_duplicates_lowest_index(vq, prec):
+    r = np.random.default_rng(3)
+    X = r.random((37, 45, 32)).astype(np.float32)
+    C1 = r.random((1, 32)).astype(np.float32)
+    assert int(vq.vqnnf_assign(_dev(X), _dev(C1), prec).max()) == 0
+    base = r.random((5, 32)).astype(np.float32)
+    C = np.concatenate([base, base[[3, 1]]])          # duplicates at 5 (of 3) and 6 (of 1)
+    ref = oracle.assign(X, C)
+    got = vq.vqnnf_assign(_dev(X), _dev(C), prec).cpu().numpy()
+    assert np.array_equal(got.astype(np.int32), ref)
+    assert got.max() <= 4
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_assign_points_on_centroids(vq, prec):
+    # pixels equal to centroids: distance 0 against a clear second best
+    r = np.random.default_rng(4)
+    C = r.random((24, 64)).astype(np.float32)
+    X = C[r.integers(0, 24, size=(31, 33))]
+    got = vq.vqnnf_assign(_dev(X), _dev(C), prec).cpu().numpy()
+    assert np.array_equal(got.astype(np.int32), oracle.assign(X, C))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("h,w,D,k,iters", [(32, 32, 64, 16, 10), (48, 40, 128, 32, 6),
+                                           (8, 8, 16, 64, 3), (20, 13, 32, 1, 2)])
+def test_fit_codebook_bit_exact(vq, prec, h, w, D, k, iters):
+    q = synth.query_map(4 * h, 4 * w, D, M=12, n_sp=60, seed=h + w)
+    T, _ = synth.crop_template(q, h, w, seed=5)
+    ref = oracle.fit_codebook(T.numpy(), k, iters, 99)
+    got = vq.vqnnf_fit_codebook(_dev(T), k, iters, 99, prec).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_fit_zero_iters_gathers_seeded_init(vq):
+    r = np.random.default_rng(6)
+    T = r.random((30, 31, 8)).astype(np.float32)
+    got = vq.vqnnf_fit_codebook(_dev(T), 40, 0, 2024).cpu().numpy()
+    assert np.array_equal(got, T.reshape(-1, 8)[oracle.kmeans_init(30 * 31, 40, 2024)])
+
+
+def _banks(th, tw):
+    weighted = [
+        {"rects": [(0, 0, tw, th, 1)], "w_f": 1.0, "area": float(th * tw)},
+        {"rects": [(0, 0, tw // 2, th, 1), (tw // 2, 0, tw, th, -1)], "w_f": 0.25,
+         "area": float(th * tw)},
+        {"rects": [(0, 0, tw, th // 3, 1), (0, th // 3, tw, 2 * th // 3, -2),
+                   (0, 2 * th // 3, tw, th, 1)], "w_f": 0.25, "area": float(th * tw)},
+        {"rects": [(1, 2, tw - 1, th - 1, 3)], "w_f": 0.5, "area": float((tw - 2) * (th - 3))},
+    ]
+    return {"grid2": synth.grid_bank(th, tw, 2), "grid3": synth.grid_bank(th, tw, 3),
+            "grid3_nofull": synth.grid_bank(th, tw, 3, full=False),
+            "grid4": synth.grid_bank(th, tw, 4), "full_only": synth.grid_bank(th, tw, 1, full=False),
+            "weighted": weighted}
+
+
+@pytest.mark.parametrize("bank_name", ["grid2", "grid3", "grid3_nofull", "grid4", "full_only",
+                                       "weighted"])
+def test_filter_responses_exact(vq, bank_name):
+    r = np.random.default_rng(7)
+    th, tw, k = 37, 29, 11
+    t = r.integers(0, k, size=(th, tw)).astype(np.int32)
+    bank = _banks(th, tw)[bank_name]
+    got = vq.vqnnf_filter_responses(_dev(t.astype(np.uint8)), k, bank).cpu().numpy()
+    assert np.array_equal(got, oracle.filter_counts(t, k, bank))
+
+
+def _check_heat(got_heat, got_am, ref_heat, rtol):
+    scale = max(np.abs(ref_heat).max(), 1e-30)
+    err = np.abs(got_heat - ref_heat).max() / scale
+    assert err <= rtol, f"heatmap relative error {err:.3g}"
+    y, x = got_am
+    # the reported maximum is a maximum of the oracle heatmap up to the tolerance, and the
+    # lowest row-major index among the GPU's own maxima
+    assert ref_heat[y, x] >= ref_heat.max() - 2 * rtol * scale
+    flat = np.flatnonzero(got_heat.ravel() == got_heat.max())[0]
+    assert (y, x) == divmod(int(flat), got_heat.shape[1])
+
+
+@pytest.mark.parametrize("bank_name", ["grid2", "grid3", "grid3_nofull", "grid4", "full_only",
+                                       "weighted"])
+@pytest.mark.parametrize("H,W,th,tw,k", [(96, 300, 37, 29, 11), (70, 64, 70, 64, 6),
+                                         (41, 260, 9, 5, 3)])
+def test_score_from_oracle_labels(vq, bank_name, H, W, th, tw, k):
+    r = np.random.default_rng(H + W)
+    q = synth.query_map(H, W, 4, M=6, n_sp=max(8, H * W // 150), seed=H)
+    ql = (q.sp_id.numpy() * 7 % k).astype(np.int32)       # piecewise-constant label field
+    ql[r.random(ql.shape) < 0.05] = r.integers(0, k)      # plus salt
+    t = ql[3:3 + th, 1:1 + tw].copy() if th < H else ql.copy()
+    bank = _banks(th, tw)[bank_name]
+    tc = oracle.filter_counts(t, k, bank)
+    ref, _ = oracle.score(ql, k, th, tw, bank, tc)
+    heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank,
+                              _dev(tc.astype(np.int32)))
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+
+
+def test_score_k1_and_whole_query(vq):
+    ql = np.zeros((50, 40), np.int32)
+    bank = synth.grid_bank(10, 8, 3)
+    tc = oracle.filter_counts(ql[:10, :8], 1, bank)
+    heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), 1, 10, 8, bank, _dev(tc.astype(np.int32)))
+    assert float(heat.abs().max()) == 0.0 and am.cpu().tolist() == [0, 0]
+    r = np.random.default_rng(9)
+    ql = r.integers(0, 5, size=(23, 31)).astype(np.int32)
+    bank = synth.grid_bank(23, 31, 2)
+    tc = oracle.filter_counts(ql, 5, bank)
+    heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), 5, 23, 31, bank, _dev(tc.astype(np.int32)))
+    assert heat.shape == (1, 1) and float(heat[0, 0]) == 0.0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_whole_path_config1(vq, prec):
+    """256x256 query, D=64, k=16, 32x32 template, F=5: every step on the GPU vs the oracle."""
+    q = synth.query_map(256, 256, 64, M=32, n_sp=200, seed=1000)
+    T, (ty, tx) = synth.crop_template(q, 32, 32, seed=2000)
+    k, iters, seed = 16, 10, 3000
+    bank = synth.grid_bank(32, 32, 2)
+    C = vq.vqnnf_fit_codebook(_dev(T), k, iters, seed, prec)
+    t_lab = vq.vqnnf_assign(_dev(T), C, prec)
+    q_lab = vq.vqnnf_assign(_dev(q.X), C, prec)
+    tc = vq.vqnnf_filter_responses(t_lab, k, bank)
+    heat, am = vq.vqnnf_score(q_lab, k, 32, 32, bank, tc)
+    C_ref = oracle.fit_codebook(T.numpy(), k, iters, seed)
+    assert np.array_equal(C.cpu().numpy(), C_ref)
+    ql_ref, d1, d2 = oracle.assign(q.X.numpy(), C_ref, return_dist=True)
+    bad, _ = _labels_ok(q_lab.cpu().numpy(), ql_ref, d1, d2)
+    assert bad == 0
+    tl_ref = oracle.assign(T.numpy(), C_ref)
+    tc_ref = oracle.filter_counts(tl_ref, k, bank)
+    heat_ref, _ = oracle.score(ql_ref, k, 32, 32, bank, tc_ref)
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), heat_ref, 1e-4)
+
+
+def test_whole_path_graph_capture(vq):
+    """The calls only enqueue work: the whole path captures into a CUDA graph and replays
+    to the same results."""
+    q = synth.query_map(128, 96, 32, M=10, n_sp=50, seed=11)
+    T, _ = synth.crop_template(q, 20, 16, seed=12)
+    k, bank = 12, vq.Bank(synth.grid_bank(20, 16, 3))
+    X, Td = _dev(q.X), _dev(T)
+    ws_fit = vq.Workspace(vq.vqnnf_workspace_bytes(0, 20, 16, 32, 12))
+    ws_a = vq.Workspace(vq.vqnnf_workspace_bytes(1, 128, 96, 32, 12))
+    ws_s = vq.Workspace(vq.vqnnf_workspace_bytes(3, 128, 96, 0, 12, 20, 16, bank.F))
+    C = torch.empty((k, 32), device="cuda")
+    tl = torch.empty((20, 16), dtype=torch.uint8, device="cuda")
+    ql = torch.empty((128, 96), dtype=torch.uint8, device="cuda")
+    tc = torch.empty((bank.F, k), dtype=torch.int32, device="cuda")
+    heat = torch.empty((109, 81), device="cuda")
+    am = torch.empty(2, dtype=torch.int32, device="cuda")
+
+    def step(stream=None):
+        vq.vqnnf_fit_codebook(Td, k, 5, 1, C=C, ws=ws_fit, stream=stream)
+        vq.vqnnf_assign(Td, C, labels=tl, ws=ws_a, stream=stream)
+        vq.vqnnf_assign(X, C, labels=ql, ws=ws_a, stream=stream)
+        vq.vqnnf_filter_responses(tl, k, bank, counts=tc, stream=stream)
+        vq.vqnnf_score(ql, k, 20, 16, bank, tc, heatmap=heat, argmax_yx=am, ws=ws_s, stream=stream)
+
+    step()
+    torch.cuda.synchronize()
+    want = (C.clone(), ql.clone(), heat.clone(), am.clone())
+    for t in (C, ql, heat, am):
+        t.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            step(stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip((C, ql, heat, am), want):
+        assert torch.equal(a, b)
