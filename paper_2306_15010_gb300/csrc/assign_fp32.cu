@@ -191,10 +191,11 @@ __global__ void __launch_bounds__(NT) assign_fp32_kernel(const float *__restrict
     const long long p0 = (long long)blockIdx.x * BM;
     for (int j = tid; j < kp; j += NT) {
         const bool ok = j < k;
-        ca[j] = ok ? p.a[j] : 0.f;
-        cv[j] = ok ? p.v[j] : 0.f;
-        cb[j] = ok ? p.b[j] : 0.f;
-        cn[j] = ok ? p.nrm[j] : 0.f;
+        const int jc = ok ? j : k - 1;
+        ca[j] = ok ? p.a[jc] : 0.f;
+        cv[j] = ok ? p.v[jc] : 0.f;
+        cb[j] = ok ? p.b[jc] : 0.f;
+        cn[j] = ok ? p.nrm[jc] : 0.f;
     }
     // loader mapping: row lp (pixel or centroid), dims lh*8 .. lh*8+7 of the k-step
     const int lp = tid >> 1, lh = tid & 1;
@@ -214,19 +215,23 @@ __global__ void __launch_bounds__(NT) assign_fp32_kernel(const float *__restrict
             for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
 
         float ra[8], rb[8];
+        // Every load address is clamped into its buffer and out-of-range values are
+        // zeroed afterwards: no address past a buffer is ever formed, even for loads the
+        // compiler may issue ahead of their guard.
         auto gload = [&](int d0) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int d = d0 + lh * 8 + q * 4;
-                float4 xa = make_float4(0, 0, 0, 0), cbv = make_float4(0, 0, 0, 0);
-                if (d < D) {
-                    if (prow_ok) {
-                        xa = __ldg(reinterpret_cast<const float4 *>(xrow + d));
-                        const float4 mm = __ldg(reinterpret_cast<const float4 *>(p.mean + d));
-                        xa.x -= mm.x; xa.y -= mm.y; xa.z -= mm.z; xa.w -= mm.w;
-                    }
-                    if (crow_ok) cbv = __ldg(reinterpret_cast<const float4 *>(crw + d));
-                }
+                const bool din = d < D;
+                const int dc = din ? d : D - 4;
+                float4 xa = __ldg(reinterpret_cast<const float4 *>(xrow + dc));
+                const float4 mm = __ldg(reinterpret_cast<const float4 *>(p.mean + dc));
+                float4 cbv = __ldg(reinterpret_cast<const float4 *>(crw + dc));
+                const bool xok = din && prow_ok, cok = din && crow_ok;
+                xa.x = xok ? xa.x - mm.x : 0.f; xa.y = xok ? xa.y - mm.y : 0.f;
+                xa.z = xok ? xa.z - mm.z : 0.f; xa.w = xok ? xa.w - mm.w : 0.f;
+                cbv.x = cok ? cbv.x : 0.f; cbv.y = cok ? cbv.y : 0.f;
+                cbv.z = cok ? cbv.z : 0.f; cbv.w = cok ? cbv.w : 0.f;
                 ra[q * 4 + 0] = xa.x; ra[q * 4 + 1] = xa.y; ra[q * 4 + 2] = xa.z; ra[q * 4 + 3] = xa.w;
                 rb[q * 4 + 0] = cbv.x; rb[q * 4 + 1] = cbv.y; rb[q * 4 + 2] = cbv.z; rb[q * 4 + 3] = cbv.w;
             }
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(NT) assign_fp32_kernel(const float *__restrict
         int buf = 0;
         for (int d0 = 0; d0 < D; d0 += BK) {
             const bool more = d0 + BK < D;
-            if (more) gload(d0 + BK);
+            if (more) gload(d0 + BK);   // gload clamps its addresses
             const float *a = As + buf * BK * BM;
             const float *b = Bs + buf * BK * BN;
 #pragma unroll
@@ -342,18 +347,20 @@ __device__ __forceinline__ void df_warp_sum(float &hi, float &lo)
 
 __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ X, int D,
                                                       const float *__restrict__ C, int k,
-                                                      uint8_t *__restrict__ labels, FlagList fl)
+                                                      uint8_t *__restrict__ labels, FlagList fl,
+                                                      unsigned cap)
 {
     const int lane = threadIdx.x & 31;
     const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-    const unsigned n_entries = *fl.count;
+    const unsigned n_entries = min(*fl.count, cap);     // the list holds at most cap entries
     const float u = (float)kU32;
     const float rho = ((float)((D + 31) / 32) + 8.0f) * u * 1.01f + 4.0f * u;
     unsigned long long my_cand = 0, my_deep = 0;
     for (unsigned e = wid; e < n_entries; e += nw) {
         const unsigned pix = fl.pix[e];
-        unsigned mw = lane < kMaskWords ? fl.mask[(size_t)e * kMaskWords + lane] : 0u;
+        const unsigned mw0 = fl.mask[(size_t)e * kMaskWords + (lane & (kMaskWords - 1))];
+        const unsigned mw = lane < kMaskWords ? mw0 : 0u;
         const float *x = X + (size_t)pix * D;
         float r1 = FLT_MAX, r2 = FLT_MAX;
         int a = 0, nc = 0;
@@ -364,9 +371,11 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
                 bits &= bits - 1;
                 const float *c = C + (size_t)j * D;
                 float acc = 0.f;
-                for (int i = lane; i < D; i += 32) {
+                for (int i0 = 0; i0 < D; i0 += 32) {
+                    const bool ok = i0 + lane < D;
+                    const int i = ok ? i0 + lane : D - 1;
                     const float d = x[i] - c[i];
-                    acc = fmaf(d, d, acc);
+                    acc = ok ? fmaf(d, d, acc) : acc;
                 }
                 const float r = warp_sum(acc);
                 ++nc;
@@ -385,8 +394,10 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
                     bits &= bits - 1;
                     const float *c = C + (size_t)j * D;
                     float S = 0.f, E = 0.f;
-                    for (int i = lane; i < D; i += 32) {
-                        const float xi = x[i], ci = c[i];
+                    for (int i0 = 0; i0 < D; i0 += 32) {
+                        const bool ok = i0 + lane < D;
+                        const int i = ok ? i0 + lane : D - 1;
+                        const float xi = ok ? x[i] : 0.f, ci = ok ? c[i] : 0.f;
                         float h, l;
                         two_sum(xi, -ci, h, l);          // xi - ci = h + l exactly
                         const float p2 = h * h;
@@ -451,11 +462,10 @@ cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k, const 
 cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
                            uint8_t *labels, FlagList fl, cudaStream_t s)
 {
-    (void)n;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    rescore_kernel<<<sms * 8, 256, 0, s>>>(X, D, C, k, labels, fl);
+    rescore_kernel<<<sms * 8, 256, 0, s>>>(X, D, C, k, labels, fl, (unsigned)n);
     return cudaGetLastError();
 }
 

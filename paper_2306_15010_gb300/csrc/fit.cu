@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
         __syncthreads();
         const int p = c0 + t;
         const bool ok = p < l;
-        const int lb = ok ? (int)lab[p] : -1 - lane;     // unique dummies never match
+        const int l0 = (int)lab[ok ? p : l - 1];          // clamped address
+        const int lb = ok ? l0 : -1 - lane;               // unique dummies never match
         const unsigned same = __match_any_sync(0xffffffffu, lb);
         const int rank = __popc(same & ((1u << lane) - 1u));
         if (ok && rank == 0) wc[w][lb] = __popc(same);

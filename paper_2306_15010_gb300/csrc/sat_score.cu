@@ -75,11 +75,12 @@ __global__ void __launch_bounds__(128) sat_sweep_kernel(const uint8_t *__restric
         if (j < k && xin) S[(size_t)j * P + x] = 0;
     }
     for (int y = 0; y < H; ++y) {
-        // labels at columns x - 1 ... the row prefix of column x counts labels left of x
         const int xl = s * SW + lane;      // label column tested by this lane
-        const int lb = (xl < W) ? (int)lab[(size_t)y * W + xl] : -1;
-        const int cj = (lane < CGW && cg * CGW + lane < k)
-                           ? carry[((size_t)y * nS + s) * k + cg * CGW + lane] : 0;
+        const int l0 = (int)lab[(size_t)y * W + min(xl, W - 1)];   // clamped address
+        const int lb = (xl < W) ? l0 : -1;
+        const int jc = min(cg * CGW + (lane & (CGW - 1)), k - 1);
+        const int c0 = carry[((size_t)y * nS + s) * k + jc];
+        const int cj = (lane < CGW && cg * CGW + lane < k) ? c0 : 0;
 #pragma unroll
         for (int q = 0; q < CGW; ++q) {
             const int j = cg * CGW + q;
