@@ -37,10 +37,17 @@ def _labels_ok(gpu, ref, d1, d2):
     return int(bad.sum()), int(band.sum())
 
 
-def _codebook_case(H, W, D, k, seed, th=None, tw=None, iters=3):
+def _codebook_case(H, W, D, k, seed, iters=3):
+    """Query features and a codebook fitted by the oracle on a crop of the query (so that
+    near-duplicate centroids and near-ties occur as in real use).  A query with fewer
+    pixels than k gets a seeded random codebook instead."""
     q = synth.query_map(H, W, D, M=max(4, k // 2 + 3), n_sp=max(8, H * W // 200), seed=seed)
-    th = th or max(4, H // 4)
-    tw = tw or max(4, W // 4)
+    if H * W < k:
+        r = np.random.default_rng(seed)
+        return q, None, r.random((k, D)).astype(np.float32)
+    th, tw = min(H, max(4, H // 4)), min(W, max(4, W // 4))
+    while th * tw < k:
+        th, tw = min(H, th + 1), min(W, tw + 1)
     T, _ = synth.crop_template(q, th, tw, seed=seed + 1000)
     C = oracle.fit_codebook(T.numpy(), k, iters, seed)
     return q, T, C
