@@ -7,6 +7,7 @@ stream) into the C ABI of ``include/vqnnf.h``.
 """
 from .api import (  # noqa: F401
     vqnnf_assign,
+    vqnnf_assign_noalloc,
     vqnnf_fit_codebook,
     vqnnf_filter_responses,
     vqnnf_last_device_error,

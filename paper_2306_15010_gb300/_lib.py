@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libvqnnf.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 PREC = {"fp32": 0, "bf16": 1}
 OP_FIT, OP_ASSIGN, OP_FILTER_RESPONSES, OP_SCORE = range(4)
+NOALLOC_SCRATCH_BYTES = 16 << 20      # VQNNF_NOALLOC_SCRATCH_BYTES
 
 # every entry point the header declares, with its ctypes signature
 _vp = ctypes.c_void_p
@@ -22,6 +23,7 @@ SIGNATURES = {
     "vqnnf_workspace_bytes": (_sz, [_i, _i, _i, _i, _i, _i, _i, _i, _i]),
     "vqnnf_fit_codebook": (_i, [_vp, _i, _i, _i, _i, _i, ctypes.c_uint64, _i, _vp, _vp, _sz, _vp]),
     "vqnnf_assign": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "vqnnf_assign_noalloc": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _vp, _vp]),
     "vqnnf_filter_responses": (_i, [_vp, _i, _i, _i, _vp, _i, _vp, _vp, _sz, _vp]),
     "vqnnf_score": (_i, [_vp, _i, _i, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "vqnnf_status_str": (ctypes.c_char_p, [_i]),

@@ -174,6 +174,31 @@ def vqnnf_assign(X: torch.Tensor, C: torch.Tensor, prec="fp32", *,
     return labels
 
 
+def vqnnf_assign_noalloc(X: torch.Tensor, C: torch.Tensor, prec="fp32", *,
+                         labels: torch.Tensor, stats: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """vqnnf_assign without a workspace, for callers that cannot allocate device memory
+    (e.g. while a CUDA graph is being captured): the library's fixed 16 MiB scratch area is
+    used instead.  ``labels`` must be passed in; nothing is allocated here either.  Calls
+    that overlap on the GPU share that area and race; requests that need more scratch than
+    it holds raise (status VQNNF_ENOMEM)."""
+    _need(X, "X", torch.float32)
+    _need(C, "C", torch.float32)
+    _need(labels, "labels", torch.uint8)
+    if X.dim() == 2:
+        H, W, D = 1, X.shape[0], X.shape[1]
+    else:
+        H, W, D = X.shape
+    sp = 0
+    if stats is not None:
+        _need(stats, "stats", torch.int64)
+        sp = stats.data_ptr()
+    st = _lib.load().vqnnf_assign_noalloc(X.data_ptr(), H, W, D, C.data_ptr(), C.shape[0],
+                                          _prec(prec), labels.data_ptr(), sp, _stream(stream))
+    _lib.check("vqnnf_assign_noalloc", st)
+    return labels
+
+
 def vqnnf_filter_responses(labels: torch.Tensor, k: int, bank, *,
                            counts: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """F x k int32 template representation vectors of the template NNF."""

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "score_spec.cuh"
@@ -398,3 +399,57 @@ vqnnf_status vqnnf_last_device_error(void *stream)
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------------
+// Allocation-free assignment: the scratch workspace is a fixed device array compiled into
+// the library.  Host code may not pass the array's name to a kernel (on the host it is only
+// a stand-in symbol); its device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, and cached.
+// ----------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocBytes = VQNNF_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices];
+
+// Device address of the scratch area on the current device (set up on first use).
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" vqnnf_status vqnnf_assign_noalloc(const float *X, int H, int W, int D, const float *C,
+                                             int k, vqnnf_prec prec, uint8_t *labels,
+                                             vqnnf_assign_stats *stats, void *stream)
+{
+    if (!X || !C || !labels || H < 1 || W < 1 || D < 1 || k < 1) return VQNNF_EINVAL;
+    if (!aligned(X, 16) || !aligned(C, 16)) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    const long long n = (long long)H * W;
+    if (n >= (1ll << 32)) return VQNNF_EUNSUPPORTED;
+    const size_t need = vqnnf_workspace_bytes(VQNNF_OP_ASSIGN, H, W, D, k, 0, 0, 0, prec);
+    if (need == 0 || need > kNoallocBytes) return VQNNF_ENOMEM;
+    void *base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return VQNNF_ECUDA;
+    WsCursor c{static_cast<char *>(base), 0};
+    AssignWs w = carve_assign(c, n, D, k);
+    return run_assign(X, n, D, C, k, prec, labels, stats, w, as_stream(stream));
+}
