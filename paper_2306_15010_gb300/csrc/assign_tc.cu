@@ -1,16 +1,542 @@
-// Tensor-core (tcgen05) BF16 distance contraction -- placeholder until the kernel lands.
+// Nearest-neighbour field (Algorithm 1) on the tcgen05 tensor cores.
+//
+// The distance contraction s_j = ||c_j - m||^2 - 2 (x - m).(c_j - m) runs as a BF16 x BF16
+// UMMA with FP32 accumulation in tensor memory; each centroid enters as two BF16 planes
+// (hi = bf16(c - m), lo = bf16(c - m - hi)) accumulated into the same result, so only the
+// pixel side is rounded to 8 significant bits.  The epilogue applies the same proven
+// interval test as the FP32 path (assign_fp32.cu) and flags ambiguous pixels for the
+// shared re-scoring stage, so labels stay exact.
+//
+// One persistent CTA per SM, 128-pixel tiles, warp-specialised:
+//   warp 0      TMA producer: FP32 feature boxes (128 rows x 32 floats, 128B swizzle) and
+//               the two BF16 centroid planes (k rows x 64 elements, 128B swizzle)
+//   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warps 2-5   converters: thread r owns pixel row r; FP32 -> centred BF16 written in the
+//               UMMA K-major 128B-swizzled layout; accumulates ||x'_bf16||^2, ||x' - x'_bf16||^2
+//   warps 6-9   epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
+//               flag push; the TMEM accumulator is double-buffered
+// Every mbarrier wait is bounded: on timeout the CTA records VQNNF_ETIMEOUT in the device
+// error word, all roles leave their loops, in-flight copies and MMAs are drained (bounded)
+// and the tensor memory is released before the kernel returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cfloat>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace vqnnf {
-
 namespace {
+
 __device__ int g_tc_error = 0;
+
+constexpr int TM = 128;            // pixels per tile (UMMA M)
+constexpr int KC = 64;             // K elements per chunk (128 bytes of BF16)
+constexpr int SF = 2;              // FP32 staging stages
+constexpr int SA = 2;              // BF16 A-operand stages
+constexpr int NT = 320;            // 10 warps
+constexpr int F32_STAGE = TM * KC * 4;     // 32 KB (two 16 KB boxes)
+constexpr int A_STAGE = TM * KC * 2;       // 16 KB
+constexpr double kU = 5.9604644775390625e-08;
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+struct TcArgs {
+    long long n;
+    int D, k, npad, nkc, sb;
+    long long ntiles;
+    CodebookPrep p;
+    uint8_t *labels;
+    FlagList fl;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}" ::"r"(
+                     smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when this CTA gave up (timeout here or abort raised elsewhere).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort)
+{
+    if (mbar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(b, parity)) return true;
+        if ((i & 63) == 0) {
+            if (*abort) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                *abort = 1;
+                atomicExch(&g_tc_error, (int)VQNNF_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-cudaError_t launch_assign_bf16(const float *, long long, int, int, const CodebookPrep &,
-                               uint8_t *, FlagList, cudaStream_t)
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1 KB apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
-    return cudaErrorNotSupported;
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: BF16 x BF16 -> F32, both K-major, M = 128, N = npad.
+__host__ __device__ constexpr uint32_t bf16_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b, float &ra, float &rb)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a -> low half
+    ra = __low2float(h);
+    rb = __high2float(h);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmBhi,
+                                                          const __grid_constant__ CUtensorMap tmBlo,
+                                                          TcArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int npad = g.npad, D = g.D, k = g.k, nkc = g.nkc, SB = g.sb;
+    const int B_PLANE = npad * 128;
+    uint8_t *f32s = base;                                  // SF x 32 KB
+    uint8_t *as = f32s + SF * F32_STAGE;                   // SA x 16 KB
+    uint8_t *bs = as + SA * A_STAGE;                       // SB x (hi, lo)
+    float *ca = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
+    float *cv = ca + npad;
+    float *cb = cv + npad;
+    float *cn = cb + npad;
+    float *mean = cn + npad;                               // roundup(D, 64)
+    float *norms = mean + nkc * KC;                        // [2 buf][2][128]
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 2 * TM);   // [128][8]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(maskbuf + TM * kMaskWords);
+    uint64_t *full_f = bar, *empty_f = bar + SF, *a_full = bar + 2 * SF, *a_empty = bar + 2 * SF + SA;
+    uint64_t *full_b = bar + 2 * SF + 2 * SA, *empty_b = full_b + 2;
+    uint64_t *acc_full = empty_b + 2, *acc_empty = acc_full + 2, *nrm_full = acc_empty + 2,
+             *nrm_empty = nrm_full + 2, *drain = nrm_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem_cols = (2 * npad <= 32) ? 32 : (2 * npad <= 64) ? 64 : (2 * npad <= 128) ? 128
+                                                    : (2 * npad <= 256) ? 256 : 512;
+
+    for (int j = tid; j < npad; j += NT) {
+        const bool ok = j < k;
+        const int jc = ok ? j : k - 1;
+        ca[j] = ok ? g.p.a[jc] : 0.f;
+        cv[j] = ok ? g.p.v[jc] : 0.f;
+        cb[j] = ok ? g.p.b[jc] : 0.f;
+        cn[j] = ok ? g.p.nrm[jc] : 0.f;
+    }
+    for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
+    if (tid == 0) {
+        for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], TM); }
+        for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], TM); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full_b[s], 1); mbar_init(&empty_b[s], 1);
+            mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], TM);
+            mbar_init(&nrm_full[s], TM); mbar_init(&nrm_empty[s], TM);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            uint32_t it = 0, itb = 0;
+            bool ok = true;
+            long long last_f[SF], last_b[2];
+            for (int s = 0; s < SF; ++s) last_f[s] = -1;
+            for (int s = 0; s < 2; ++s) last_b[s] = -1;
+            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
+                for (int kc = 0; kc < nkc; ++kc, ++it, ++itb) {
+                    const int s = it % SF;
+                    if (!(ok = mbar_wait(&empty_f[s], ((it / SF) & 1) ^ 1, abort))) break;
+                    mbar_expect_tx(&full_f[s], F32_STAGE);
+                    uint8_t *dst = f32s + s * F32_STAGE;
+                    tma_load_2d(dst, &tmA, kc * KC, (int)(tile * TM), &full_f[s]);
+                    tma_load_2d(dst + F32_STAGE / 2, &tmA, kc * KC + 32, (int)(tile * TM), &full_f[s]);
+                    last_f[s] = it;
+                    const int sb = itb % SB;
+                    if (!(ok = mbar_wait(&empty_b[sb], ((itb / SB) & 1) ^ 1, abort))) break;
+                    mbar_expect_tx(&full_b[sb], 2 * B_PLANE);
+                    uint8_t *bd = bs + sb * 2 * B_PLANE;
+                    tma_load_2d(bd, &tmBhi, kc * KC, 0, &full_b[sb]);
+                    tma_load_2d(bd + B_PLANE, &tmBlo, kc * KC, 0, &full_b[sb]);
+                    last_b[sb] = itb;
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for every copy this thread issued to land
+                volatile int no_abort = 0;
+                for (int s = 0; s < SF; ++s)
+                    if (last_f[s] >= 0) mbar_wait(&full_f[s], (uint32_t)((last_f[s] / SF) & 1), &no_abort);
+                for (int s = 0; s < SB; ++s)
+                    if (last_b[s] >= 0) mbar_wait(&full_b[s], (uint32_t)((last_b[s] / SB) & 1), &no_abort);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = bf16_idesc(TM, npad);
+            uint32_t it = 0, itb = 0, tl = 0;
+            bool ok = true;
+            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+                const uint32_t buf = tl & 1;
+                if (!(ok = mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort))) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + buf * npad;
+                for (int kc = 0; kc < nkc; ++kc, ++it, ++itb) {
+                    const int sa = it % SA, sb = itb % SB;
+                    if (!(ok = mbar_wait(&a_full[sa], (it / SA) & 1, abort))) break;
+                    if (!(ok = mbar_wait(&full_b[sb], (itb / SB) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(as + sa * A_STAGE);
+                    const uint32_t b0 = smem_u32(bs + sb * 2 * B_PLANE);
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint64_t ad = sw128_desc(a0 + ks * 32);
+                        tc_mma(d_tmem, ad, sw128_desc(b0 + ks * 32), idesc, (kc | ks) != 0);
+                        tc_mma(d_tmem, ad, sw128_desc(b0 + B_PLANE + ks * 32), idesc, 1u);
+                    }
+                    tc_commit(&a_empty[sa]);
+                    tc_commit(&empty_b[sb]);
+                }
+                if (ok) tc_commit(&acc_full[buf]);
+            }
+            // drain every MMA issued before the tensor memory is released
+            tc_commit(drain);
+            volatile int no_abort = 0;
+            mbar_wait(drain, 0, &no_abort);
+        }
+    } else if (warp < 6) {
+        // ---------------------------------------------------------- converters
+        const int r = tid - 64;                  // pixel row of the tile
+        const int sw = r & 7;
+        uint32_t it = 0, tl = 0;
+        bool ok = true;
+        for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+            const uint32_t buf = tl & 1;
+            float xh2 = 0.f, dl2 = 0.f;
+            for (int kc = 0; kc < nkc; ++kc, ++it) {
+                const int s = it % SF, sa = it % SA;
+                ok = mbar_wait(&full_f[s], (it / SF) & 1, abort);
+                ok = __all_sync(0xffffffffu, ok && mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort));
+                if (!ok) break;
+                const uint8_t *frow = f32s + s * F32_STAGE + r * 128;
+                uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint8_t *box = frow + (c >> 2) * (F32_STAGE / 2);
+                    const int c0 = (c & 3) * 2;
+                    const float4 v0 = *reinterpret_cast<const float4 *>(box + ((c0 ^ sw) << 4));
+                    const float4 v1 = *reinterpret_cast<const float4 *>(box + (((c0 + 1) ^ sw) << 4));
+                    const int d0 = kc * KC + c * 8;
+                    const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int da = d0 + 2 * q;
+                        const float xa = (da < D) ? xs[2 * q] - mean[da] : 0.f;
+                        const float xb = (da + 1 < D) ? xs[2 * q + 1] - mean[da + 1] : 0.f;
+                        float ra, rb;
+                        w[q] = pack_bf16(xa, xb, ra, rb);
+                        xh2 = fmaf(ra, ra, fmaf(rb, rb, xh2));
+                        const float ea = xa - ra, eb = xb - rb;
+                        dl2 = fmaf(ea, ea, fmaf(eb, eb, dl2));
+                    }
+                    *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                fence_proxy_async();
+                mbar_arrive(&a_full[sa]);
+                mbar_arrive(&empty_f[s]);
+            }
+            if (!ok) break;
+            ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[buf], ((tl >> 1) & 1) ^ 1, abort));
+            if (!ok) break;
+            norms[(buf * 2 + 0) * TM + r] = xh2;
+            norms[(buf * 2 + 1) * TM + r] = dl2;
+            mbar_arrive(&nrm_full[buf]);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int grp = warp & 3;                 // TMEM lane group this warp may read
+        const int r = grp * 32 + lane;
+        const float u = (float)kU;
+        const float infl = 1.0f + 0.00390625f;
+        uint32_t tl = 0;
+        bool ok = true;
+        for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+            const uint32_t buf = tl & 1, ph = (tl >> 1) & 1;
+            ok = mbar_wait(&acc_full[buf], ph, abort);
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort));
+            if (!ok) break;
+            tc_fence_after();
+            const float inf = 1.0f + (float)(D + 8) * u;
+            const float X = sqrtf(norms[(buf * 2 + 0) * TM + r]) * inf;
+            const float Dl = sqrtf(norms[(buf * 2 + 1) * TM + r]) * inf;
+            mbar_arrive(&nrm_empty[buf]);
+            const float Y = Dl + u * (X + Dl) * (1.0f + 4.0f * u);
+            const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
+            float U = FLT_MAX, smin = FLT_MAX;
+            int amin = 0;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    if (col < k) {
+                        const float s = fmaf(-2.0f, v[j], cn[col]);
+                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
+                        U = fminf(U, s + B);
+                        if (s < smin) { smin = s; amin = col; }
+                    }
+                }
+            }
+            int cnt = 0, last = amin;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + c0, v);
+                uint32_t word = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    if (col < k) {
+                        const float s = fmaf(-2.0f, v[j], cn[col]);
+                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
+                        if (s - B <= U) {
+                            ++cnt;
+                            last = col;
+                            word |= 1u << j;
+                        }
+                    }
+                }
+                maskbuf[r * kMaskWords + (c0 >> 5)] = word;
+            }
+            for (int w = (npad + 31) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);
+            const long long pix = tile * TM + r;
+            const bool valid = pix < g.n;
+            const int lab = cnt == 1 ? last : amin;
+            if (valid) g.labels[pix] = (uint8_t)lab;
+            const bool flagged = valid && cnt > 1;
+            const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+            if (ballot) {
+                const int leader = __ffs(ballot) - 1;
+                unsigned basei = 0;
+                if (lane == leader) basei = atomicAdd(g.fl.count, (unsigned)__popc(ballot));
+                basei = __shfl_sync(0xffffffffu, basei, leader);
+                if (flagged) {
+                    const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
+                    if (slot < (unsigned long long)g.n) {
+                        g.fl.pix[slot] = (unsigned)pix;
+#pragma unroll
+                        for (int w = 0; w < kMaskWords; ++w)
+                            g.fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                    }
+                }
+            }
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t get_encode()
+{
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode ? cudaSuccess : cudaErrorNotSupported;
+}
+
+cudaError_t make_map(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, uint64_t cols, uint64_t rows,
+                     uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows)
+{
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = g_encode(m, dt, 2, const_cast<void *>(ptr), dims, strides, box, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t tc_smem_bytes(int npad, int D, int sb)
+{
+    const int nkc = (D + KC - 1) / KC;
+    size_t b = 1024;                                       // alignment slack
+    b += (size_t)SF * F32_STAGE + (size_t)SA * A_STAGE + (size_t)sb * 2 * npad * 128;
+    b += sizeof(float) * (4 * (size_t)npad + (size_t)nkc * KC + 4 * TM);
+    b += sizeof(uint32_t) * TM * kMaskWords;
+    b += sizeof(uint64_t) * (2 * SF + 2 * SA + 12 + 1) + 16;   // 21 barriers, TMEM slot, abort flag
+    return b;
+}
+
+}  // namespace
+
+cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const CodebookPrep &p,
+                               uint8_t *labels, FlagList fl, cudaStream_t s)
+{
+    if (D % 16 != 0 || k < 1 || k > kMaxK) return cudaErrorNotSupported;
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int npad = (k + 31) / 32 * 32;      // UMMA N (multiple of 16) and whole 32-column TMEM loads
+    int sb = 2;
+    size_t smem = tc_smem_bytes(npad, D, sb);
+    if (smem > (size_t)optin) {
+        sb = 1;
+        smem = tc_smem_bytes(npad, D, sb);
+    }
+    if (smem > (size_t)optin) return cudaErrorNotSupported;
+    CUtensorMap tmA, tmBhi, tmBlo;
+    if ((e = make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)D, (uint64_t)n, (uint64_t)D * 4, 32,
+                      TM)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&tmBhi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.chi, (uint64_t)D, (uint64_t)k,
+                      (uint64_t)D * 2, KC, (uint32_t)npad)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&tmBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.clo, (uint64_t)D, (uint64_t)k,
+                      (uint64_t)D * 2, KC, (uint32_t)npad)) != cudaSuccess)
+        return e;
+    TcArgs a;
+    a.n = n;
+    a.D = D;
+    a.k = k;
+    a.npad = npad;
+    a.nkc = (D + KC - 1) / KC;
+    a.sb = sb;
+    a.ntiles = (n + TM - 1) / TM;
+    a.p = p;
+    a.labels = labels;
+    a.fl = fl;
+    e = cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = a.ntiles < sms ? a.ntiles : sms;
+    assign_tc_kernel<<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+    return cudaGetLastError();
 }
 
 cudaError_t read_and_clear_tc_error(int *out)

@@ -53,7 +53,7 @@ def _codebook_case(H, W, D, k, seed, iters=3):
     return q, T, C
 
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "bf16"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
