@@ -211,6 +211,25 @@ def run_gpu(args, rank, world):
     am = pipe.am.cpu().tolist()
     clocks = clk.summary()
 
+    # the other precision on the same inputs, same GPU, for the BF16-vs-FP32 comparison
+    other = "fp32" if args.prec == "bf16" else "bf16"
+    pipe2 = Pipeline(vq, X, T, cfg, bank, other, s)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            pipe2.step()
+    torch.cuda.synchronize()
+    st2 = torch.cuda.Event(enable_timing=True)
+    sp2 = torch.cuda.Event(enable_timing=True)
+    st2.record(s)
+    with torch.cuda.stream(s):
+        for i in range(K):
+            pipe2.step()
+    sp2.record(s)
+    torch.cuda.synchronize()
+    ms2 = st2.elapsed_time(sp2) / K
+    same_labels = bool(torch.equal(pipe.ql, pipe2.ql))
+    del pipe2
+
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = run_e2e(vq, pipe, X, T, cfg, args, s, dev)
 
@@ -234,6 +253,10 @@ def run_gpu(args, rank, world):
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "clocks": clocks, "e2e": e2e,
+        f"{other}_path": {"value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+                          "ms_per_step": round(ms2, 4),
+                          "speedup_bf16_over_fp32": round((ms2 / ms) if other == "fp32" else (ms / ms2), 3),
+                          "labels_identical": same_labels},
         "gpu_launches": kernels_per_step(cfg, args.prec) * K,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -250,7 +273,8 @@ def roofline(cfg, prec, assign_ms, peaks, src):
         peak = float(peaks["hbm_gbs"])
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "traffic": None,
-                "kernel": "query assign (contraction + re-scoring)", "peak_source": src}
+                "kernel": "query assign call: codebook prep + tcgen05 contraction + re-scoring",
+                "algorithmic_bytes_per_px": D * 4 + 1, "peak_source": src}
     # FP32 SIMT: bound by the FP32 FMA pipes, 152 SMs x 128 lanes x 2 flop x max SM clock
     flops = 2.0 * L * D * k
     ach = flops / (assign_ms * 1e-3) / 1e12
@@ -361,7 +385,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", choices=["bf16", "fp32"], default="fp32")
+    ap.add_argument("--prec", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

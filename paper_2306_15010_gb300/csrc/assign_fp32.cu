@@ -100,10 +100,12 @@ __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restr
             a = 2.0 * gD * ncc + 2.0 * (1.0 + 2.0 * u) * nd32;
             v = 2.0 * (ncc > nc ? ncc : nc);
         } else {
-            // tensor-core accumulation order and rounding are not documented: take four
-            // times the sequential FP32 bound
+            // Three BF16 products x_hi.hi + x_hi.lo + x_lo.hi.  Tensor-core accumulation
+            // order and rounding are not documented: take four times the sequential FP32
+            // bound.  The x_lo terms (||x_lo|| <= 2^-8 ||x_hi||) are folded into a_j:
+            //   |err| <= X [gacc (|hi| + |lo|) + |d|] + X_lo [gacc |hi| + |lo| + |d|] + ...
             const double gacc = (double)D * 4.0 * u;
-            a = 2.0 * gacc * (nhi + nlo) + 2.0 * nd16;
+            a = 2.0 * (gacc * (nhi + nlo) + nd16) + 2.0 * 0.00390625 * (gacc * nhi + nlo + nd16);
             v = 2.0 * nc;
         }
         p.nrm[j] = n32;
@@ -144,7 +146,7 @@ __device__ __forceinline__ int decide_pixel(const float *srow, int stride, int k
                                             unsigned *mask, int *ncand)
 {
     const float u = (float)kU32;
-    const float Y = Dl + u * (X + Dl) * (1.0f + 4.0f * u);
+    const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
     const float infl = 1.0f + 0.00390625f;
     float U = FLT_MAX, smin = FLT_MAX;
     int amin = 0;

@@ -1,9 +1,10 @@
 // Nearest-neighbour field (Algorithm 1) on the tcgen05 tensor cores.
 //
-// The distance contraction s_j = ||c_j - m||^2 - 2 (x - m).(c_j - m) runs as a BF16 x BF16
-// UMMA with FP32 accumulation in tensor memory; each centroid enters as two BF16 planes
-// (hi = bf16(c - m), lo = bf16(c - m - hi)) accumulated into the same result, so only the
-// pixel side is rounded to 8 significant bits.  The epilogue applies the same proven
+// The distance contraction s_j = ||c_j - m||^2 - 2 (x - m).(c_j - m) runs as BF16 x BF16
+// UMMAs with FP32 accumulation in tensor memory.  Both sides are split into two BF16 planes
+// (v = hi + lo + rest, hi = bf16(v), lo = bf16(v - hi)) and three products are accumulated
+// into the same result: x_hi.c_hi + x_hi.c_lo + x_lo.c_hi, so the rounding left in the
+// contraction is about 2^-16 relative instead of 2^-8.  The epilogue applies the same proven
 // interval test as the FP32 path (assign_fp32.cu) and flags ambiguous pixels for the
 // shared re-scoring stage, so labels stay exact.
 //
@@ -11,8 +12,9 @@
 //   warp 0      TMA producer: FP32 feature boxes (128 rows x 32 floats, 128B swizzle) and
 //               the two BF16 centroid planes (k rows x 64 elements, 128B swizzle)
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warps 2-5   converters: thread r owns pixel row r; FP32 -> centred BF16 written in the
-//               UMMA K-major 128B-swizzled layout; accumulates ||x'_bf16||^2, ||x' - x'_bf16||^2
+//   warps 2-5   converters: thread r owns pixel row r; FP32 -> centred BF16 hi and lo planes
+//               written in the UMMA K-major 128B-swizzled layout; accumulates ||x_hi||^2 and the
+//               squared norm of what the two planes leave out
 //   warps 6-9   epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
 //               flag push; the TMEM accumulator is double-buffered
 // Every mbarrier wait is bounded: on timeout the CTA records VQNNF_ETIMEOUT in the device
@@ -38,7 +40,8 @@ constexpr int SF = 2;              // FP32 staging stages
 constexpr int SA = 2;              // BF16 A-operand stages
 constexpr int NT = 320;            // 10 warps
 constexpr int F32_STAGE = TM * KC * 4;     // 32 KB (two 16 KB boxes)
-constexpr int A_STAGE = TM * KC * 2;       // 16 KB
+constexpr int A_TILE = TM * KC * 2;        // 16 KB: one BF16 plane of the pixel tile
+constexpr int A_STAGE = 2 * A_TILE;        // hi and lo planes
 constexpr double kU = 5.9604644775390625e-08;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
@@ -294,9 +297,12 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     const uint32_t b0 = smem_u32(bs + sb * 2 * B_PLANE);
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint64_t ad = sw128_desc(a0 + ks * 32);
-                        tc_mma(d_tmem, ad, sw128_desc(b0 + ks * 32), idesc, (kc | ks) != 0);
-                        tc_mma(d_tmem, ad, sw128_desc(b0 + B_PLANE + ks * 32), idesc, 1u);
+                        const uint64_t ahi = sw128_desc(a0 + ks * 32);
+                        const uint64_t alo = sw128_desc(a0 + A_TILE + ks * 32);
+                        const uint64_t bhi = sw128_desc(b0 + ks * 32);
+                        tc_mma(d_tmem, ahi, bhi, idesc, (kc | ks) != 0);
+                        tc_mma(d_tmem, ahi, sw128_desc(b0 + B_PLANE + ks * 32), idesc, 1u);
+                        tc_mma(d_tmem, alo, bhi, idesc, 1u);
                     }
                     tc_commit(&a_empty[sa]);
                     tc_commit(&empty_b[sb]);
@@ -324,6 +330,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 if (!ok) break;
                 const uint8_t *frow = f32s + s * F32_STAGE + r * 128;
                 uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
+                uint8_t *lrow = arow + A_TILE;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const uint8_t *box = frow + (c >> 2) * (F32_STAGE / 2);
@@ -332,19 +339,22 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     const float4 v1 = *reinterpret_cast<const float4 *>(box + (((c0 + 1) ^ sw) << 4));
                     const int d0 = kc * KC + c * 8;
                     const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    uint32_t w[4];
+                    uint32_t w[4], wl[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int da = d0 + 2 * q;
                         const float xa = (da < D) ? xs[2 * q] - mean[da] : 0.f;
                         const float xb = (da + 1 < D) ? xs[2 * q + 1] - mean[da + 1] : 0.f;
-                        float ra, rb;
-                        w[q] = pack_bf16(xa, xb, ra, rb);
-                        xh2 = fmaf(ra, ra, fmaf(rb, rb, xh2));
-                        const float ea = xa - ra, eb = xb - rb;
+                        float ha, hb, la, lb;
+                        w[q] = pack_bf16(xa, xb, ha, hb);
+                        xh2 = fmaf(ha, ha, fmaf(hb, hb, xh2));
+                        const float ra = xa - ha, rb = xb - hb;       // exact
+                        wl[q] = pack_bf16(ra, rb, la, lb);
+                        const float ea = ra - la, eb = rb - lb;       // exact
                         dl2 = fmaf(ea, ea, fmaf(eb, eb, dl2));
                     }
                     *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+                    *reinterpret_cast<uint4 *>(lrow + ((c ^ sw) << 4)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
                 }
                 fence_proxy_async();
                 mbar_arrive(&a_full[sa]);
@@ -375,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             const float X = sqrtf(norms[(buf * 2 + 0) * TM + r]) * inf;
             const float Dl = sqrtf(norms[(buf * 2 + 1) * TM + r]) * inf;
             mbar_arrive(&nrm_empty[buf]);
-            const float Y = Dl + u * (X + Dl) * (1.0f + 4.0f * u);
+            const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
             const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
             float U = FLT_MAX, smin = FLT_MAX;
             int amin = 0;
