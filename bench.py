@@ -231,7 +231,7 @@ def run_gpu(args, rank, world):
     del pipe2
 
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
-    e2e = run_e2e(vq, pipe, X, T, cfg, args, s, dev)
+    e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev)
 
     if rank != 0:
         return None
@@ -388,6 +388,7 @@ def main():
     ap.add_argument("--prec", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

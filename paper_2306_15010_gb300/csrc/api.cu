@@ -60,16 +60,21 @@ FitWs carve_fit(WsCursor &c, long long l, int D, int k)
 }
 
 struct ScoreWs {
-    int *S;
+    void *S;          // integral image, uint16 (mod 2^16) or uint32, plus read slack
+    bool u16;
     int *carry;
+    int *bandsum;
     unsigned long long *amax;
 };
 
-ScoreWs carve_score(WsCursor &c, int H, int W, int k)
+ScoreWs carve_score(WsCursor &c, int H, int W, int k, int th, int tw)
 {
     ScoreWs w;
-    w.S = c.take<int>((size_t)(H + 1) * k * sat_pitch(W));
+    w.u16 = sat_is_u16(th, tw);
+    const size_t elems = (size_t)(H + 1) * k * sat_pitch(W) + sat_slack_elems(tw);
+    w.S = w.u16 ? (void *)c.take<uint16_t>(elems) : (void *)c.take<uint32_t>(elems);
     w.carry = c.take<int>((size_t)H * sat_strips(W) * k);
+    w.bandsum = c.take<int>((size_t)sat_bands(H) * k * sat_pitch(W));
     w.amax = c.take<unsigned long long>(1);
     return w;
 }
@@ -278,7 +283,7 @@ const char *vqnnf_status_str(vqnnf_status s)
 
 size_t vqnnf_workspace_bytes(int op, int H, int W, int D, int k, int th, int tw, int F, int prec)
 {
-    (void)th; (void)tw; (void)F; (void)prec;
+    (void)F; (void)prec;
     WsCursor c{nullptr, 0};
     switch (op) {
     case VQNNF_OP_FIT:
@@ -292,8 +297,8 @@ size_t vqnnf_workspace_bytes(int op, int H, int W, int D, int k, int th, int tw,
     case VQNNF_OP_FILTER_RESPONSES:
         return 256;
     case VQNNF_OP_SCORE:
-        if (H < 1 || W < 1 || k < 1 || k > kMaxK) return 0;
-        carve_score(c, H, W, k);
+        if (H < 1 || W < 1 || k < 1 || k > kMaxK || th < 1 || tw < 1 || th > H || tw > W) return 0;
+        carve_score(c, H, W, k, th, tw);
         break;
     default:
         return 0;
@@ -378,24 +383,26 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
     GridSpec gs;
     vqnnf_status st = compile_bank(bank, F, th, tw, bs, gs);
     if (st != VQNNF_OK) return st;
-    const size_t smem = score_smem_bytes(bs, gs, k);
+    const bool u16 = sat_is_u16(th, tw);
+    const size_t smem = score_smem_bytes_for(u16 ? 2 : 4, bs, gs, k);
     if (smem > (size_t)device_smem_optin()) return VQNNF_EUNSUPPORTED;
     cudaStream_t s = as_stream(stream);
     WsCursor c{static_cast<char *>(ws), 0};
-    ScoreWs sw = carve_score(c, H, W, k);
-    cudaError_t e = launch_sat(q_labels, H, W, k, sw.carry, sw.S, s);
+    ScoreWs sw = carve_score(c, H, W, k, th, tw);
+    cudaError_t e = launch_sat(q_labels, H, W, k, sw.u16, sw.carry, sw.bandsum, sw.S, s);
     if (e != cudaSuccess) return from_cuda(e);
     const int HO = H - th + 1, WO = W - tw + 1;
-    return from_cuda(launch_score(sw.S, W, k, HO, WO, bs, gs, t_counts, heatmap, sw.amax,
+    return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, t_counts, heatmap, sw.amax,
                                   argmax_yx, s));
 }
 
 vqnnf_status vqnnf_last_device_error(void *stream)
 {
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return VQNNF_ECUDA;
-    int err = 0;
+    int err = 0, err2 = 0;
     if (read_and_clear_tc_error(&err) != cudaSuccess) return VQNNF_ECUDA;
-    return err ? VQNNF_ETIMEOUT : VQNNF_OK;
+    if (read_and_clear_score_error(&err2) != cudaSuccess) return VQNNF_ECUDA;
+    return (err || err2) ? VQNNF_ETIMEOUT : VQNNF_OK;
 }
 
 }  // extern "C"

@@ -44,6 +44,7 @@ constexpr int A_TILE = TM * KC * 2;        // 16 KB: one BF16 plane of the pixel
 constexpr int A_STAGE = 2 * A_TILE;        // hi and lo planes
 constexpr double kU = 5.9604644775390625e-08;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int PF = 8;              // chunks prefetched into L2 ahead of the loads
 
 struct TcArgs {
     long long n;
@@ -117,6 +118,12 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global [%0, {%1, %2}];" ::"l"(reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         ca[j] = ok ? g.p.a[jc] : 0.f;
         cv[j] = ok ? g.p.v[jc] : 0.f;
         cb[j] = ok ? g.p.b[jc] : 0.f;
-        cn[j] = ok ? g.p.nrm[jc] : 0.f;
+        cn[j] = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
     }
     for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
     if (tid == 0) {
@@ -250,8 +257,20 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             long long last_f[SF], last_b[2];
             for (int s = 0; s < SF; ++s) last_f[s] = -1;
             for (int s = 0; s < 2; ++s) last_b[s] = -1;
+            // L2 prefetch runs PF chunks ahead of the shared-memory loads, so the HBM latency
+            // is covered without more shared-memory stages
+            long long pf_tile = blockIdx.x;
+            int pf_kc = 0;
+            auto prefetch_next = [&]() {
+                if (pf_tile >= g.ntiles) return;
+                tma_prefetch_2d(&tmA, pf_kc * KC, (int)(pf_tile * TM));
+                tma_prefetch_2d(&tmA, pf_kc * KC + 32, (int)(pf_tile * TM));
+                if (++pf_kc == nkc) { pf_kc = 0; pf_tile += gridDim.x; }
+            };
+            for (int q = 0; q < PF; ++q) prefetch_next();
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
                 for (int kc = 0; kc < nkc; ++kc, ++it, ++itb) {
+                    prefetch_next();
                     const int s = it % SF;
                     if (!(ok = mbar_wait(&empty_f[s], ((it / SF) & 1) ^ 1, abort))) break;
                     mbar_expect_tx(&full_f[s], F32_STAGE);
@@ -347,11 +366,9 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                         const float xb = (da + 1 < D) ? xs[2 * q + 1] - mean[da + 1] : 0.f;
                         float ha, hb, la, lb;
                         w[q] = pack_bf16(xa, xb, ha, hb);
-                        xh2 = fmaf(ha, ha, fmaf(hb, hb, xh2));
+                        xh2 = fmaf(xa, xa, fmaf(xb, xb, xh2));        // ||x'||^2
                         const float ra = xa - ha, rb = xb - hb;       // exact
                         wl[q] = pack_bf16(ra, rb, la, lb);
-                        const float ea = ra - la, eb = rb - lb;       // exact
-                        dl2 = fmaf(ea, ea, fmaf(eb, eb, dl2));
                     }
                     *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
                     *reinterpret_cast<uint4 *>(lrow + ((c ^ sw) << 4)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
@@ -373,6 +390,12 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const int r = grp * 32 + lane;
         const float u = (float)kU;
         const float infl = 1.0f + 0.00390625f;
+        float amax_s = 0.f, vmax_s = 0.f, bmax_s = 0.f;
+        for (int j = 0; j < k; ++j) {
+            amax_s = fmaxf(amax_s, ca[j]);
+            vmax_s = fmaxf(vmax_s, cv[j]);
+            bmax_s = fmaxf(bmax_s, cb[j]);
+        }
         uint32_t tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
@@ -381,48 +404,59 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort));
             if (!ok) break;
             tc_fence_after();
-            const float inf = 1.0f + (float)(D + 8) * u;
-            const float X = sqrtf(norms[(buf * 2 + 0) * TM + r]) * inf;
-            const float Dl = sqrtf(norms[(buf * 2 + 1) * TM + r]) * inf;
+            // ||x_hi|| <= (1 + 2^-8) ||x'||  and  ||x' - x_hi - x_lo|| <= 2^-16 ||x'||  (two
+            // round-to-nearest BF16 roundings, each within 2^-8 relative)
+            const float nx = sqrtf(norms[(buf * 2 + 0) * TM + r]) * (1.0f + (float)(D + 8) * u);
+            const float X = nx * (1.0f + 0.00390625f);
+            const float Dl = nx * 1.5318e-05f + 1e-30f;      // 2^-16 * 1.004
             mbar_arrive(&nrm_empty[buf]);
             const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
             const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
-            float U = FLT_MAX, smin = FLT_MAX;
+            // pass 1: smallest score.  Columns past k hold +inf in cn (never chosen).
+            float smin = FLT_MAX, smax_abs = 0.f;
             int amin = 0;
             for (int c0 = 0; c0 < npad; c0 += 32) {
                 float v[32];
                 tc_ld32(taddr + c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
-                    if (col < k) {
-                        const float s = fmaf(-2.0f, v[j], cn[col]);
-                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
-                        U = fminf(U, s + B);
-                        if (s < smin) { smin = s; amin = col; }
-                    }
+                    const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
+                    if (s < smin) { smin = s; amin = c0 + j; }
+                    if (c0 + j < k) smax_abs = fmaxf(smax_abs, fabsf(s));
                 }
             }
+            // Bmax >= every B_j of this pixel (largest a, v, b and |s| of the row).  The upper
+            // end U = min_i s_i + B_i is reached among columns with s_i <= smin + Bmax, and a
+            // column with s_j > smin + 2 Bmax has s_j - B_j > smin + Bmax >= U: only columns
+            // with s_j <= smin + 2 Bmax are examined, with their own B_j.
+            const float Bmax = fmaf(X, amax_s, fmaf(Y, vmax_s, bmax_s + 4.0f * u * smax_abs)) * infl;
+            const float lim = smin + 2.0f * Bmax;
+            float U = FLT_MAX;
             int cnt = 0, last = amin;
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                float v[32];
-                tc_ld32(taddr + c0, v);
-                uint32_t word = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int c0 = 0; c0 < npad; c0 += 32) {
+                    float v[32];
+                    tc_ld32(taddr + c0, v);
+                    uint32_t word = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
-                    if (col < k) {
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = c0 + j;
                         const float s = fmaf(-2.0f, v[j], cn[col]);
-                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
-                        if (s - B <= U) {
-                            ++cnt;
-                            last = col;
-                            word |= 1u << j;
+                        if (s <= lim) {
+                            const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
+                            if (pass == 0) {
+                                U = fminf(U, s + B);
+                            } else if (s - B <= U) {
+                                ++cnt;
+                                last = col;
+                                word |= 1u << j;
+                            }
                         }
                     }
+                    if (pass == 1) maskbuf[r * kMaskWords + (c0 >> 5)] = word;
                 }
-                maskbuf[r * kMaskWords + (c0 >> 5)] = word;
             }
+
             for (int w = (npad + 31) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);

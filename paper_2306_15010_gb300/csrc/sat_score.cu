@@ -3,30 +3,40 @@
 // Integral image (Supp. "Integral Image"; exclusive-prefix reading): for cluster j,
 //     S[y][j][x] = #{ (y', x') : y' < y, x' < x, label(y', x') = j },  0 <= y <= H, 0 <= x <= W
 // stored channel-planar: element (y, j, x) at (y * k + j) * P + x, P = W + 1 rounded up to a
-// multiple of 4 (16-byte rows for vector copies).  A half-open rectangle's count is the
+// multiple of 8 (16-byte rows for bulk copies).  A half-open rectangle's count is the
 // four-corner sum S(y1,x1) - S(y0,x1) - S(y1,x0) + S(y0,x0); a filter is a weighted sum of
 // such boxes, i.e. the dilation filter that Algorithm 2 builds on the integral image.
 //
-// Build: (1) per row, the count of every cluster left of every 32-column strip; (2) one
-// warp per (strip, 8 clusters) sweeps the rows, each lane one column: the row prefix
-// inside the strip is a ballot + popcount, added to the running column sum.
+// Element type: uint16_t holding S mod 2^16 when every rectangle of the bank is smaller than
+// 65,536 pixels (template area <= 65,535) -- the four-corner sum taken mod 2^16 is then the
+// exact count -- else uint32_t.
 //
-// Score: one block per (window row, 256 windows); the corner rows of its windows are
-// staged in shared memory 8 clusters at a time (cp.async double buffering), each thread
-// owns two windows and accumulates exact integer L1 distances per filter over all
-// clusters, then combines them in float32 in bank order.
-#include <cuda_pipeline.h>
-
+// Build, in bands of BH rows so that every warp sweeps few rows:
+//   (1) row carries: per row, the count of every cluster left of every 32-column strip;
+//   (2) band sums: per band, the column sums of the row prefixes (exact int32);
+//   (3) exclusive prefix of the band sums over bands = S at every band's first row;
+//   (4) one warp per (band, strip, 8 clusters) sweeps its band from there and writes S;
+//       each lane owns one column, the row prefix inside the strip is a ballot + popcount.
+//
+// Score: one block per (window row, 512 windows).  The corner rows of its windows are
+// staged in shared memory 8 clusters at a time by bulk copies (one per row segment,
+// completing on an mbarrier, double-buffered); each thread owns four windows and
+// accumulates exact integer L1 distances per filter over all clusters, then combines them
+// in float32 in bank order.
 #include <cfloat>
 
 #include "common.cuh"
+#include "ptx.cuh"
 #include "score_spec.cuh"
 
 namespace vqnnf {
 namespace {
 
+__device__ int g_score_error = 0;
+
 constexpr int SW = 32;     // columns per strip = lanes
 constexpr int CGW = 8;     // clusters per warp in the sweep
+constexpr int BH = 64;     // rows per band
 
 // carry[(y * nS + s) * k + j] = #{x' < 32 s : label(y, x') = j}
 __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, int nS,
@@ -52,31 +62,41 @@ __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, 
     }
 }
 
-__global__ void __launch_bounds__(128) sat_sweep_kernel(const uint8_t *__restrict__ lab, int H,
-                                                        int W, int k, int P, int nS,
-                                                        const int *__restrict__ carry,
-                                                        int *__restrict__ S)
+// One warp per (band, strip, cluster group).  WRITE = false: accumulate the band's column
+// sums into bandsum.  WRITE = true: start from the band's prefix and write its S rows.
+template <typename T, bool WRITE>
+__global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict__ lab, int H, int W,
+                                                       int k, int P, int nS, int nB,
+                                                       const int *__restrict__ carry,
+                                                       int *__restrict__ bandsum, T *__restrict__ S)
 {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int ncg = (k + CGW - 1) / CGW;
-    if (gw >= nS * ncg) return;
-    const int s = gw / ncg, cg = gw % ncg;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= (long long)nB * nS * ncg) return;
+    const int cg = (int)(gw % ncg);
+    const int s = (int)((gw / ncg) % nS);
+    const int b = (int)(gw / ((long long)ncg * nS));
     const int x = s * SW + lane;          // S column owned by this lane
     const bool xin = x < P;
     const unsigned lt = (1u << lane) - 1u;
+    const int y0 = b * BH, y1 = min(H, y0 + BH);
     int acc[CGW];
-#pragma unroll
-    for (int q = 0; q < CGW; ++q) acc[q] = 0;
-    // row 0 of S is all zero
 #pragma unroll
     for (int q = 0; q < CGW; ++q) {
         const int j = cg * CGW + q;
-        if (j < k && xin) S[(size_t)j * P + x] = 0;
+        if (WRITE) {
+            const int jc = min(j, k - 1), xc = min(x, P - 1);      // clamped addresses
+            const int v = bandsum[((size_t)b * k + jc) * P + xc];
+            acc[q] = (j < k && xin) ? v : 0;
+            if (b == 0 && j < k && xin) S[(size_t)j * P + x] = (T)0;   // row 0 of S
+        } else {
+            acc[q] = 0;
+        }
     }
-    for (int y = 0; y < H; ++y) {
+    for (int y = y0; y < y1; ++y) {
         const int xl = s * SW + lane;      // label column tested by this lane
-        const int l0 = (int)lab[(size_t)y * W + min(xl, W - 1)];   // clamped address
+        const int l0 = (int)lab[(size_t)y * W + min(xl, W - 1)];
         const int lb = (xl < W) ? l0 : -1;
         const int jc = min(cg * CGW + (lane & (CGW - 1)), k - 1);
         const int c0 = carry[((size_t)y * nS + s) * k + jc];
@@ -84,11 +104,30 @@ __global__ void __launch_bounds__(128) sat_sweep_kernel(const uint8_t *__restric
 #pragma unroll
         for (int q = 0; q < CGW; ++q) {
             const int j = cg * CGW + q;
-            const unsigned b = __ballot_sync(0xffffffffu, lb == j);
-            const int r = __shfl_sync(0xffffffffu, cj, q) + __popc(b & lt);
-            acc[q] += r;
-            if (j < k && xin) S[((size_t)(y + 1) * k + j) * P + x] = acc[q];
+            const unsigned bal = __ballot_sync(0xffffffffu, lb == j);
+            acc[q] += __shfl_sync(0xffffffffu, cj, q) + __popc(bal & lt);
+            if (WRITE && j < k && xin) S[((size_t)(y + 1) * k + j) * P + x] = (T)(unsigned)acc[q];
         }
+    }
+    if (!WRITE) {
+#pragma unroll
+        for (int q = 0; q < CGW; ++q) {
+            const int j = cg * CGW + q;
+            if (j < k && xin) bandsum[((size_t)b * k + j) * P + x] = acc[q];
+        }
+    }
+}
+
+// Exclusive prefix of the band sums over bands, per (cluster, column), in place.
+__global__ void band_prefix_kernel(int *__restrict__ bandsum, int nB, long long kP)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kP) return;
+    int run = 0;
+    for (int b = 0; b < nB; ++b) {
+        const int t = bandsum[(size_t)b * kP + i];
+        bandsum[(size_t)b * kP + i] = run;
+        run += t;
     }
 }
 
@@ -117,8 +156,9 @@ __global__ void filter_responses_kernel(const uint8_t *__restrict__ lab, int w, 
 // ---------------------------------------------------------------------------------
 // Score.
 // ---------------------------------------------------------------------------------
-constexpr int TXW = 256;          // windows per block along x
-constexpr int STH = 128;          // threads (2 windows each)
+constexpr int STH = 128;          // threads per block
+constexpr int WPT = 4;            // windows per thread
+constexpr int TXW = STH * WPT;    // windows per block along x
 constexpr int CH = 8;             // clusters per staged chunk
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
@@ -128,32 +168,32 @@ __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
     return ((unsigned long long)b << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
 }
 
-// Stage corner rows [nrow] x NCOL columns of CH clusters starting at cluster j0.
-__device__ __forceinline__ void stage_chunk(int *dst, const int *__restrict__ S, int k, int P,
-                                            int y, int x0, int j0, int ncol, const int *roff,
-                                            int nrow)
+// Box count from four integral-image values; exact mod 2^16 for the 16-bit table.
+template <typename T>
+__device__ __forceinline__ int box(int s11, int s10, int s01, int s00)
 {
-    const int per_row = ncol / 4;                 // 16-byte pieces
-    const int total = CH * nrow * per_row;
-    for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int piece = q % per_row;
-        const int rr = (q / per_row) % nrow;
-        const int c = q / (per_row * nrow);
-        const int j = j0 + c;
-        int *d = dst + ((c * nrow + rr) * ncol + piece * 4);
-        const int col = x0 + piece * 4;
-        if (j < k && col < P) {
-            const int *src = S + ((size_t)(y + roff[rr]) * k + j) * P + col;
-            __pipeline_memcpy_async(d, src, 16);
-        } else {
-            d[0] = d[1] = d[2] = d[3] = 0;
-        }
-    }
-    __pipeline_commit();
+    const int v = s11 - s10 - s01 + s00;
+    return sizeof(T) == 2 ? (v & 0xFFFF) : v;
 }
 
-template <int G, bool FULL>
-__global__ void __launch_bounds__(STH) score_grid_kernel(const int *__restrict__ S, int P, int k,
+// Thread 0 issues the bulk copies of one chunk of corner rows: for cluster c of the chunk
+// and corner row rr, the ncol elements of S starting at column x0.
+template <typename T>
+__device__ __forceinline__ void issue_chunk(T *dst, const T *__restrict__ S, int k, int P, int y, int x0,
+                                            int j0, int ncol, const int *roff, int nrow, uint64_t *bar)
+{
+    const int cmax = min(CH, k - j0);
+    const uint32_t row_bytes = (uint32_t)(ncol * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads before the refill
+    ptx::mbar_expect_tx(bar, row_bytes * (uint32_t)(cmax * nrow));
+    for (int c = 0; c < cmax; ++c)
+        for (int rr = 0; rr < nrow; ++rr)
+            ptx::bulk_g2s(dst + (size_t)(c * nrow + rr) * ncol,
+                          S + ((size_t)(y + roff[rr]) * k + (j0 + c)) * P + x0, row_bytes, bar);
+}
+
+template <typename T, int G, bool FULL>
+__global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S, int P, int k,
                                                          int HO, int WO, GridSpec gs,
                                                          const int32_t *__restrict__ tcounts,
                                                          float *__restrict__ heat,
@@ -161,68 +201,74 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const int *__restrict__
 {
     constexpr int NR = G + 1;
     constexpr int NSLOT = G * G + (FULL ? 1 : 0);
-    extern __shared__ __align__(16) int sm[];
+    extern __shared__ __align__(128) uint8_t smem_raw[];
     const int ncol = gs.ncol;
-    int *buf0 = sm;
-    int *buf1 = sm + CH * NR * ncol;
-    int *tc = buf1 + CH * NR * ncol;      // [NSLOT][k]
+    T *buf0 = reinterpret_cast<T *>(smem_raw);
+    T *buf1 = buf0 + (size_t)CH * NR * ncol;
+    int *tc = reinterpret_cast<int *>(buf1 + (size_t)CH * NR * ncol);       // [NSLOT][k]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tc + NSLOT * k + (NSLOT * k & 1));   // [2]
     const int y = blockIdx.y;
     const int x0 = blockIdx.x * TXW;
+    const int nchunk = (k + CH - 1) / CH;
     for (int q = threadIdx.x; q < NSLOT * k; q += blockDim.x) {
         const int slot = q / k, j = q % k;
         tc[q] = tcounts[(size_t)gs.slot_filter[slot] * k + j];
     }
-    const int nchunk = (k + CH - 1) / CH;
-    stage_chunk(buf0, S, k, P, y, x0, 0, ncol, gs.by, NR);
-    int l1[2][NSLOT];
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar[0], 1);
+        ptx::mbar_init(&bar[1], 1);
+        ptx::fence_barrier_init();
+        issue_chunk<T>(buf0, S, k, P, y, x0, 0, ncol, gs.by, NR, &bar[0]);
+    }
+    __syncthreads();
+    int l1[WPT][NSLOT];
 #pragma unroll
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < WPT; ++w)
 #pragma unroll
         for (int q = 0; q < NSLOT; ++q) l1[w][q] = 0;
-    const int xl = threadIdx.x * 2;
+    bool ok = true;
     for (int ch = 0; ch < nchunk; ++ch) {
-        int *cur = (ch & 1) ? buf1 : buf0;
-        if (ch + 1 < nchunk) {
-            stage_chunk((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, gs.by, NR);
-            __pipeline_wait_prior(1);
-        } else {
-            __pipeline_wait_prior(0);
-        }
-        __syncthreads();
+        T *cur = (ch & 1) ? buf1 : buf0;
+        if (threadIdx.x == 0 && ch + 1 < nchunk)
+            issue_chunk<T>((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, gs.by, NR,
+                           &bar[(ch + 1) & 1]);
+        ok = ptx::mbar_wait_bounded(&bar[ch & 1], (ch >> 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
+        if (!__syncthreads_and(ok)) { ok = false; break; }
         const int cmax = min(CH, k - ch * CH);
         for (int c = 0; c < cmax; ++c) {
             const int j = ch * CH + c;
-            const int *base = cur + c * NR * ncol;
+            const T *base = cur + (size_t)c * NR * ncol;
             int t[NSLOT];
 #pragma unroll
             for (int q = 0; q < NSLOT; ++q) t[q] = tc[q * k + j];
 #pragma unroll
-            for (int w = 0; w < 2; ++w) {
+            for (int w = 0; w < WPT; ++w) {
+                const int xl = threadIdx.x + w * STH;
                 int cr[NR][NR];
 #pragma unroll
                 for (int r = 0; r < NR; ++r)
 #pragma unroll
-                    for (int cc = 0; cc < NR; ++cc) cr[r][cc] = base[r * ncol + xl + w + gs.bx[cc]];
+                    for (int cc = 0; cc < NR; ++cc) cr[r][cc] = (int)base[r * ncol + xl + gs.bx[cc]];
 #pragma unroll
                 for (int r = 0; r < G; ++r)
 #pragma unroll
                     for (int cc = 0; cc < G; ++cc) {
-                        const int v = cr[r + 1][cc + 1] - cr[r + 1][cc] - cr[r][cc + 1] + cr[r][cc];
-                        l1[w][r * G + cc] += abs(t[r * G + cc] - v);
+                        const int v = box<T>(cr[r + 1][cc + 1], cr[r + 1][cc], cr[r][cc + 1], cr[r][cc]);
+                        l1[w][r * G + cc] = (int)__sad(t[r * G + cc], v, (unsigned)l1[w][r * G + cc]);
                     }
                 if (FULL) {
-                    const int v = cr[G][G] - cr[G][0] - cr[0][G] + cr[0][0];
-                    l1[w][NSLOT - 1] += abs(t[NSLOT - 1] - v);
+                    const int v = box<T>(cr[G][G], cr[G][0], cr[0][G], cr[0][0]);
+                    l1[w][NSLOT - 1] = (int)__sad(t[NSLOT - 1], v, (unsigned)l1[w][NSLOT - 1]);
                 }
             }
         }
-        __syncthreads();
+        __syncthreads();    // the buffer is refilled next
     }
     // combine in bank order: H = - sum_f coef_f * L1_f
     unsigned long long best = 0ull;
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-        const int x = x0 + xl + w;
+    for (int w = 0; w < WPT; ++w) {
+        const int x = x0 + threadIdx.x + w * STH;
         float acc = 0.f;
         for (int f = 0; f < gs.F; ++f) {
             int v = 0;
@@ -232,7 +278,7 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const int *__restrict__
             acc = fmaf(gs.coef[f], (float)v, acc);
         }
         const float h = -acc;
-        if (x < WO) {
+        if (ok && x < WO) {
             heat[(size_t)y * WO + x] = h;
             const unsigned long long key = pack_key(h, (unsigned)(y * WO + x));
             best = key > best ? key : best;
@@ -250,48 +296,55 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const int *__restrict__
 
 // Generic bank: any weighted half-open rectangles.  Corner rows are the distinct row
 // offsets of the bank; each rectangle reads its four corners from shared memory.
-__global__ void __launch_bounds__(STH) score_generic_kernel(const int *__restrict__ S, int P,
-                                                            int k, int HO, int WO, BankSpec bs,
+template <typename T>
+__global__ void __launch_bounds__(STH) score_generic_kernel(const T *__restrict__ S, int P, int k,
+                                                            int HO, int WO, BankSpec bs,
                                                             const int32_t *__restrict__ tcounts,
                                                             float *__restrict__ heat,
                                                             unsigned long long *amax)
 {
-    extern __shared__ __align__(16) int sm[];
+    extern __shared__ __align__(128) uint8_t smem_raw[];
     const int ncol = bs.ncol, nrow = bs.nrow;
-    int *buf0 = sm;
-    int *buf1 = sm + CH * nrow * ncol;
-    int *tc = buf1 + CH * nrow * ncol;    // [F][k]
+    T *buf0 = reinterpret_cast<T *>(smem_raw);
+    T *buf1 = buf0 + (size_t)CH * nrow * ncol;
+    int *tc = reinterpret_cast<int *>(buf1 + (size_t)CH * nrow * ncol);      // [F][k]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tc + bs.F * k + (bs.F * k & 1));
     const int y = blockIdx.y;
     const int x0 = blockIdx.x * TXW;
-    for (int q = threadIdx.x; q < bs.F * k; q += blockDim.x) tc[q] = tcounts[q];
     const int nchunk = (k + CH - 1) / CH;
-    stage_chunk(buf0, S, k, P, y, x0, 0, ncol, bs.roff, nrow);
-    long long l1[2][kMaxFilters];
-    for (int w = 0; w < 2; ++w)
+    for (int q = threadIdx.x; q < bs.F * k; q += blockDim.x) tc[q] = tcounts[q];
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar[0], 1);
+        ptx::mbar_init(&bar[1], 1);
+        ptx::fence_barrier_init();
+        issue_chunk<T>(buf0, S, k, P, y, x0, 0, ncol, bs.roff, nrow, &bar[0]);
+    }
+    __syncthreads();
+    long long l1[WPT][kMaxFilters];
+    for (int w = 0; w < WPT; ++w)
         for (int f = 0; f < kMaxFilters; ++f) l1[w][f] = 0;
-    const int xl = threadIdx.x * 2;
+    bool ok = true;
     for (int ch = 0; ch < nchunk; ++ch) {
-        int *cur = (ch & 1) ? buf1 : buf0;
-        if (ch + 1 < nchunk) {
-            stage_chunk((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, bs.roff, nrow);
-            __pipeline_wait_prior(1);
-        } else {
-            __pipeline_wait_prior(0);
-        }
-        __syncthreads();
+        T *cur = (ch & 1) ? buf1 : buf0;
+        if (threadIdx.x == 0 && ch + 1 < nchunk)
+            issue_chunk<T>((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, bs.roff, nrow,
+                           &bar[(ch + 1) & 1]);
+        ok = ptx::mbar_wait_bounded(&bar[ch & 1], (ch >> 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
+        if (!__syncthreads_and(ok)) { ok = false; break; }
         const int cmax = min(CH, k - ch * CH);
         for (int c = 0; c < cmax; ++c) {
             const int j = ch * CH + c;
-            const int *base = cur + c * nrow * ncol;
+            const T *base = cur + (size_t)c * nrow * ncol;
             for (int f = 0; f < bs.F; ++f) {
                 const int t = tc[f * k + j];
-                for (int w = 0; w < 2; ++w) {
+                for (int w = 0; w < WPT; ++w) {
+                    const int xl = threadIdx.x + w * STH;
                     int v = 0;
                     for (int r = bs.rect_begin[f]; r < bs.rect_begin[f + 1]; ++r) {
                         const RectSpec rc = bs.rect[r];
-                        const int *r0 = base + rc.ry0 * ncol + xl + w;
-                        const int *r1 = base + rc.ry1 * ncol + xl + w;
-                        v += rc.weight * (r1[rc.x1] - r1[rc.x0] - r0[rc.x1] + r0[rc.x0]);
+                        const T *r0 = base + rc.ry0 * ncol + xl;
+                        const T *r1 = base + rc.ry1 * ncol + xl;
+                        v += rc.weight * box<T>(r1[rc.x1], r1[rc.x0], r0[rc.x1], r0[rc.x0]);
                     }
                     l1[w][f] += abs(t - v);
                 }
@@ -300,12 +353,12 @@ __global__ void __launch_bounds__(STH) score_generic_kernel(const int *__restric
         __syncthreads();
     }
     unsigned long long best = 0ull;
-    for (int w = 0; w < 2; ++w) {
-        const int x = x0 + xl + w;
+    for (int w = 0; w < WPT; ++w) {
+        const int x = x0 + threadIdx.x + w * STH;
         float acc = 0.f;
         for (int f = 0; f < bs.F; ++f) acc = fmaf(bs.coef[f], (float)l1[w][f], acc);
         const float h = -acc;
-        if (x < WO) {
+        if (ok && x < WO) {
             heat[(size_t)y * WO + x] = h;
             const unsigned long long key = pack_key(h, (unsigned)(y * WO + x));
             best = key > best ? key : best;
@@ -328,62 +381,46 @@ __global__ void argmax_finish_kernel(const unsigned long long *amax, int WO, int
     out[1] = (int32_t)(idx % (unsigned)WO);
 }
 
-template <int G, bool FULL>
-cudaError_t launch_grid(const int *S, int P, int k, int HO, int WO, const GridSpec &gs,
+template <typename T, int G, bool FULL>
+cudaError_t launch_grid(const T *S, int P, int k, int HO, int WO, const GridSpec &gs,
                         const int32_t *tc, float *heat, unsigned long long *amax, cudaStream_t s)
 {
-    constexpr int NR = G + 1;
-    constexpr int NSLOT = G * G + (FULL ? 1 : 0);
-    const size_t smem = sizeof(int) * ((size_t)2 * CH * NR * gs.ncol + (size_t)NSLOT * k);
-    cudaError_t e = cudaFuncSetAttribute(score_grid_kernel<G, FULL>,
+    BankSpec none;
+    none.F = 0;
+    const size_t smem = score_smem_bytes_for(sizeof(T), none, gs, k);
+    cudaError_t e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((WO + TXW - 1) / TXW, HO);
-    score_grid_kernel<G, FULL><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+    score_grid_kernel<T, G, FULL><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t score_smem_bytes(const BankSpec &bs, const GridSpec &gs, int k)
-{
-    if (gs.G > 0) {
-        const int NR = gs.G + 1;
-        const int NSLOT = gs.G * gs.G + (gs.full ? 1 : 0);
-        return sizeof(int) * ((size_t)2 * CH * NR * gs.ncol + (size_t)NSLOT * k);
-    }
-    return sizeof(int) * ((size_t)2 * CH * bs.nrow * bs.ncol + (size_t)bs.F * k);
-}
-
-int sat_pitch(int W) { return (W + 1 + 3) / 4 * 4; }
-int sat_strips(int W) { return (W + 1 + SW - 1) / SW; }
-int score_ncol(int tw) { return (TXW + tw + 3) / 4 * 4; }
-
-cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, int *carry, int *S, cudaStream_t s)
+template <typename T>
+cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, int *bandsum, T *S,
+                         cudaStream_t s)
 {
     const int nS = sat_strips(W);
     const int P = sat_pitch(W);
+    const int nB = sat_bands(H);
     const size_t hsmem = sizeof(int) * (size_t)nS * k;
     cudaError_t e = cudaFuncSetAttribute(row_carry_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     if (e != cudaSuccess) return e;
     row_carry_kernel<<<H, 256, hsmem, s>>>(lab, W, k, nS, carry);
-    const int nwarps = nS * ((k + CGW - 1) / CGW);
-    sat_sweep_kernel<<<(nwarps + 3) / 4, 128, 0, s>>>(lab, H, W, k, P, nS, carry, S);
+    const long long nwarps = (long long)nB * nS * ((k + CGW - 1) / CGW);
+    const unsigned blocks = (unsigned)((nwarps + 3) / 4);
+    sat_band_kernel<T, false><<<blocks, 128, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
+    const long long kP = (long long)k * P;
+    band_prefix_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, s>>>(bandsum, nB, kP);
+    sat_band_kernel<T, true><<<blocks, 128, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, const BankSpec &bs,
-                                    int32_t *counts, cudaStream_t s)
-{
-    (void)h;
-    filter_responses_kernel<<<bs.F, 256, 0, s>>>(lab, w, k, bs, counts);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankSpec &bs,
-                         const GridSpec &gs, const int32_t *tc, float *heat,
-                         unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s)
+template <typename T>
+cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankSpec &bs,
+                           const GridSpec &gs, const int32_t *tc, float *heat,
+                           unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s)
 {
     const int P = sat_pitch(W);
     cudaError_t e = cudaSuccess;
@@ -394,7 +431,7 @@ cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankS
     bool done = false;
 #define VQNNF_GRID_CASE(GG, FF)                                                         \
     if (!done && gs.G == GG && gs.full == FF) {                                         \
-        e = launch_grid<GG, FF>(S, P, k, HO, WO, gs, tc, heat, amax, s);                 \
+        e = launch_grid<T, GG, FF>(S, P, k, HO, WO, gs, tc, heat, amax, s);              \
         done = true;                                                                    \
     }
     VQNNF_GRID_CASE(1, false) VQNNF_GRID_CASE(1, true) VQNNF_GRID_CASE(2, false)
@@ -402,12 +439,14 @@ cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankS
     VQNNF_GRID_CASE(4, false) VQNNF_GRID_CASE(4, true)
 #undef VQNNF_GRID_CASE
     if (!done) {
-        const size_t smem = score_smem_bytes(bs, gs, k);
-        e = cudaFuncSetAttribute(score_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GridSpec none;
+        none.G = 0;
+        const size_t smem = score_smem_bytes_for(sizeof(T), bs, none, k);
+        e = cudaFuncSetAttribute(score_generic_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((WO + TXW - 1) / TXW, HO);
-        score_generic_kernel<<<grid, STH, smem, s>>>(S, P, k, HO, WO, bs, tc, heat, amax);
+        score_generic_kernel<T><<<grid, STH, smem, s>>>(S, P, k, HO, WO, bs, tc, heat, amax);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
@@ -415,6 +454,58 @@ cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankS
         argmax_finish_kernel<<<1, 1, 0, s>>>(amax, WO, argmax_yx);
         e = cudaGetLastError();
     }
+    return e;
+}
+
+}  // namespace
+
+size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs, int k)
+{
+    if (gs.G > 0) {
+        const int NR = gs.G + 1;
+        const int NSLOT = gs.G * gs.G + (gs.full ? 1 : 0);
+        return elem * (size_t)2 * CH * NR * gs.ncol + sizeof(int) * ((size_t)NSLOT * k + 1) + 32;
+    }
+    return elem * (size_t)2 * CH * bs.nrow * bs.ncol + sizeof(int) * ((size_t)bs.F * k + 1) + 32;
+}
+
+bool sat_is_u16(int th, int tw) { return (long long)th * tw <= 65535; }
+int sat_pitch(int W) { return (W + 1 + 7) / 8 * 8; }
+int sat_strips(int W) { return (W + 1 + SW - 1) / SW; }
+int sat_bands(int H) { return (H + BH - 1) / BH; }
+int score_ncol(int tw) { return (TXW + tw + 7) / 8 * 8; }
+size_t sat_slack_elems(int tw) { return (size_t)score_ncol(tw) + 64; }
+
+cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, bool u16, int *carry, int *bandsum,
+                       void *S, cudaStream_t s)
+{
+    return u16 ? launch_sat_t<uint16_t>(lab, H, W, k, carry, bandsum, static_cast<uint16_t *>(S), s)
+               : launch_sat_t<uint32_t>(lab, H, W, k, carry, bandsum, static_cast<uint32_t *>(S), s);
+}
+
+cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, const BankSpec &bs,
+                                    int32_t *counts, cudaStream_t s)
+{
+    (void)h;
+    filter_responses_kernel<<<bs.F, 256, 0, s>>>(lab, w, k, bs, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, const BankSpec &bs,
+                         const GridSpec &gs, const int32_t *tc, float *heat,
+                         unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s)
+{
+    return u16 ? launch_score_t<uint16_t>(static_cast<const uint16_t *>(S), W, k, HO, WO, bs, gs, tc, heat,
+                                          amax, argmax_yx, s)
+               : launch_score_t<uint32_t>(static_cast<const uint32_t *>(S), W, k, HO, WO, bs, gs, tc, heat,
+                                          amax, argmax_yx, s);
+}
+
+cudaError_t read_and_clear_score_error(int *out)
+{
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_score_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_score_error, &zero, sizeof(int));
     return e;
 }
 

@@ -42,15 +42,20 @@ struct GridSpec {
     float coef[kMaxFilters];
 };
 
-size_t score_smem_bytes(const BankSpec &bs, const GridSpec &gs, int k);
+size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs, int k);
+bool sat_is_u16(int th, int tw);
 int sat_pitch(int W);
 int sat_strips(int W);
+int sat_bands(int H);
 int score_ncol(int tw);
-cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, int *carry, int *S, cudaStream_t s);
+size_t sat_slack_elems(int tw);
+cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, bool u16, int *carry, int *bandsum,
+                       void *S, cudaStream_t s);
 cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, const BankSpec &bs,
                                     int32_t *counts, cudaStream_t s);
-cudaError_t launch_score(const int *S, int W, int k, int HO, int WO, const BankSpec &bs,
+cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, const BankSpec &bs,
                          const GridSpec &gs, const int32_t *tc, float *heat,
                          unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s);
+cudaError_t read_and_clear_score_error(int *out);
 
 }  // namespace vqnnf

@@ -49,8 +49,12 @@ def test_workspace_sizes(lib):
     a = lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 2048, 2048, 512, 128, 0, 0, 0, 1)
     assert a % 256 == 0 and a > 2048 * 2048 * 36
     assert lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 2048, 2048, 512, 257, 0, 0, 0, 1) == 0
+    # 16-bit integral image while the template area is below 65,536 pixels, 32-bit beyond
     s = lib.vqnnf_workspace_bytes(_lib.OP_SCORE, 256, 256, 0, 16, 32, 32, 5, 0)
-    assert s >= 257 * 16 * 260 * 4
+    assert s >= 257 * 16 * 264 * 2
+    big = lib.vqnnf_workspace_bytes(_lib.OP_SCORE, 600, 600, 0, 16, 300, 300, 5, 0)
+    assert big >= 601 * 16 * 608 * 4
+    assert lib.vqnnf_workspace_bytes(_lib.OP_SCORE, 256, 256, 0, 16, 300, 32, 5, 0) == 0
     assert lib.vqnnf_workspace_bytes(99, 1, 1, 1, 1, 1, 1, 1, 0) == 0
     f = lib.vqnnf_workspace_bytes(_lib.OP_FIT, 128, 128, 512, 128, 0, 0, 0, 0)
     assert f > lib.vqnnf_workspace_bytes(_lib.OP_ASSIGN, 128, 128, 512, 128, 0, 0, 0, 0)

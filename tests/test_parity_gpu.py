@@ -256,3 +256,19 @@ def test_whole_path_graph_capture(vq):
     torch.cuda.synchronize()
     for a, b in zip((C, ql, heat, am), want):
         assert torch.equal(a, b)
+
+
+def test_score_large_template_uses_32bit_table(vq):
+    """Template area above 65,535 pixels: the integral image is kept in 32 bits."""
+    r = np.random.default_rng(21)
+    k, th, tw = 5, 260, 260
+    q = synth.query_map(300, 290, 4, M=6, n_sp=400, seed=21)
+    ql = (q.sp_id.numpy() * 3 % k).astype(np.int32)
+    ql[r.random(ql.shape) < 0.02] = r.integers(0, k)
+    t = ql[10:10 + th, 7:7 + tw].copy()
+    bank = synth.grid_bank(th, tw, 2)
+    tc = oracle.filter_counts(t, k, bank)
+    ref, _ = oracle.score(ql, k, th, tw, bank, tc)
+    heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank, _dev(tc.astype(np.int32)))
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+    assert am.cpu().tolist() == [10, 7]
