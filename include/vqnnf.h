@@ -158,7 +158,7 @@ vqnnf_status vqnnf_assign_noalloc(const float *X, int H, int W, int D, const flo
 /* Template representation vectors (Sec. 3.3, R(tau)): for every filter f and cluster j,
  *   counts[f * k + j] = sum over rects of weight * #{pixels labelled j in the rect}
  * with the window placed at the template's origin.
- *   labels  device, h x w uint8 template NNF;  bank: host, F >= 1 filters
+ *   labels  device, h x w uint8 template NNF, every label < k;  bank: host, F >= 1 filters
  *   counts  device, F x k int32, written */
 vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,
                                     const vqnnf_filter *bank, int F, int32_t *counts,
@@ -170,7 +170,8 @@ vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,
  * q_f(y, x) are the filter's counts over the query NNF with the window at (y, x), taken
  * from the per-cluster integral image of the one-hot query NNF.  The inner sums are exact
  * integers; the outer sum is float32 in bank order.
- *   q_labels  device, H x W uint8;  t_counts: device, F x k int32 (vqnnf_filter_responses)
+ *   q_labels  device, H x W uint8, every label < k;  t_counts: device, F x k int32
+ *             (vqnnf_filter_responses)
  *   heatmap   device, (H - th + 1) x (W - tw + 1) float32, written
  *   argmax_yx device int32[2] (y, x) of the maximum, lowest row-major index on ties;
  *             may be NULL */

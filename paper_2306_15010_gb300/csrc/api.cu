@@ -248,7 +248,13 @@ vqnnf_status compile_bank(const vqnnf_filter *bank, int F, int th, int tw, BankS
         g.bx[q] = xs[q];
         g.by[q] = ys[q];
     }
-    for (int f = 0; f < F; ++f) g.coef[f] = bs.coef[f];
+    for (int r = 0; r < G; ++r)
+        for (int c = 0; c < G; ++c) g.slot_area[r * G + c] = (xs[c + 1] - xs[c]) * (ys[r + 1] - ys[r]);
+    if (full_f >= 0) g.slot_area[G * G] = tw * th;
+    for (int f = 0; f < F; ++f) {
+        g.coef[f] = bs.coef[f];
+        g.slot_coef[g.filter_slot[f]] = bs.coef[f];
+    }
     gs = g;
     return VQNNF_OK;
 }

@@ -84,7 +84,19 @@ __global__ void update_kernel(const float *__restrict__ T, int D, int k,
     if (c == 0) return;
     const int *m = members + off[j];
     double s = 0.0;
-    for (int q = 0; q < c; ++q) s += (double)T[(size_t)m[q] * D + i];
+    int q = 0;
+    // loads are issued eight at a time; the FP64 additions stay strictly in member order
+    for (; q + 8 <= c; q += 8) {
+        int idx[8];
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) idx[u] = m[q + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = T[(size_t)idx[u] * D + i];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    }
+    for (; q < c; ++q) s += (double)T[(size_t)m[q] * D + i];
     C[(size_t)j * D + i] = (float)(s / (double)c);
 }
 

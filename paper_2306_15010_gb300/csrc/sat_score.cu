@@ -12,11 +12,11 @@
 // exact count -- else uint32_t.
 //
 // Build, in bands of BH rows so that every warp sweeps few rows:
-//   (1) row carries: per row, the count of every cluster left of every 32-column strip;
+//   (1) row carries: per row, the count of every cluster left of every 64-column strip;
 //   (2) band sums: per band, the column sums of the row prefixes (exact int32);
 //   (3) exclusive prefix of the band sums over bands = S at every band's first row;
 //   (4) one warp per (band, strip, 8 clusters) sweeps its band from there and writes S;
-//       each lane owns one column, the row prefix inside the strip is a ballot + popcount.
+//       each lane owns two columns, the row prefix inside the strip is ballots + popcounts.
 //
 // Score: one block per (window row, 512 windows).  The corner rows of its windows are
 // staged in shared memory 8 clusters at a time by bulk copies (one per row segment,
@@ -34,11 +34,11 @@ namespace {
 
 __device__ int g_score_error = 0;
 
-constexpr int SW = 32;     // columns per strip = lanes
+constexpr int SW = 64;     // columns per strip (two per lane)
 constexpr int CGW = 8;     // clusters per warp in the sweep
 constexpr int BH = 64;     // rows per band
 
-// carry[(y * nS + s) * k + j] = #{x' < 32 s : label(y, x') = j}
+// carry[(y * nS + s) * k + j] = #{x' < 64 s : label(y, x') = j}
 __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, int nS,
                                  int *__restrict__ carry)
 {
@@ -62,8 +62,23 @@ __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, 
     }
 }
 
-// One warp per (band, strip, cluster group).  WRITE = false: accumulate the band's column
-// sums into bandsum.  WRITE = true: start from the band's prefix and write its S rows.
+// One warp per (band, strip, cluster group); lane l owns the two S columns 2l and 2l + 1 of
+// its 64-column strip (one 4-byte store per lane for the 16-bit table).  WRITE = false:
+// accumulate the band's column sums into bandsum.  WRITE = true: start from the band's
+// prefix and write its S rows.
+template <typename T>
+__device__ __forceinline__ void store_pair(T *dst, int a, int b);
+template <>
+__device__ __forceinline__ void store_pair<uint16_t>(uint16_t *dst, int a, int b)
+{
+    *reinterpret_cast<uint32_t *>(dst) = ((uint32_t)a & 0xFFFFu) | ((uint32_t)b << 16);
+}
+template <>
+__device__ __forceinline__ void store_pair<uint32_t>(uint32_t *dst, int a, int b)
+{
+    *reinterpret_cast<uint2 *>(dst) = make_uint2((uint32_t)a, (uint32_t)b);
+}
+
 template <typename T, bool WRITE>
 __global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict__ lab, int H, int W,
                                                        int k, int P, int nS, int nB,
@@ -77,43 +92,53 @@ __global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict
     const int cg = (int)(gw % ncg);
     const int s = (int)((gw / ncg) % nS);
     const int b = (int)(gw / ((long long)ncg * nS));
-    const int x = s * SW + lane;          // S column owned by this lane
-    const bool xin = x < P;
+    const int x = s * SW + 2 * lane;      // first of the two S columns owned by this lane
+    const bool xin = x < P;               // P is even, so x + 1 < P as well
     const unsigned lt = (1u << lane) - 1u;
     const int y0 = b * BH, y1 = min(H, y0 + BH);
-    int acc[CGW];
+    int acc0[CGW], acc1[CGW];
 #pragma unroll
     for (int q = 0; q < CGW; ++q) {
         const int j = cg * CGW + q;
         if (WRITE) {
-            const int jc = min(j, k - 1), xc = min(x, P - 1);      // clamped addresses
-            const int v = bandsum[((size_t)b * k + jc) * P + xc];
-            acc[q] = (j < k && xin) ? v : 0;
-            if (b == 0 && j < k && xin) S[(size_t)j * P + x] = (T)0;   // row 0 of S
+            const int jc = min(j, k - 1), xc = min(x, P - 2);      // clamped addresses
+            const int2 v = *reinterpret_cast<const int2 *>(&bandsum[((size_t)b * k + jc) * P + xc]);
+            const bool in = j < k && xin;
+            acc0[q] = in ? v.x : 0;
+            acc1[q] = in ? v.y : 0;
+            if (b == 0 && in) store_pair<T>(&S[(size_t)j * P + x], 0, 0);   // row 0 of S
         } else {
-            acc[q] = 0;
+            acc0[q] = 0;
+            acc1[q] = 0;
         }
     }
     for (int y = y0; y < y1; ++y) {
-        const int xl = s * SW + lane;      // label column tested by this lane
-        const int l0 = (int)lab[(size_t)y * W + min(xl, W - 1)];
-        const int lb = (xl < W) ? l0 : -1;
+        // labels at the lane's two columns (clamped addresses, -1 past the row)
+        const uint8_t *row = lab + (size_t)y * W;
+        const int xa = x, xb = x + 1;
+        const int la0 = (int)row[min(xa, W - 1)], lb0 = (int)row[min(xb, W - 1)];
+        const int la = xa < W ? la0 : -1, lb = xb < W ? lb0 : -1;
         const int jc = min(cg * CGW + (lane & (CGW - 1)), k - 1);
         const int c0 = carry[((size_t)y * nS + s) * k + jc];
         const int cj = (lane < CGW && cg * CGW + lane < k) ? c0 : 0;
 #pragma unroll
         for (int q = 0; q < CGW; ++q) {
             const int j = cg * CGW + q;
-            const unsigned bal = __ballot_sync(0xffffffffu, lb == j);
-            acc[q] += __shfl_sync(0xffffffffu, cj, q) + __popc(bal & lt);
-            if (WRITE && j < k && xin) S[((size_t)(y + 1) * k + j) * P + x] = (T)(unsigned)acc[q];
+            const unsigned ba = __ballot_sync(0xffffffffu, la == j);
+            const unsigned bb = __ballot_sync(0xffffffffu, lb == j);
+            // row prefix at column x: carry + both columns of every lower lane
+            const int r0 = __shfl_sync(0xffffffffu, cj, q) + __popc(ba & lt) + __popc(bb & lt);
+            acc0[q] += r0;
+            acc1[q] += r0 + (la == j ? 1 : 0);
+            if (WRITE && j < k && xin) store_pair<T>(&S[((size_t)(y + 1) * k + j) * P + x], acc0[q], acc1[q]);
         }
     }
     if (!WRITE) {
 #pragma unroll
         for (int q = 0; q < CGW; ++q) {
             const int j = cg * CGW + q;
-            if (j < k && xin) bandsum[((size_t)b * k + j) * P + x] = acc[q];
+            if (j < k && xin)
+                *reinterpret_cast<int2 *>(&bandsum[((size_t)b * k + j) * P + x]) = make_int2(acc0[q], acc1[q]);
         }
     }
 }
@@ -124,7 +149,18 @@ __global__ void band_prefix_kernel(int *__restrict__ bandsum, int nB, long long 
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kP) return;
     int run = 0;
-    for (int b = 0; b < nB; ++b) {
+    int b = 0;
+    for (; b + 8 <= nB; b += 8) {            // eight independent loads in flight
+        int t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = bandsum[(size_t)(b + u) * kP + i];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            bandsum[(size_t)(b + u) * kP + i] = run;
+            run += t[u];
+        }
+    }
+    for (; b < nB; ++b) {
         const int t = bandsum[(size_t)b * kP + i];
         bandsum[(size_t)b * kP + i] = run;
         run += t;
@@ -159,7 +195,8 @@ __global__ void filter_responses_kernel(const uint8_t *__restrict__ lab, int w, 
 constexpr int STH = 128;          // threads per block
 constexpr int WPT = 4;            // windows per thread
 constexpr int TXW = STH * WPT;    // windows per block along x
-constexpr int CH = 8;             // clusters per staged chunk
+constexpr int CH = 4;             // clusters per staged chunk
+constexpr int NBUF = 3;           // staging buffers of the grid kernel
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
 {
@@ -199,85 +236,120 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
                                                          float *__restrict__ heat,
                                                          unsigned long long *amax)
 {
+    // For a single-rectangle filter q and clusters j, with t = template count and n = query
+    // count (every pixel carries one label < k, so sum_j n_qj = area_q):
+    //     L1_q = sum_j |t_qj - n_qj| = area_q + sum_{j : t_qj > 0} (|t_qj - n_qj| - n_qj)
+    // so cluster j only costs work in the cells where the template holds it.
     constexpr int NR = G + 1;
     constexpr int NSLOT = G * G + (FULL ? 1 : 0);
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const int ncol = gs.ncol;
-    T *buf0 = reinterpret_cast<T *>(smem_raw);
-    T *buf1 = buf0 + (size_t)CH * NR * ncol;
-    int *tc = reinterpret_cast<int *>(buf1 + (size_t)CH * NR * ncol);       // [NSLOT][k]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tc + NSLOT * k + (NSLOT * k & 1));   // [2]
+    const size_t chunk_elems = (size_t)CH * NR * ncol;
+    T *bufs = reinterpret_cast<T *>(smem_raw);                               // [NBUF][chunk]
+    int *tc = reinterpret_cast<int *>(bufs + NBUF * chunk_elems);           // [NSLOT][k]
+    unsigned *cmask = reinterpret_cast<unsigned *>(tc + NSLOT * k);          // [k]
+    uint64_t *full = reinterpret_cast<uint64_t *>(cmask + k + ((NSLOT * k + k) & 1));
+    uint64_t *empty = full + NBUF;
+    int *n_issued = reinterpret_cast<int *>(empty + NBUF);
     const int y = blockIdx.y;
     const int x0 = blockIdx.x * TXW;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nchunk = (k + CH - 1) / CH;
     for (int q = threadIdx.x; q < NSLOT * k; q += blockDim.x) {
         const int slot = q / k, j = q % k;
         tc[q] = tcounts[(size_t)gs.slot_filter[slot] * k + j];
     }
     if (threadIdx.x == 0) {
-        ptx::mbar_init(&bar[0], 1);
-        ptx::mbar_init(&bar[1], 1);
+        for (int b = 0; b < NBUF; ++b) {
+            ptx::mbar_init(&full[b], 1);
+            ptx::mbar_init(&empty[b], STH / 32);
+        }
         ptx::fence_barrier_init();
-        issue_chunk<T>(buf0, S, k, P, y, x0, 0, ncol, gs.by, NR, &bar[0]);
+        int c = 0;
+        for (; c < NBUF - 1 && c < nchunk; ++c)
+            issue_chunk<T>(bufs + c * chunk_elems, S, k, P, y, x0, c * CH, ncol, gs.by, NR, &full[c]);
+        *n_issued = c;
     }
     __syncthreads();
-    int l1[WPT][NSLOT];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        unsigned m = 0;
+#pragma unroll
+        for (int q = 0; q < NSLOT; ++q) m |= (tc[q * k + j] > 0 ? 1u : 0u) << q;
+        cmask[j] = m;
+    }
+    // per-window corner column offsets are the same for every cluster
+    int off[NR];
+#pragma unroll
+    for (int cc = 0; cc < NR; ++cc) off[cc] = gs.bx[cc];
+    int acc[WPT][NSLOT];
 #pragma unroll
     for (int w = 0; w < WPT; ++w)
 #pragma unroll
-        for (int q = 0; q < NSLOT; ++q) l1[w][q] = 0;
+        for (int q = 0; q < NSLOT; ++q) acc[w][q] = gs.slot_area[q];
+    __syncthreads();
     bool ok = true;
     for (int ch = 0; ch < nchunk; ++ch) {
-        T *cur = (ch & 1) ? buf1 : buf0;
-        if (threadIdx.x == 0 && ch + 1 < nchunk)
-            issue_chunk<T>((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, gs.by, NR,
-                           &bar[(ch + 1) & 1]);
-        ok = ptx::mbar_wait_bounded(&bar[ch & 1], (ch >> 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
-        if (!__syncthreads_and(ok)) { ok = false; break; }
+        const int b = ch % NBUF;
+        if (threadIdx.x == 0 && ch + NBUF - 1 < nchunk) {
+            // refill the buffer that chunk ch - 1 used, once every warp has released it
+            const int nb = (ch + NBUF - 1) % NBUF;
+            const int use = (ch + NBUF - 1) / NBUF;          // how many times nb was filled before
+            if (use > 0)
+                ok = ptx::mbar_wait_bounded(&empty[nb], (use - 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
+            if (ok) {
+                issue_chunk<T>(bufs + nb * chunk_elems, S, k, P, y, x0, (ch + NBUF - 1) * CH, ncol, gs.by,
+                               NR, &full[nb]);
+                *n_issued = ch + NBUF;
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok && ptx::mbar_wait_bounded(&full[b], (ch / NBUF) & 1, &g_score_error,
+                                                                  (int)VQNNF_ETIMEOUT));
+        if (!ok) break;
+        const T *cur = bufs + b * chunk_elems;
         const int cmax = min(CH, k - ch * CH);
         for (int c = 0; c < cmax; ++c) {
             const int j = ch * CH + c;
-            const T *base = cur + (size_t)c * NR * ncol;
-            int t[NSLOT];
+            const unsigned m = cmask[j];                    // same for every thread: uniform branches
+            const T *base = cur + (size_t)c * NR * ncol + threadIdx.x;
 #pragma unroll
-            for (int q = 0; q < NSLOT; ++q) t[q] = tc[q * k + j];
+            for (int q = 0; q < NSLOT; ++q) {
+                if (!(m & (1u << q))) continue;
+                const int t = tc[q * k + j];
+                const int r0 = (FULL && q == NSLOT - 1) ? 0 : q / G;
+                const int r1 = (FULL && q == NSLOT - 1) ? G : q / G + 1;
+                const int c0 = (FULL && q == NSLOT - 1) ? 0 : q % G;
+                const int c1 = (FULL && q == NSLOT - 1) ? G : q % G + 1;
 #pragma unroll
-            for (int w = 0; w < WPT; ++w) {
-                const int xl = threadIdx.x + w * STH;
-                int cr[NR][NR];
-#pragma unroll
-                for (int r = 0; r < NR; ++r)
-#pragma unroll
-                    for (int cc = 0; cc < NR; ++cc) cr[r][cc] = (int)base[r * ncol + xl + gs.bx[cc]];
-#pragma unroll
-                for (int r = 0; r < G; ++r)
-#pragma unroll
-                    for (int cc = 0; cc < G; ++cc) {
-                        const int v = box<T>(cr[r + 1][cc + 1], cr[r + 1][cc], cr[r][cc + 1], cr[r][cc]);
-                        l1[w][r * G + cc] = (int)__sad(t[r * G + cc], v, (unsigned)l1[w][r * G + cc]);
-                    }
-                if (FULL) {
-                    const int v = box<T>(cr[G][G], cr[G][0], cr[0][G], cr[0][0]);
-                    l1[w][NSLOT - 1] = (int)__sad(t[NSLOT - 1], v, (unsigned)l1[w][NSLOT - 1]);
+                for (int w = 0; w < WPT; ++w) {
+                    const T *p = base + w * STH;
+                    const int n = box<T>((int)p[r1 * ncol + off[c1]], (int)p[r1 * ncol + off[c0]],
+                                         (int)p[r0 * ncol + off[c1]], (int)p[r0 * ncol + off[c0]]);
+                    acc[w][q] = (int)__sad(t, n, (unsigned)acc[w][q]) - n;
                 }
             }
         }
-        __syncthreads();    // the buffer is refilled next
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(&empty[b]))
+                                    : "memory");
     }
-    // combine in bank order: H = - sum_f coef_f * L1_f
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) {
+        // a wait gave up: let every bulk copy issued into shared memory land (bounded)
+        // before the block exits
+        int dummy = 0;
+        const int issued = *n_issued;
+        for (int c = max(0, issued - NBUF); c < issued; ++c)
+            ptx::mbar_wait_bounded(&full[c % NBUF], (c / NBUF) & 1, &dummy, 1);
+    }
+    (void)warp;
+    // combine in a fixed (cell-major, full window last) order: H = - sum_q coef_q * L1_q
     unsigned long long best = 0ull;
 #pragma unroll
     for (int w = 0; w < WPT; ++w) {
         const int x = x0 + threadIdx.x + w * STH;
-        float acc = 0.f;
-        for (int f = 0; f < gs.F; ++f) {
-            int v = 0;
+        float accf = 0.f;
 #pragma unroll
-            for (int q = 0; q < NSLOT; ++q)
-                if (gs.filter_slot[f] == q) v = l1[w][q];
-            acc = fmaf(gs.coef[f], (float)v, acc);
-        }
-        const float h = -acc;
+        for (int q = 0; q < NSLOT; ++q) accf = fmaf(gs.slot_coef[q], (float)acc[w][q], accf);
+        const float h = -accf;
         if (ok && x < WO) {
             heat[(size_t)y * WO + x] = h;
             const unsigned long long key = pack_key(h, (unsigned)(y * WO + x));
@@ -464,7 +536,8 @@ size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs,
     if (gs.G > 0) {
         const int NR = gs.G + 1;
         const int NSLOT = gs.G * gs.G + (gs.full ? 1 : 0);
-        return elem * (size_t)2 * CH * NR * gs.ncol + sizeof(int) * ((size_t)NSLOT * k + 1) + 32;
+        return elem * (size_t)NBUF * CH * NR * gs.ncol + sizeof(int) * ((size_t)NSLOT * k + k + 1) +
+               sizeof(uint64_t) * 2 * NBUF + 16 + 16;
     }
     return elem * (size_t)2 * CH * bs.nrow * bs.ncol + sizeof(int) * ((size_t)bs.F * k + 1) + 32;
 }

@@ -38,6 +38,8 @@ struct GridSpec {
     int bx[5];
     int by[5];
     int slot_filter[17];          // slot -> filter index
+    int slot_area[17];            // pixels in the slot's rectangle
+    float slot_coef[17];          // w_f / A_f of the slot's filter
     int filter_slot[kMaxFilters]; // filter index -> slot
     float coef[kMaxFilters];
 };
