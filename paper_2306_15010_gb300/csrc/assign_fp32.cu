@@ -32,17 +32,24 @@ constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
 // The reference point m only has to be the same FP32 vector for every use (the bound holds
 // for any m); the codebook mean keeps the centred norms small.  Four interleaved FP32 partial
 // sums in a fixed order: deterministic and short.
-__global__ void prep_mean_kernel(const float *__restrict__ C, int k, int D, float *mean)
+__global__ void __launch_bounds__(256) prep_mean_kernel(const float *__restrict__ C, int k, int D,
+                                                        float *mean)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D) return;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    int j = 0;
-    for (; j + 4 <= k; j += 4)
+    // block: 32 dimensions x 8 row groups; partial sums combined in a fixed order
+    __shared__ float part[8][33];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int g = threadIdx.x >> 5;
+    float s = 0.f;
+    if (i < D)
+        for (int j = g; j < k; j += 8) s += C[(size_t)j * D + i];
+    part[g][threadIdx.x & 31] = s;
+    __syncthreads();
+    if (g == 0 && i < D) {
+        float t = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] += C[(size_t)(j + u) * D + i];
-    for (; j < k; ++j) s[0] += C[(size_t)j * D + i];
-    mean[i] = ((s[0] + s[1]) + (s[2] + s[3])) / (float)k;
+        for (int q = 0; q < 8; ++q) t += part[q][threadIdx.x];
+        mean[i] = t / (float)k;
+    }
 }
 
 __device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h)
@@ -445,7 +452,7 @@ __global__ void finish_stats_kernel(FlagList fl, vqnnf_assign_stats *out)
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
                                  cudaStream_t s)
 {
-    prep_mean_kernel<<<(D + 63) / 64, 64, 0, s>>>(C, k, D, p.mean);
+    prep_mean_kernel<<<(D + 31) / 32, 256, 0, s>>>(C, k, D, p.mean);
     prep_centroid_kernel<<<k, 256, 0, s>>>(C, k, D, prec, p);
     return cudaGetLastError();
 }

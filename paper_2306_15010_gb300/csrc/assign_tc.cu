@@ -87,12 +87,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
     return ok != 0;
 }
 // Bounded wait: false when this CTA gave up (timeout here or abort raised elsewhere).
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort)
+// `nap` > 0 sleeps that many ns between polls (warps that are not on the critical path),
+// so that waiting warps leave their issue slots to the working ones.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, int nap = 0)
 {
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, parity)) return true;
+        if (nap) __nanosleep(nap);
         if ((i & 63) == 0) {
             if (*abort) return false;
             if (clock64() - t0 > kWaitCycles) {
@@ -344,8 +347,8 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             float xh2 = 0.f, dl2 = 0.f;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int s = it % SF, sa = it % SA;
-                ok = mbar_wait(&full_f[s], (it / SF) & 1, abort);
-                ok = __all_sync(0xffffffffu, ok && mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort));
+                ok = mbar_wait(&full_f[s], (it / SF) & 1, abort, 20);
+                ok = __all_sync(0xffffffffu, ok && mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort, 20));
                 if (!ok) break;
                 const uint8_t *frow = f32s + s * F32_STAGE + r * 128;
                 uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
@@ -390,18 +393,21 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const int r = grp * 32 + lane;
         const float u = (float)kU;
         const float infl = 1.0f + 0.00390625f;
-        float amax_s = 0.f, vmax_s = 0.f, bmax_s = 0.f;
+        float amax_s = 0.f, vmax_s = 0.f, bmax_s = 0.f, nrm_max = 0.f;
         for (int j = 0; j < k; ++j) {
             amax_s = fmaxf(amax_s, ca[j]);
             vmax_s = fmaxf(vmax_s, cv[j]);
             bmax_s = fmaxf(bmax_s, cb[j]);
+            nrm_max = fmaxf(nrm_max, cn[j]);
         }
+        const float cnorm_max = sqrtf(nrm_max) * 1.0001f;    // max ||c_j*|| (cn = ||c*||^2 in FP32)
+        nrm_max *= 1.0001f;
         uint32_t tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
             const uint32_t buf = tl & 1, ph = (tl >> 1) & 1;
-            ok = mbar_wait(&acc_full[buf], ph, abort);
-            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort));
+            ok = mbar_wait(&acc_full[buf], ph, abort, 200);
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort, 200));
             if (!ok) break;
             tc_fence_after();
             // ||x_hi|| <= (1 + 2^-8) ||x'||  and  ||x' - x_hi - x_lo|| <= 2^-16 ||x'||  (two
@@ -422,9 +428,11 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 for (int j = 0; j < 32; ++j) {
                     const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
                     if (s < smin) { smin = s; amin = c0 + j; }
-                    if (c0 + j < k) smax_abs = fmaxf(smax_abs, fabsf(s));
                 }
             }
+            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
+            // contraction's own error, so Bmax covers every column's 4u|s_j| term
+            smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
             // Bmax >= every B_j of this pixel (largest a, v, b and |s| of the row).  The upper
             // end U = min_i s_i + B_i is reached among columns with s_i <= smin + Bmax, and a
             // column with s_j > smin + 2 Bmax has s_j - B_j > smin + Bmax >= U: only columns

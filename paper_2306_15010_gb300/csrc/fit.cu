@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
     }
     __syncthreads();
     for (int c0 = 0; c0 < l; c0 += blockDim.x) {
-        for (int q = t; q < 32 * kMaxK; q += blockDim.x) (&wc[0][0])[q] = 0;
+        for (int q = t; q < 32 * kMaxK; q += blockDim.x)
+            if ((q & (kMaxK - 1)) < k) (&wc[0][0])[q] = 0;
         __syncthreads();
         const int p = c0 + t;
         const bool ok = p < l;
@@ -113,8 +114,10 @@ cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8
                                 int *off, int *members, float *C, cudaStream_t s)
 {
     stable_sort_kernel<<<1, 1024, 0, s>>>(lab, l, k, cnt, off, members);
-    dim3 g((D + 127) / 128, k);
-    update_kernel<<<g, 128, 0, s>>>(T, D, k, cnt, off, members, C);
+    // one warp per (32 dimensions, cluster): a large cluster's in-order FP64 chains spread
+    // over many SMs (FP64 throughput per SM is small)
+    dim3 g((D + 31) / 32, k);
+    update_kernel<<<g, 32, 0, s>>>(T, D, k, cnt, off, members, C);
     return cudaGetLastError();
 }
 
