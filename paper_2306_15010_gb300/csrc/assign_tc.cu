@@ -9,8 +9,10 @@
 // shared re-scoring stage, so labels stay exact.
 //
 // One persistent CTA per SM, 128-pixel tiles, warp-specialised:
-//   warp 0      TMA producer: FP32 feature boxes (128 rows x 32 floats, 128B swizzle) and
-//               the two BF16 centroid planes (k rows x 64 elements, 128B swizzle)
+//   warp 0      TMA producer of the FP32 feature boxes (128 rows x 32 floats, 128B swizzle),
+//               five boxes in flight, plus L2 prefetch further ahead
+//   warp 10     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
+//               swizzle); separate from warp 0 so that feature loads never wait for MMAs
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 //   warps 2-5   converters: thread r owns pixel row r; FP32 -> centred BF16 hi and lo planes
 //               written in the UMMA K-major 128B-swizzled layout; accumulates ||x_hi||^2 and the
@@ -36,10 +38,10 @@ __device__ int g_tc_error = 0;
 
 constexpr int TM = 128;            // pixels per tile (UMMA M)
 constexpr int KC = 64;             // K elements per chunk (128 bytes of BF16)
-constexpr int SF = 2;              // FP32 staging stages
+constexpr int SF = 5;              // FP32 staging slots, one 16 KB box (32 columns) each
 constexpr int SA = 2;              // BF16 A-operand stages
-constexpr int NT = 320;            // 10 warps
-constexpr int F32_STAGE = TM * KC * 4;     // 32 KB (two 16 KB boxes)
+constexpr int NT = 352;            // 11 warps
+constexpr int F32_BOX = TM * 32 * 4;       // 16 KB: 128 rows x 32 floats
 constexpr int A_TILE = TM * KC * 2;        // 16 KB: one BF16 plane of the pixel tile
 constexpr int A_STAGE = 2 * A_TILE;        // hi and lo planes
 constexpr double kU = 5.9604644775390625e-08;
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int npad = g.npad, D = g.D, k = g.k, nkc = g.nkc, SB = g.sb;
     const int B_PLANE = npad * 128;
-    uint8_t *f32s = base;                                  // SF x 32 KB
-    uint8_t *as = f32s + SF * F32_STAGE;                   // SA x 16 KB
+    uint8_t *f32s = base;                                  // SF x 16 KB
+    uint8_t *as = f32s + SF * F32_BOX;                     // SA x 32 KB
     uint8_t *bs = as + SA * A_STAGE;                       // SB x (hi, lo)
     float *ca = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
     float *cv = ca + npad;
@@ -253,15 +255,13 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------------------------------------------------- TMA producer
+        // ---------------------------------------------------------- feature producer
         if (lane == 0) {
-            uint32_t it = 0, itb = 0;
+            uint32_t ib = 0;                                  // box counter
             bool ok = true;
-            long long last_f[SF], last_b[2];
-            for (int s = 0; s < SF; ++s) last_f[s] = -1;
-            for (int s = 0; s < 2; ++s) last_b[s] = -1;
-            // L2 prefetch runs PF chunks ahead of the shared-memory loads, so the HBM latency
-            // is covered without more shared-memory stages
+            long long last[SF];
+            for (int q = 0; q < SF; ++q) last[q] = -1;
+            // L2 prefetch runs PF chunks ahead of the shared-memory loads
             long long pf_tile = blockIdx.x;
             int pf_kc = 0;
             auto prefetch_next = [&]() {
@@ -272,15 +272,32 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             };
             for (int q = 0; q < PF; ++q) prefetch_next();
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
-                for (int kc = 0; kc < nkc; ++kc, ++it, ++itb) {
+                for (int kc = 0; ok && kc < nkc; ++kc) {
                     prefetch_next();
-                    const int s = it % SF;
-                    if (!(ok = mbar_wait(&empty_f[s], ((it / SF) & 1) ^ 1, abort))) break;
-                    mbar_expect_tx(&full_f[s], F32_STAGE);
-                    uint8_t *dst = f32s + s * F32_STAGE;
-                    tma_load_2d(dst, &tmA, kc * KC, (int)(tile * TM), &full_f[s]);
-                    tma_load_2d(dst + F32_STAGE / 2, &tmA, kc * KC + 32, (int)(tile * TM), &full_f[s]);
-                    last_f[s] = it;
+                    for (int h = 0; h < 2; ++h, ++ib) {
+                        const int s = ib % SF;
+                        if (!(ok = mbar_wait(&empty_f[s], ((ib / SF) & 1) ^ 1, abort))) break;
+                        mbar_expect_tx(&full_f[s], F32_BOX);
+                        tma_load_2d(f32s + s * F32_BOX, &tmA, kc * KC + 32 * h, (int)(tile * TM), &full_f[s]);
+                        last[s] = ib;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for every copy this thread issued to land
+                volatile int no_abort = 0;
+                for (int q = 0; q < SF; ++q)
+                    if (last[q] >= 0) mbar_wait(&full_f[q], (uint32_t)((last[q] / SF) & 1), &no_abort);
+            }
+        }
+    } else if (warp == 10) {
+        // ---------------------------------------------------------- centroid producer
+        if (lane == 0) {
+            uint32_t itb = 0;
+            bool ok = true;
+            long long last_b[2] = {-1, -1};
+            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
+                for (int kc = 0; kc < nkc; ++kc, ++itb) {
                     const int sb = itb % SB;
                     if (!(ok = mbar_wait(&empty_b[sb], ((itb / SB) & 1) ^ 1, abort))) break;
                     mbar_expect_tx(&full_b[sb], 2 * B_PLANE);
@@ -291,12 +308,9 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 }
             }
             if (!ok) {
-                // drain: wait (bounded) for every copy this thread issued to land
                 volatile int no_abort = 0;
-                for (int s = 0; s < SF; ++s)
-                    if (last_f[s] >= 0) mbar_wait(&full_f[s], (uint32_t)((last_f[s] / SF) & 1), &no_abort);
-                for (int s = 0; s < SB; ++s)
-                    if (last_b[s] >= 0) mbar_wait(&full_b[s], (uint32_t)((last_b[s] / SB) & 1), &no_abort);
+                for (int q = 0; q < SB; ++q)
+                    if (last_b[q] >= 0) mbar_wait(&full_b[q], (uint32_t)((last_b[q] / SB) & 1), &no_abort);
             }
         }
     } else if (warp == 1) {
@@ -336,26 +350,29 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             volatile int no_abort = 0;
             mbar_wait(drain, 0, &no_abort);
         }
-    } else if (warp < 6) {
+    } else if (warp >= 2 && warp < 6) {
         // ---------------------------------------------------------- converters
         const int r = tid - 64;                  // pixel row of the tile
         const int sw = r & 7;
-        uint32_t it = 0, tl = 0;
+        uint32_t it = 0, ib = 0, tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
             const uint32_t buf = tl & 1;
             float xh2 = 0.f, dl2 = 0.f;
             for (int kc = 0; kc < nkc; ++kc, ++it) {
-                const int s = it % SF, sa = it % SA;
-                ok = mbar_wait(&full_f[s], (it / SF) & 1, abort, 20);
-                ok = __all_sync(0xffffffffu, ok && mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort, 20));
+                const int sa = it % SA;
+                ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort, 20));
                 if (!ok) break;
-                const uint8_t *frow = f32s + s * F32_STAGE + r * 128;
                 uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
                 uint8_t *lrow = arow + A_TILE;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const uint8_t *box = frow + (c >> 2) * (F32_STAGE / 2);
+                    if ((c & 3) == 0) {
+                        const int s = ib % SF;
+                        ok = __all_sync(0xffffffffu, mbar_wait(&full_f[s], (ib / SF) & 1, abort, 20));
+                        if (!ok) break;
+                    }
+                    const uint8_t *box = f32s + (ib % SF) * F32_BOX + r * 128;
                     const int c0 = (c & 3) * 2;
                     const float4 v0 = *reinterpret_cast<const float4 *>(box + ((c0 ^ sw) << 4));
                     const float4 v1 = *reinterpret_cast<const float4 *>(box + (((c0 + 1) ^ sw) << 4));
@@ -375,10 +392,14 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     }
                     *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
                     *reinterpret_cast<uint4 *>(lrow + ((c ^ sw) << 4)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+                    if ((c & 3) == 3) {
+                        mbar_arrive(&empty_f[ib % SF]);      // this box has been read
+                        ++ib;
+                    }
                 }
+                if (!ok) break;
                 fence_proxy_async();
                 mbar_arrive(&a_full[sa]);
-                mbar_arrive(&empty_f[s]);
             }
             if (!ok) break;
             ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[buf], ((tl >> 1) & 1) ^ 1, abort));
@@ -387,7 +408,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             norms[(buf * 2 + 1) * TM + r] = dl2;
             mbar_arrive(&nrm_full[buf]);
         }
-    } else {
+    } else if (warp >= 6 && warp < 10) {
         // ---------------------------------------------------------- epilogue
         const int grp = warp & 3;                 // TMEM lane group this warp may read
         const int r = grp * 32 + lane;
@@ -536,10 +557,10 @@ size_t tc_smem_bytes(int npad, int D, int sb)
 {
     const int nkc = (D + KC - 1) / KC;
     size_t b = 1024;                                       // alignment slack
-    b += (size_t)SF * F32_STAGE + (size_t)SA * A_STAGE + (size_t)sb * 2 * npad * 128;
+    b += (size_t)SF * F32_BOX + (size_t)SA * A_STAGE + (size_t)sb * 2 * npad * 128;
     b += sizeof(float) * (4 * (size_t)npad + (size_t)nkc * KC + 4 * TM);
     b += sizeof(uint32_t) * TM * kMaskWords;
-    b += sizeof(uint64_t) * (2 * SF + 2 * SA + 12 + 1) + 16;   // 21 barriers, TMEM slot, abort flag
+    b += sizeof(uint64_t) * (2 * SF + 2 * SA + 12 + 1) + 16;   // barriers, TMEM slot, abort flag
     return b;
 }
 

@@ -74,31 +74,58 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
 }
 
 // c_j[i] = fl32( (sum over members, pixel order, FP64) / count ); empty clusters keep c_j.
-__global__ void update_kernel(const float *__restrict__ T, int D, int k,
-                              const int *__restrict__ cnt, const int *__restrict__ off,
-                              const int *__restrict__ members, float *__restrict__ C)
+// One warp per (cluster, 32 dimensions).  Each lane streams its own column of the member
+// rows through a shared-memory ring (cp.async, UR rows ahead), so the in-order FP64
+// additions are not serialised behind scattered-row load latency.
+constexpr int UR = 64;       // ring depth (member rows in flight per lane)
+constexpr int UIDX = 1024;   // member indices staged per block
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
 {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__global__ void __launch_bounds__(32) update_kernel(const float *__restrict__ T, int D, int k,
+                                                    const int *__restrict__ cnt, const int *__restrict__ off,
+                                                    const int *__restrict__ members, float *__restrict__ C)
+{
+    __shared__ float ring[UR][32];
+    __shared__ int idx[UIDX];
     const int j = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D) return;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
     const int c = cnt[j];
     if (c == 0) return;
     const int *m = members + off[j];
+    const int ic = i < D ? i : D - 1;           // clamped column (every address in bounds)
     double s = 0.0;
-    int q = 0;
-    // loads are issued eight at a time; the FP64 additions stay strictly in member order
-    for (; q + 8 <= c; q += 8) {
-        int idx[8];
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) idx[u] = m[q + u];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = T[(size_t)idx[u] * D + i];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s += (double)v[u];
+    for (int q0 = 0; q0 < c; q0 += UIDX) {
+        const int nq = min(UIDX, c - q0);
+        __syncwarp();
+        for (int t = lane; t < nq; t += 32) idx[t] = m[q0 + t];
+        __syncwarp();
+        int qi = 0;                              // next row to issue
+        for (; qi < nq && qi < UR; ++qi) {
+            cp_async4(&ring[qi % UR][lane], T + (size_t)idx[qi] * D + ic);
+            cp_commit();
+        }
+        for (int q = 0; q < nq; ++q) {
+            if (qi - q == UR) cp_wait<UR - 1>();
+            else cp_wait<0>();
+            s += (double)ring[q % UR][lane];     // strictly in member (pixel) order
+            if (qi < nq) {
+                cp_async4(&ring[qi % UR][lane], T + (size_t)idx[qi] * D + ic);
+                cp_commit();
+                ++qi;
+            }
+        }
     }
-    for (; q < c; ++q) s += (double)T[(size_t)m[q] * D + i];
-    C[(size_t)j * D + i] = (float)(s / (double)c);
+    if (i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
 }
 
 }  // namespace
