@@ -11,13 +11,13 @@
 // One persistent CTA per SM, 128-pixel tiles, warp-specialised:
 //   warp 0      TMA producer of the FP32 feature boxes (128 rows x 32 floats, 128B swizzle),
 //               five boxes in flight, plus L2 prefetch further ahead
-//   warp 10     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
+//   warp 14     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
 //               swizzle); separate from warp 0 so that feature loads never wait for MMAs
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warps 2-5   converters: thread r owns pixel row r; FP32 -> centred BF16 hi and lo planes
-//               written in the UMMA K-major 128B-swizzled layout; accumulates ||x_hi||^2 and the
-//               squared norm of what the two planes leave out
-//   warps 6-9   epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
+//   warps 2-9   converters: thread (h, r) owns pixel row r and the h-th 32-column box of
+//               every 64-column chunk; FP32 -> centred BF16 hi and lo planes written in the
+//               UMMA K-major 128B-swizzled layout; accumulates its part of ||x'||^2
+//   warps 10-13 epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
 //               flag push; the TMEM accumulator is double-buffered
 // Every mbarrier wait is bounded: on timeout the CTA records VQNNF_ETIMEOUT in the device
 // error word, all roles leave their loops, in-flight copies and MMAs are drained (bounded)
@@ -40,7 +40,7 @@ constexpr int TM = 128;            // pixels per tile (UMMA M)
 constexpr int KC = 64;             // K elements per chunk (128 bytes of BF16)
 constexpr int SF = 5;              // FP32 staging slots, one 16 KB box (32 columns) each
 constexpr int SA = 2;              // BF16 A-operand stages
-constexpr int NT = 352;            // 11 warps
+constexpr int NT = 480;            // 15 warps
 constexpr int F32_BOX = TM * 32 * 4;       // 16 KB: 128 rows x 32 floats
 constexpr int A_TILE = TM * KC * 2;        // 16 KB: one BF16 plane of the pixel tile
 constexpr int A_STAGE = 2 * A_TILE;        // hi and lo planes
@@ -89,15 +89,12 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
     return ok != 0;
 }
 // Bounded wait: false when this CTA gave up (timeout here or abort raised elsewhere).
-// `nap` > 0 sleeps that many ns between polls (warps that are not on the critical path),
-// so that waiting warps leave their issue slots to the working ones.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort, int nap = 0)
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort)
 {
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, parity)) return true;
-        if (nap) __nanosleep(nap);
         if ((i & 63) == 0) {
             if (*abort) return false;
             if (clock64() - t0 > kWaitCycles) {
@@ -232,11 +229,11 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
     if (tid == 0) {
         for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], TM); }
-        for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], TM); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], 2 * TM); mbar_init(&a_empty[s], 1); }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&full_b[s], 1); mbar_init(&empty_b[s], 1);
             mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], TM);
-            mbar_init(&nrm_full[s], TM); mbar_init(&nrm_empty[s], TM);
+            mbar_init(&nrm_full[s], 2 * TM); mbar_init(&nrm_empty[s], TM);
         }
         mbar_init(drain, 1);
         *abort = 0;
@@ -290,7 +287,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     if (last[q] >= 0) mbar_wait(&full_f[q], (uint32_t)((last[q] / SF) & 1), &no_abort);
             }
         }
-    } else if (warp == 10) {
+    } else if (warp == 14) {
         // ---------------------------------------------------------- centroid producer
         if (lane == 0) {
             uint32_t itb = 0;
@@ -350,65 +347,65 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             volatile int no_abort = 0;
             mbar_wait(drain, 0, &no_abort);
         }
-    } else if (warp >= 2 && warp < 6) {
+    } else if (warp >= 2 && warp < 10) {
         // ---------------------------------------------------------- converters
-        const int r = tid - 64;                  // pixel row of the tile
+        const int ct = tid - 64;
+        const int r = ct & (TM - 1);             // pixel row of the tile
+        const int h = ct >> 7;                   // 32-column box of each chunk this thread converts
         const int sw = r & 7;
-        uint32_t it = 0, ib = 0, tl = 0;
+        uint32_t it = 0, tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
             const uint32_t buf = tl & 1;
-            float xh2 = 0.f, dl2 = 0.f;
+            float xa2 = 0.f, xb2 = 0.f;                     // partial ||x'||^2 of this half
             for (int kc = 0; kc < nkc; ++kc, ++it) {
                 const int sa = it % SA;
-                ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort, 20));
+                const uint32_t ib = 2 * it + h;             // box counter of the feature producer
+                const int sf = ib % SF;
+                ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort));
+                ok = __all_sync(0xffffffffu, ok && mbar_wait(&full_f[sf], (ib / SF) & 1, abort));
                 if (!ok) break;
+                const uint8_t *box = f32s + sf * F32_BOX + r * 128;
                 uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
-                uint8_t *lrow = arow + A_TILE;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if ((c & 3) == 0) {
-                        const int s = ib % SF;
-                        ok = __all_sync(0xffffffffu, mbar_wait(&full_f[s], (ib / SF) & 1, abort, 20));
-                        if (!ok) break;
-                    }
-                    const uint8_t *box = f32s + (ib % SF) * F32_BOX + r * 128;
-                    const int c0 = (c & 3) * 2;
-                    const float4 v0 = *reinterpret_cast<const float4 *>(box + ((c0 ^ sw) << 4));
-                    const float4 v1 = *reinterpret_cast<const float4 *>(box + (((c0 + 1) ^ sw) << 4));
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = 4 * h + cc;                // 16-byte group of the 128-byte BF16 row
                     const int d0 = kc * KC + c * 8;
-                    const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                    uint32_t w[4], wl[4];
+                    uint4 w = make_uint4(0u, 0u, 0u, 0u), wl = w;
+                    if (d0 < D) {                            // D % 16 == 0: all 8 columns valid
+                        const float4 v0 = *reinterpret_cast<const float4 *>(box + (((2 * cc) ^ sw) << 4));
+                        const float4 v1 = *reinterpret_cast<const float4 *>(box + (((2 * cc + 1) ^ sw) << 4));
+                        const float4 m0 = *reinterpret_cast<const float4 *>(mean + d0);
+                        const float4 m1 = *reinterpret_cast<const float4 *>(mean + d0 + 4);
+                        const float xs[8] = {v0.x - m0.x, v0.y - m0.y, v0.z - m0.z, v0.w - m0.w,
+                                             v1.x - m1.x, v1.y - m1.y, v1.z - m1.z, v1.w - m1.w};
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int da = d0 + 2 * q;
-                        const float xa = (da < D) ? xs[2 * q] - mean[da] : 0.f;
-                        const float xb = (da + 1 < D) ? xs[2 * q + 1] - mean[da + 1] : 0.f;
-                        float ha, hb, la, lb;
-                        w[q] = pack_bf16(xa, xb, ha, hb);
-                        xh2 = fmaf(xa, xa, fmaf(xb, xb, xh2));        // ||x'||^2
-                        const float ra = xa - ha, rb = xb - hb;       // exact
-                        wl[q] = pack_bf16(ra, rb, la, lb);
+                        for (int q = 0; q < 4; ++q) {
+                            const float xa = xs[2 * q], xb = xs[2 * q + 1];
+                            float ha, hb, la, lb;
+                            hw[q] = pack_bf16(xa, xb, ha, hb);
+                            xa2 = fmaf(xa, xa, xa2);
+                            xb2 = fmaf(xb, xb, xb2);
+                            lw[q] = pack_bf16(xa - ha, xb - hb, la, lb);   // exact residuals
+                        }
+                        w = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        wl = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
-                    *reinterpret_cast<uint4 *>(lrow + ((c ^ sw) << 4)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
-                    if ((c & 3) == 3) {
-                        mbar_arrive(&empty_f[ib % SF]);      // this box has been read
-                        ++ib;
-                    }
+                    *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = w;
+                    *reinterpret_cast<uint4 *>(arow + A_TILE + ((c ^ sw) << 4)) = wl;
                 }
-                if (!ok) break;
+                mbar_arrive(&empty_f[sf]);                   // this box has been read
                 fence_proxy_async();
                 mbar_arrive(&a_full[sa]);
             }
             if (!ok) break;
             ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[buf], ((tl >> 1) & 1) ^ 1, abort));
             if (!ok) break;
-            norms[(buf * 2 + 0) * TM + r] = xh2;
-            norms[(buf * 2 + 1) * TM + r] = dl2;
+            norms[(buf * 2 + h) * TM + r] = xa2 + xb2;
             mbar_arrive(&nrm_full[buf]);
         }
-    } else if (warp >= 6 && warp < 10) {
+    } else if (warp >= 10 && warp < 14) {
         // ---------------------------------------------------------- epilogue
         const int grp = warp & 3;                 // TMEM lane group this warp may read
         const int r = grp * 32 + lane;
@@ -427,63 +424,67 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
             const uint32_t buf = tl & 1, ph = (tl >> 1) & 1;
-            ok = mbar_wait(&acc_full[buf], ph, abort, 200);
-            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort, 200));
+            ok = mbar_wait(&acc_full[buf], ph, abort);
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort));
             if (!ok) break;
             tc_fence_after();
             // ||x_hi|| <= (1 + 2^-8) ||x'||  and  ||x' - x_hi - x_lo|| <= 2^-16 ||x'||  (two
             // round-to-nearest BF16 roundings, each within 2^-8 relative)
-            const float nx = sqrtf(norms[(buf * 2 + 0) * TM + r]) * (1.0f + (float)(D + 8) * u);
+            const float x2 = norms[(buf * 2 + 0) * TM + r] + norms[(buf * 2 + 1) * TM + r];
+            const float nx = sqrtf(x2) * (1.0f + (float)(D + 8) * u);
             const float X = nx * (1.0f + 0.00390625f);
             const float Dl = nx * 1.5318e-05f + 1e-30f;      // 2^-16 * 1.004
             mbar_arrive(&nrm_empty[buf]);
             const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
             const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
-            // pass 1: smallest score.  Columns past k hold +inf in cn (never chosen).
-            float smin = FLT_MAX, smax_abs = 0.f;
-            int amin = 0;
+            // pass 1: smallest score, lowest column on ties, as four interleaved running minima.
+            // Columns past k hold +inf in cn (never chosen).
+            float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+            int am[4] = {0, 0, 0, 0};
             for (int c0 = 0; c0 < npad; c0 += 32) {
                 float v[32];
                 tc_ld32(taddr + c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
-                    if (s < smin) { smin = s; amin = c0 + j; }
+                    if (s < sm[j & 3]) { sm[j & 3] = s; am[j & 3] = c0 + j; }
                 }
             }
+            float smin = sm[0];
+            int amin = am[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
             // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
             // contraction's own error, so Bmax covers every column's 4u|s_j| term
-            smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
-            // Bmax >= every B_j of this pixel (largest a, v, b and |s| of the row).  The upper
-            // end U = min_i s_i + B_i is reached among columns with s_i <= smin + Bmax, and a
-            // column with s_j > smin + 2 Bmax has s_j - B_j > smin + Bmax >= U: only columns
-            // with s_j <= smin + 2 Bmax are examined, with their own B_j.
+            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
             const float Bmax = fmaf(X, amax_s, fmaf(Y, vmax_s, bmax_s + 4.0f * u * smax_abs)) * infl;
-            const float lim = smin + 2.0f * Bmax;
-            float U = FLT_MAX;
+            // U, the upper end of column amin's interval, bounds the smallest distance from
+            // above, so the nearest column j has s_j - B_j <= U and s_j <= U + Bmax.  The
+            // prefilter limit U + 2 Bmax leaves room for the rounding of that sum (u |U| is
+            // below Bmax / 2 because Bmax >= 4u |smin|): only columns under it get their own B_j.
+            const float Ba = fmaf(X, ca[amin], fmaf(Y, cv[amin], cb[amin] + 4.0f * u * fabsf(smin))) * infl;
+            const float U = smin + Ba;
+            const float lim = U + 2.0f * Bmax;
             int cnt = 0, last = amin;
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int c0 = 0; c0 < npad; c0 += 32) {
-                    float v[32];
-                    tc_ld32(taddr + c0, v);
-                    uint32_t word = 0;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + c0, v);
+                uint32_t word = 0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = c0 + j;
-                        const float s = fmaf(-2.0f, v[j], cn[col]);
-                        if (s <= lim) {
-                            const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
-                            if (pass == 0) {
-                                U = fminf(U, s + B);
-                            } else if (s - B <= U) {
-                                ++cnt;
-                                last = col;
-                                word |= 1u << j;
-                            }
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    const float s = fmaf(-2.0f, v[j], cn[col]);
+                    if (s <= lim) {
+                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
+                        if (s - B <= U) {
+                            ++cnt;
+                            last = col;
+                            word |= 1u << j;
                         }
                     }
-                    if (pass == 1) maskbuf[r * kMaskWords + (c0 >> 5)] = word;
                 }
+                maskbuf[r * kMaskWords + (c0 >> 5)] = word;
             }
 
             for (int w = (npad + 31) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;

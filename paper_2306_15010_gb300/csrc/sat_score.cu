@@ -335,10 +335,9 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
     if (!__syncthreads_and(ok) && threadIdx.x == 0) {
         // a wait gave up: let every bulk copy issued into shared memory land (bounded)
         // before the block exits
-        int dummy = 0;
         const int issued = *n_issued;
         for (int c = max(0, issued - NBUF); c < issued; ++c)
-            ptx::mbar_wait_bounded(&full[c % NBUF], (c / NBUF) & 1, &dummy, 1);
+            ptx::mbar_wait_bounded(&full[c % NBUF], (c / NBUF) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
     }
     (void)warp;
     // combine in a fixed (cell-major, full window last) order: H = - sum_q coef_q * L1_q
