@@ -10,15 +10,17 @@
 //
 // One persistent CTA per SM, 128-pixel tiles, warp-specialised:
 //   warp 0      TMA producer of the FP32 feature boxes (128 rows x 32 floats, 128B swizzle),
-//               five boxes in flight, plus L2 prefetch further ahead
+//               up to eight boxes in flight, plus L2 prefetch further ahead
 //   warp 14     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
 //               swizzle); separate from warp 0 so that feature loads never wait for MMAs
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 //   warps 2-9   converters: thread (h, r) owns pixel row r and the h-th 32-column box of
-//               every 64-column chunk; FP32 -> centred BF16 hi and lo planes written in the
-//               UMMA K-major 128B-swizzled layout; accumulates its part of ||x'||^2
+//               every 64-column chunk; FP32 -> centred BF16 hi and lo planes stored with
+//               tcgen05.st straight into tensor memory, where the MMA reads its A operand (row r
+//               in lane r, two K elements per 32-bit column), so the pixel planes never pass
+//               through shared memory; accumulates its part of ||x'||^2
 //   warps 10-13 epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
-//               flag push; the TMEM accumulator is double-buffered
+//               flag push; the TMEM accumulator is double-buffered when k <= 128
 // Every mbarrier wait is bounded: on timeout the CTA records VQNNF_ETIMEOUT in the device
 // error word, all roles leave their loops, in-flight copies and MMAs are drained (bounded)
 // and the tensor memory is released before the kernel returns.
@@ -38,19 +40,18 @@ __device__ int g_tc_error = 0;
 
 constexpr int TM = 128;            // pixels per tile (UMMA M)
 constexpr int KC = 64;             // K elements per chunk (128 bytes of BF16)
-constexpr int SF = 5;              // FP32 staging slots, one 16 KB box (32 columns) each
-constexpr int SA = 2;              // BF16 A-operand stages
-constexpr int NT = 480;            // 15 warps
+constexpr int kMaxSF = 8;          // FP32 staging slots, one 16 KB box (32 columns) each
+constexpr int kMaxSB = 4;          // centroid stages (hi and lo planes of one 64-column chunk)
+constexpr int kMaxSA = 4;          // BF16 A-operand stages (tensor memory, 64 columns each)
+constexpr int NT = 736;            // 23 warps
 constexpr int F32_BOX = TM * 32 * 4;       // 16 KB: 128 rows x 32 floats
-constexpr int A_TILE = TM * KC * 2;        // 16 KB: one BF16 plane of the pixel tile
-constexpr int A_STAGE = 2 * A_TILE;        // hi and lo planes
 constexpr double kU = 5.9604644775390625e-08;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 constexpr int PF = 8;              // chunks prefetched into L2 ahead of the loads
 
 struct TcArgs {
     long long n;
-    int D, k, npad, nkc, sb;
+    int D, k, npad, nkc, sb, sf, nb, sa, pf;
     long long ntiles;
     CodebookPrep p;
     uint8_t *labels;
@@ -134,15 +135,70 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accum)
+// D (+)= A . B^T with A (128 rows x 16 BF16) in tensor memory, B in shared memory.  ACC = false
+// overwrites D.  The issuing thread feeds the tensor pipe one MMA per 64 cycles at N = 128, so
+// the issue path is kept to the instruction itself.
+template <bool ACC>
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "n"(ACC ? 1 : 0)
         : "memory");
 }
+// One 64-column chunk: for each K step ks (A columns + 8 ks, B start field + 2 ks) the three
+// products x_hi.c_hi, x_hi.c_lo, x_lo.c_hi (A hi plane at a_hi, lo plane at a_hi + 32; B lo
+// plane blo_off descriptor units after the hi plane).  The first MMA overwrites D when acc == 0.
+// In the same instruction stream the next chunk's two barriers are tested without blocking,
+// so the test latency overlaps the MMAs; returns whether both phases had completed.
+__device__ __forceinline__ uint32_t tc_mma_chunk(uint32_t d, uint32_t a_hi, uint64_t bh, uint64_t blo_off,
+                                                 uint32_t idesc, uint32_t acc, uint32_t nbar_a, uint32_t npar_a,
+                                                 uint32_t nbar_b, uint32_t npar_b)
+{
+    uint32_t ready;
+    asm volatile(
+        "{\n"
+        " .reg .pred pa, pb, pacc, pt;\n"
+        " .reg .b32 a1, a2, a3, l0, l1, l2, l3;\n"
+        " .reg .b64 h1, h2, h3, o0, o1, o2, o3;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 pa, [%7], %8;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 pb, [%9], %10;\n"
+        " setp.ne.b32 pacc, %6, 0;\n"
+        " setp.eq.b32 pt, %6, %6;\n"
+        " add.u32 a1, %1, 8;\n add.u32 a2, %1, 16;\n add.u32 a3, %1, 24;\n"
+        " add.u32 l0, %1, 32;\n add.u32 l1, %1, 40;\n add.u32 l2, %1, 48;\n add.u32 l3, %1, 56;\n"
+        " add.u64 h1, %3, 2;\n add.u64 h2, %3, 4;\n add.u64 h3, %3, 6;\n"
+        " add.u64 o0, %3, %4;\n add.u64 o1, o0, 2;\n add.u64 o2, o0, 4;\n add.u64 o3, o0, 6;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [%1], %3, %5, pacc;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [%1], o0, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [l0], %3, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a1], h1, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a1], o1, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [l1], h1, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a2], h2, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a2], o2, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [l2], h2, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a3], h3, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [a3], o3, %5, pt;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%2], [l3], h3, %5, pt;\n"
+        " and.pred pa, pa, pb;\n"
+        " selp.u32 %0, 1, 0, pa;\n"
+        "}"
+        : "=r"(ready)
+        : "r"(a_hi), "r"(d), "l"(bh), "l"(blo_off), "r"(idesc), "r"(acc), "r"(nbar_a), "r"(npar_a), "r"(nbar_b),
+          "r"(npar_b)
+        : "memory");
+    return ready;
+}
+// 8 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const uint32_t *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 // 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float *v)
 {
@@ -194,46 +250,45 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int npad = g.npad, D = g.D, k = g.k, nkc = g.nkc, SB = g.sb;
+    const int npad = g.npad, D = g.D, k = g.k, nkc = g.nkc, SB = g.sb, SF = g.sf, NB = g.nb, SA = g.sa;
     const int B_PLANE = npad * 128;
     uint8_t *f32s = base;                                  // SF x 16 KB
-    uint8_t *as = f32s + SF * F32_BOX;                     // SA x 32 KB
-    uint8_t *bs = as + SA * A_STAGE;                       // SB x (hi, lo)
-    float *ca = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
-    float *cv = ca + npad;
-    float *cb = cv + npad;
-    float *cn = cb + npad;
-    float *mean = cn + npad;                               // roundup(D, 64)
-    float *norms = mean + nkc * KC;                        // [2 buf][2][128]
-    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 2 * TM);   // [128][8]
+    uint8_t *bs = f32s + SF * F32_BOX;                     // SB x (hi, lo)
+    float *cn = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
+    float4 *colc = reinterpret_cast<float4 *>(cn + npad);  // per column {||c*||^2, a, v, b}
+    float *mean = reinterpret_cast<float *>(colc + npad);  // roundup(D, 64)
+    float *norms = mean + nkc * KC;                        // [2 buf][4 quarters][128]
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 4 * TM);   // [128][8]
     uint64_t *bar = reinterpret_cast<uint64_t *>(maskbuf + TM * kMaskWords);
     uint64_t *full_f = bar, *empty_f = bar + SF, *a_full = bar + 2 * SF, *a_empty = bar + 2 * SF + SA;
-    uint64_t *full_b = bar + 2 * SF + 2 * SA, *empty_b = full_b + 2;
-    uint64_t *acc_full = empty_b + 2, *acc_empty = acc_full + 2, *nrm_full = acc_empty + 2,
+    uint64_t *full_b = bar + 2 * SF + 2 * SA, *empty_b = full_b + kMaxSB;
+    uint64_t *acc_full = empty_b + kMaxSB, *acc_empty = acc_full + 2, *nrm_full = acc_empty + 2,
              *nrm_empty = nrm_full + 2, *drain = nrm_empty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t tmem_cols = (2 * npad <= 32) ? 32 : (2 * npad <= 64) ? 64 : (2 * npad <= 128) ? 128
-                                                    : (2 * npad <= 256) ? 256 : 512;
+    // tensor memory: NB accumulator buffers of npad columns, then SA A-operand stages of 64
+    // columns (32 for the hi plane, 32 for the lo plane: two BF16 per 32-bit column)
+    const int a_col0 = NB * npad;
+    const int need = a_col0 + SA * 64;
+    const uint32_t tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 
     for (int j = tid; j < npad; j += NT) {
         const bool ok = j < k;
         const int jc = ok ? j : k - 1;
-        ca[j] = ok ? g.p.a[jc] : 0.f;
-        cv[j] = ok ? g.p.v[jc] : 0.f;
-        cb[j] = ok ? g.p.b[jc] : 0.f;
-        cn[j] = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
+        const float nrm = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
+        cn[j] = nrm;
+        colc[j] = make_float4(nrm, ok ? g.p.a[jc] : 0.f, ok ? g.p.v[jc] : 0.f, ok ? g.p.b[jc] : 0.f);
     }
     for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
     if (tid == 0) {
-        for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], TM); }
-        for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], 2 * TM); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], 2 * TM); }
+        for (int s = 0; s < SA; ++s) { mbar_init(&a_full[s], 4 * TM); mbar_init(&a_empty[s], 1); }
+        for (int s = 0; s < SB; ++s) { mbar_init(&full_b[s], 1); mbar_init(&empty_b[s], 1); }
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&full_b[s], 1); mbar_init(&empty_b[s], 1);
             mbar_init(&acc_full[s], 1); mbar_init(&acc_empty[s], TM);
-            mbar_init(&nrm_full[s], 2 * TM); mbar_init(&nrm_empty[s], TM);
+            mbar_init(&nrm_full[s], 4 * TM); mbar_init(&nrm_empty[s], TM);
         }
         mbar_init(drain, 1);
         *abort = 0;
@@ -254,10 +309,10 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     if (warp == 0) {
         // ---------------------------------------------------------- feature producer
         if (lane == 0) {
-            uint32_t ib = 0;                                  // box counter
+            uint32_t ib = 0, fs = 0, fp = 0;                  // box counter, its slot and phase parity
             bool ok = true;
-            long long last[SF];
-            for (int q = 0; q < SF; ++q) last[q] = -1;
+            long long last[kMaxSF];
+            for (int q = 0; q < kMaxSF; ++q) last[q] = -1;
             // L2 prefetch runs PF chunks ahead of the shared-memory loads
             long long pf_tile = blockIdx.x;
             int pf_kc = 0;
@@ -267,16 +322,16 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 tma_prefetch_2d(&tmA, pf_kc * KC + 32, (int)(pf_tile * TM));
                 if (++pf_kc == nkc) { pf_kc = 0; pf_tile += gridDim.x; }
             };
-            for (int q = 0; q < PF; ++q) prefetch_next();
+            for (int q = 0; q < g.pf; ++q) prefetch_next();
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
                 for (int kc = 0; ok && kc < nkc; ++kc) {
-                    prefetch_next();
+                    if (g.pf) prefetch_next();
                     for (int h = 0; h < 2; ++h, ++ib) {
-                        const int s = ib % SF;
-                        if (!(ok = mbar_wait(&empty_f[s], ((ib / SF) & 1) ^ 1, abort))) break;
-                        mbar_expect_tx(&full_f[s], F32_BOX);
-                        tma_load_2d(f32s + s * F32_BOX, &tmA, kc * KC + 32 * h, (int)(tile * TM), &full_f[s]);
-                        last[s] = ib;
+                        if (!(ok = mbar_wait(&empty_f[fs], fp ^ 1, abort))) break;
+                        mbar_expect_tx(&full_f[fs], F32_BOX);
+                        tma_load_2d(f32s + fs * F32_BOX, &tmA, kc * KC + 32 * h, (int)(tile * TM), &full_f[fs]);
+                        last[fs] = ib;
+                        if (++fs == SF) { fs = 0; fp ^= 1; }
                     }
                 }
             }
@@ -287,21 +342,21 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     if (last[q] >= 0) mbar_wait(&full_f[q], (uint32_t)((last[q] / SF) & 1), &no_abort);
             }
         }
-    } else if (warp == 14) {
+    } else if (warp == 22) {
         // ---------------------------------------------------------- centroid producer
         if (lane == 0) {
-            uint32_t itb = 0;
+            uint32_t itb = 0, sb = 0, pb = 0;
             bool ok = true;
-            long long last_b[2] = {-1, -1};
+            long long last_b[kMaxSB] = {-1, -1, -1, -1};
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
                 for (int kc = 0; kc < nkc; ++kc, ++itb) {
-                    const int sb = itb % SB;
-                    if (!(ok = mbar_wait(&empty_b[sb], ((itb / SB) & 1) ^ 1, abort))) break;
+                    if (!(ok = mbar_wait(&empty_b[sb], pb ^ 1, abort))) break;
                     mbar_expect_tx(&full_b[sb], 2 * B_PLANE);
                     uint8_t *bd = bs + sb * 2 * B_PLANE;
                     tma_load_2d(bd, &tmBhi, kc * KC, 0, &full_b[sb]);
                     tma_load_2d(bd + B_PLANE, &tmBlo, kc * KC, 0, &full_b[sb]);
                     last_b[sb] = itb;
+                    if (++sb == (uint32_t)SB) { sb = 0; pb ^= 1; }
                 }
             }
             if (!ok) {
@@ -314,31 +369,30 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = bf16_idesc(TM, npad);
-            uint32_t it = 0, itb = 0, tl = 0;
+            const uint32_t a_base = tmem_base + a_col0;
+            const uint64_t bdesc0 = sw128_desc(smem_u32(bs)), bstep = (uint64_t)((2 * B_PLANE) >> 4);
+            const uint64_t blo_off = (uint64_t)(B_PLANE >> 4);
+            uint32_t sa = 0, pa = 0, sb = 0, pb = 0, tl = 0;   // stage indices and phase parities
+            uint32_t ready = 0;                                // this chunk's barriers seen complete
             bool ok = true;
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
-                const uint32_t buf = tl & 1;
-                if (!(ok = mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort))) break;
+                const uint32_t buf = tl % NB;
+                if (!(ok = mbar_wait(&acc_empty[buf], ((tl / NB) & 1) ^ 1, abort))) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + buf * npad;
-                for (int kc = 0; kc < nkc; ++kc, ++it, ++itb) {
-                    const int sa = it % SA, sb = itb % SB;
-                    if (!(ok = mbar_wait(&a_full[sa], (it / SA) & 1, abort))) break;
-                    if (!(ok = mbar_wait(&full_b[sb], (itb / SB) & 1, abort))) break;
-                    tc_fence_after();
-                    const uint32_t a0 = smem_u32(as + sa * A_STAGE);
-                    const uint32_t b0 = smem_u32(bs + sb * 2 * B_PLANE);
-#pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint64_t ahi = sw128_desc(a0 + ks * 32);
-                        const uint64_t alo = sw128_desc(a0 + A_TILE + ks * 32);
-                        const uint64_t bhi = sw128_desc(b0 + ks * 32);
-                        tc_mma(d_tmem, ahi, bhi, idesc, (kc | ks) != 0);
-                        tc_mma(d_tmem, ahi, sw128_desc(b0 + B_PLANE + ks * 32), idesc, 1u);
-                        tc_mma(d_tmem, alo, bhi, idesc, 1u);
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (!ready) {
+                        if (!(ok = mbar_wait(&a_full[sa], pa, abort))) break;
+                        if (!(ok = mbar_wait(&full_b[sb], pb, abort))) break;
                     }
+                    tc_fence_after();
+                    const uint32_t nsa = sa + 1 == (uint32_t)SA ? 0 : sa + 1, npa = nsa ? pa : pa ^ 1;
+                    const uint32_t nsb = sb + 1 == (uint32_t)SB ? 0 : sb + 1, npb = nsb ? pb : pb ^ 1;
+                    ready = tc_mma_chunk(d_tmem, a_base + sa * 64, bdesc0 + (uint64_t)sb * bstep, blo_off, idesc,
+                                         kc != 0, smem_u32(&a_full[nsa]), npa, smem_u32(&full_b[nsb]), npb);
                     tc_commit(&a_empty[sa]);
                     tc_commit(&empty_b[sb]);
+                    sa = nsa; pa = npa; sb = nsb; pb = npb;
                 }
                 if (ok) tc_commit(&acc_full[buf]);
             }
@@ -347,94 +401,110 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             volatile int no_abort = 0;
             mbar_wait(drain, 0, &no_abort);
         }
-    } else if (warp >= 2 && warp < 10) {
+    } else if (warp >= 2 && warp < 18) {
         // ---------------------------------------------------------- converters
-        const int ct = tid - 64;
-        const int r = ct & (TM - 1);             // pixel row of the tile
-        const int h = ct >> 7;                   // 32-column box of each chunk this thread converts
+        const int grp = warp & 3;                 // TMEM lane group this warp may write
+        const int r = grp * 32 + lane;            // pixel row of the tile
+        const int qt = (warp - 2) >> 2;           // 16-column quarter of each chunk this thread converts
+        const int h = qt >> 1;                    // its 32-column box
         const int sw = r & 7;
-        uint32_t it = 0, tl = 0;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(grp * 32) << 16);
+        // A stage and its parity; this thread's box is number 2 it + h of the feature producer,
+        // so its slot advances by two per chunk
+        uint32_t sa = 0, pa = 0, sf = h, pf = 0, tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
-            const uint32_t buf = tl & 1;
-            float xa2 = 0.f, xb2 = 0.f;                     // partial ||x'||^2 of this half
-            for (int kc = 0; kc < nkc; ++kc, ++it) {
-                const int sa = it % SA;
-                const uint32_t ib = 2 * it + h;             // box counter of the feature producer
-                const int sf = ib % SF;
-                ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], ((it / SA) & 1) ^ 1, abort));
-                ok = __all_sync(0xffffffffu, ok && mbar_wait(&full_f[sf], (ib / SF) & 1, abort));
+            const uint32_t nb = tl & 1;
+            float xa2 = 0.f, xb2 = 0.f;                     // partial ||x'||^2 of this quarter
+            for (int kc = 0; kc < nkc; ++kc) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], pa ^ 1, abort));
+                ok = __all_sync(0xffffffffu, ok && mbar_wait(&full_f[sf], pf, abort));
                 if (!ok) break;
+                tc_fence_after();
                 const uint8_t *box = f32s + sf * F32_BOX + r * 128;
-                uint8_t *arow = as + sa * A_STAGE + (r >> 3) * 1024 + (r & 7) * 128;
+                // the quarter's 16 floats of row r (two 8-column groups of the 128B-swizzled box)
+                float4 v[4];
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    const int c = 4 * h + cc;                // 16-byte group of the 128-byte BF16 row
-                    const int d0 = kc * KC + c * 8;
-                    uint4 w = make_uint4(0u, 0u, 0u, 0u), wl = w;
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int cb = 2 * (qt & 1) + cc;
+                    v[2 * cc] = *reinterpret_cast<const float4 *>(box + (((2 * cb) ^ sw) << 4));
+                    v[2 * cc + 1] = *reinterpret_cast<const float4 *>(box + (((2 * cb + 1) ^ sw) << 4));
+                }
+                mbar_arrive(&empty_f[sf]);       // release orders the reads above before the box is refilled
+                uint32_t hw[8], lw[8];
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int d0 = kc * KC + 16 * qt + 8 * cc;
                     if (d0 < D) {                            // D % 16 == 0: all 8 columns valid
-                        const float4 v0 = *reinterpret_cast<const float4 *>(box + (((2 * cc) ^ sw) << 4));
-                        const float4 v1 = *reinterpret_cast<const float4 *>(box + (((2 * cc + 1) ^ sw) << 4));
                         const float4 m0 = *reinterpret_cast<const float4 *>(mean + d0);
                         const float4 m1 = *reinterpret_cast<const float4 *>(mean + d0 + 4);
+                        const float4 v0 = v[2 * cc], v1 = v[2 * cc + 1];
                         const float xs[8] = {v0.x - m0.x, v0.y - m0.y, v0.z - m0.z, v0.w - m0.w,
                                              v1.x - m1.x, v1.y - m1.y, v1.z - m1.z, v1.w - m1.w};
-                        uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const float xa = xs[2 * q], xb = xs[2 * q + 1];
                             float ha, hb, la, lb;
-                            hw[q] = pack_bf16(xa, xb, ha, hb);
+                            hw[4 * cc + q] = pack_bf16(xa, xb, ha, hb);
                             xa2 = fmaf(xa, xa, xa2);
                             xb2 = fmaf(xb, xb, xb2);
-                            lw[q] = pack_bf16(xa - ha, xb - hb, la, lb);   // exact residuals
+                            lw[4 * cc + q] = pack_bf16(xa - ha, xb - hb, la, lb);   // exact residuals
                         }
-                        w = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        wl = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) hw[4 * cc + q] = lw[4 * cc + q] = 0u;
                     }
-                    *reinterpret_cast<uint4 *>(arow + ((c ^ sw) << 4)) = w;
-                    *reinterpret_cast<uint4 *>(arow + A_TILE + ((c ^ sw) << 4)) = wl;
                 }
-                mbar_arrive(&empty_f[sf]);                   // this box has been read
-                fence_proxy_async();
+                const uint32_t col = lane_base + a_col0 + sa * 64 + 8 * qt;
+                tc_st8(col, hw);
+                tc_st8(col + 32, lw);
+                tc_wait_st();
+                tc_fence_before();
                 mbar_arrive(&a_full[sa]);
+                if (++sa == (uint32_t)SA) { sa = 0; pa ^= 1; }
+                sf += 2;
+                if (sf >= (uint32_t)SF) { sf -= SF; pf ^= 1; }
             }
             if (!ok) break;
-            ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[buf], ((tl >> 1) & 1) ^ 1, abort));
+            ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[nb], ((tl >> 1) & 1) ^ 1, abort));
             if (!ok) break;
-            norms[(buf * 2 + h) * TM + r] = xa2 + xb2;
-            mbar_arrive(&nrm_full[buf]);
+            norms[(nb * 4 + qt) * TM + r] = xa2 + xb2;
+            mbar_arrive(&nrm_full[nb]);
         }
-    } else if (warp >= 10 && warp < 14) {
+    } else if (warp >= 18 && warp < 22) {
         // ---------------------------------------------------------- epilogue
         const int grp = warp & 3;                 // TMEM lane group this warp may read
         const int r = grp * 32 + lane;
         const float u = (float)kU;
+        const float u4 = 4.0f * u;
         const float infl = 1.0f + 0.00390625f;
+        // largest a_j, v_j, b_j and ||c_j*||^2 of the codebook: Bmax below bounds every B_j of a pixel
         float amax_s = 0.f, vmax_s = 0.f, bmax_s = 0.f, nrm_max = 0.f;
         for (int j = 0; j < k; ++j) {
-            amax_s = fmaxf(amax_s, ca[j]);
-            vmax_s = fmaxf(vmax_s, cv[j]);
-            bmax_s = fmaxf(bmax_s, cb[j]);
-            nrm_max = fmaxf(nrm_max, cn[j]);
+            const float4 c = colc[j];
+            nrm_max = fmaxf(nrm_max, c.x);
+            amax_s = fmaxf(amax_s, c.y);
+            vmax_s = fmaxf(vmax_s, c.z);
+            bmax_s = fmaxf(bmax_s, c.w);
         }
         const float cnorm_max = sqrtf(nrm_max) * 1.0001f;    // max ||c_j*|| (cn = ||c*||^2 in FP32)
         nrm_max *= 1.0001f;
         uint32_t tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
-            const uint32_t buf = tl & 1, ph = (tl >> 1) & 1;
+            const uint32_t buf = tl % NB, ph = (tl / NB) & 1, nb = tl & 1, nph = (tl >> 1) & 1;
             ok = mbar_wait(&acc_full[buf], ph, abort);
-            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[buf], ph, abort));
+            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[nb], nph, abort));
             if (!ok) break;
             tc_fence_after();
             // ||x_hi|| <= (1 + 2^-8) ||x'||  and  ||x' - x_hi - x_lo|| <= 2^-16 ||x'||  (two
             // round-to-nearest BF16 roundings, each within 2^-8 relative)
-            const float x2 = norms[(buf * 2 + 0) * TM + r] + norms[(buf * 2 + 1) * TM + r];
+            const float x2 = (norms[(nb * 4 + 0) * TM + r] + norms[(nb * 4 + 1) * TM + r]) +
+                             (norms[(nb * 4 + 2) * TM + r] + norms[(nb * 4 + 3) * TM + r]);
             const float nx = sqrtf(x2) * (1.0f + (float)(D + 8) * u);
             const float X = nx * (1.0f + 0.00390625f);
             const float Dl = nx * 1.5318e-05f + 1e-30f;      // 2^-16 * 1.004
-            mbar_arrive(&nrm_empty[buf]);
+            mbar_arrive(&nrm_empty[nb]);
             const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
             const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
             // pass 1: smallest score, lowest column on ties, as four interleaved running minima.
@@ -455,35 +525,40 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
 #pragma unroll
             for (int q = 1; q < 4; ++q)
                 if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
-            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
-            // contraction's own error, so Bmax covers every column's 4u|s_j| term
-            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
-            const float Bmax = fmaf(X, amax_s, fmaf(Y, vmax_s, bmax_s + 4.0f * u * smax_abs)) * infl;
             // U, the upper end of column amin's interval, bounds the smallest distance from
-            // above, so the nearest column j has s_j - B_j <= U and s_j <= U + Bmax.  The
-            // prefilter limit U + 2 Bmax leaves room for the rounding of that sum (u |U| is
-            // below Bmax / 2 because Bmax >= 4u |smin|): only columns under it get their own B_j.
-            const float Ba = fmaf(X, ca[amin], fmaf(Y, cv[amin], cb[amin] + 4.0f * u * fabsf(smin))) * infl;
-            const float U = smin + Ba;
+            // above, so the nearest column j has s_j - B_j <= U.
+            const float4 ca = colc[amin];
+            const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the contraction's
+            // own error, so Bmax >= every B_j of this pixel (the float evaluation is monotone).  The
+            // nearest column has s_j <= U + B_j <= U + Bmax; the limit U + 2 Bmax also covers the
+            // rounding of that sum (u |U| < Bmax / 2 because Bmax >= 4u |smin|).  A 32-column block
+            // where no lane has a column under the limit besides amin needs no per-column interval
+            // test: its only candidate is amin.
+            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
+            const float Bmax = fmaf(X, amax_s, fmaf(Y, vmax_s, fmaf(u4, smax_abs, bmax_s))) * infl;
             const float lim = U + 2.0f * Bmax;
             int cnt = 0, last = amin;
             for (int c0 = 0; c0 < npad; c0 += 32) {
                 float v[32];
                 tc_ld32(taddr + c0, v);
-                uint32_t word = 0;
+                uint32_t maybe = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
-                    const float s = fmaf(-2.0f, v[j], cn[col]);
-                    if (s <= lim) {
-                        const float B = fmaf(X, ca[col], fmaf(Y, cv[col], cb[col] + 4.0f * u * fabsf(s))) * infl;
-                        if (s - B <= U) {
-                            ++cnt;
-                            last = col;
-                            word |= 1u << j;
-                        }
+                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
+                const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                uint32_t word = own;
+                if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
+                    word = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float4 c = colc[c0 + j];
+                        const float s = fmaf(-2.0f, v[j], c.x);
+                        const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(s), c.w))) * infl;
+                        word |= (uint32_t)(s - B <= U) << j;
                     }
                 }
+                cnt += __popc(word);
+                if (word) last = c0 + 31 - __clz(word);
                 maskbuf[r * kMaskWords + (c0 >> 5)] = word;
             }
 
@@ -554,14 +629,14 @@ cudaError_t make_map(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, ui
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t tc_smem_bytes(int npad, int D, int sb)
+size_t tc_smem_bytes(int npad, int D, int sb, int sf)
 {
     const int nkc = (D + KC - 1) / KC;
     size_t b = 1024;                                       // alignment slack
-    b += (size_t)SF * F32_BOX + (size_t)SA * A_STAGE + (size_t)sb * 2 * npad * 128;
-    b += sizeof(float) * (4 * (size_t)npad + (size_t)nkc * KC + 4 * TM);
+    b += (size_t)sf * F32_BOX + (size_t)sb * 2 * npad * 128;
+    b += sizeof(float) * (5 * (size_t)npad + (size_t)nkc * KC + 8 * TM);
     b += sizeof(uint32_t) * TM * kMaskWords;
-    b += sizeof(uint64_t) * (2 * SF + 2 * SA + 12 + 1) + 16;   // barriers, TMEM slot, abort flag
+    b += sizeof(uint64_t) * (2 * sf + 2 * kMaxSA + 2 * kMaxSB + 8 + 1) + 16;   // barriers, TMEM slot, abort flag
     return b;
 }
 
@@ -578,13 +653,18 @@ cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int npad = (k + 31) / 32 * 32;      // UMMA N (multiple of 16) and whole 32-column TMEM loads
-    int sb = 2;
-    size_t smem = tc_smem_bytes(npad, D, sb);
-    if (smem > (size_t)optin) {
-        sb = 1;
-        smem = tc_smem_bytes(npad, D, sb);
-    }
-    if (smem > (size_t)optin) return cudaErrorNotSupported;
+    // centroid stages (the codebook is streamed from L2 by every CTA) and feature boxes (HBM
+    // latency): the first split that fits
+    static const int kSplit[][2] = {{3, 6}, {2, 8}, {2, 6}, {2, 4}, {1, 4}};
+    int sb = 0, sf = 0;
+    size_t smem = 0;
+    for (const auto &c : kSplit)
+        if ((smem = tc_smem_bytes(npad, D, c[0], c[1])) <= (size_t)optin) { sb = c[0]; sf = c[1]; break; }
+    if (!sf) return cudaErrorNotSupported;
+    // accumulators double-buffered when they fit beside two A stages in the 512 TMEM columns;
+    // the remaining columns hold as many A stages as fit (at most four)
+    const int nb = 2 * npad + 2 * 64 <= 512 ? 2 : 1;
+    const int sa = (512 - nb * npad) / 64 < kMaxSA ? (512 - nb * npad) / 64 : kMaxSA;
     CUtensorMap tmA, tmBhi, tmBlo;
     if ((e = make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)D, (uint64_t)n, (uint64_t)D * 4, 32,
                       TM)) != cudaSuccess)
@@ -602,6 +682,10 @@ cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const 
     a.npad = npad;
     a.nkc = (D + KC - 1) / KC;
     a.sb = sb;
+    a.sf = sf;
+    a.nb = nb;
+    a.sa = sa;
+    a.pf = PF;
     a.ntiles = (n + TM - 1) / TM;
     a.p = p;
     a.labels = labels;
