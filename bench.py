@@ -11,6 +11,10 @@ Inputs are generated on the device from fixed seeds and stay resident (8 GiB of 
 larger than L2, so no flush is needed between steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32] [--impl reference]
+                  [--query-size S] [--no-compare] [--no-e2e] [--no-cpu-baseline]
+
+``--query-size`` shrinks the query to S x S (for profiler captures of the same kernels on a
+smaller case); the bench line itself is quoted on the default 2048.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on bounded
 samples of the same workload instead.
@@ -45,9 +49,11 @@ def _peaks():
 
 
 class Clocks:
-    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    """Samples nvidia-smi clocks and throttle reasons (every 50 ms, timestamped) from before the
+    warm-up to after the timed region; ``summary(t0, t1)`` keeps the samples taken inside the
+    timed region [t0, t1] (host wall clock)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -61,7 +67,7 @@ class Clocks:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -75,7 +81,17 @@ class Clocks:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(stamp, fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
+    def summary(self, t0=None, t1=None):
         if self.proc is None or self.tmp is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.tmp.flush()
@@ -83,18 +99,24 @@ class Clocks:
         with open(self.tmp.name) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
+                if len(parts) >= 10:
                     rows.append(parts)
         os.unlink(self.tmp.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        inside = rows
+        window = "whole run"
+        if t0 is not None:
+            sel = [r for r in rows if (w := self._when(r[0])) is not None and t0 - 0.05 <= w <= t1 + 0.05]
+            if sel:
+                inside, window = sel, "timed region"
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in inside if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        reasons = sorted({names[i] for r in inside for i in range(4) if r[6 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(inside), "window": window}
 
 
 def make_workload(dev, cfg):
@@ -175,10 +197,14 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     cfg = dict(HEADLINE)
+    if args.query_size != cfg["H"]:
+        cfg["n_sp"] = max(64, cfg["n_sp"] * args.query_size ** 2 // cfg["H"] ** 2)
+        cfg["H"] = cfg["W"] = args.query_size
     q, T, info, bank = make_workload(dev, cfg)
     X = q.X
     s = torch.cuda.Stream(device=dev)
     pipe = Pipeline(vq, X, T, cfg, bank, args.prec, s)
+    clk = Clocks(local).__enter__()
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
             pipe.step()
@@ -191,13 +217,16 @@ def run_gpu(args, rank, world):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        start.record(s)
-        with torch.cuda.stream(s):
-            for i in range(K):
-                pipe.step(evs[i])
-        stop.record(s)
-        torch.cuda.synchronize()
+    t_on = time.time()
+    start.record(s)
+    with torch.cuda.stream(s):
+        for i in range(K):
+            pipe.step(evs[i])
+    stop.record(s)
+    torch.cuda.synchronize()
+    t_off = time.time()
+    time.sleep(0.1)
+    clk.__exit__()
     ms = start.elapsed_time(stop) / K
     if world > 1:
         import torch.distributed as dist
@@ -209,26 +238,28 @@ def run_gpu(args, rank, world):
                     for e in evs]).mean(0)
     stats = pipe.stats.cpu().tolist()
     am = pipe.am.cpu().tolist()
-    clocks = clk.summary()
+    clocks = clk.summary(t_on, t_off)
 
     # the other precision on the same inputs, same GPU, for the BF16-vs-FP32 comparison
     other = "fp32" if args.prec == "bf16" else "bf16"
-    pipe2 = Pipeline(vq, X, T, cfg, bank, other, s)
-    with torch.cuda.stream(s):
-        for _ in range(args.warmup):
-            pipe2.step()
-    torch.cuda.synchronize()
-    st2 = torch.cuda.Event(enable_timing=True)
-    sp2 = torch.cuda.Event(enable_timing=True)
-    st2.record(s)
-    with torch.cuda.stream(s):
-        for i in range(K):
-            pipe2.step()
-    sp2.record(s)
-    torch.cuda.synchronize()
-    ms2 = st2.elapsed_time(sp2) / K
-    same_labels = bool(torch.equal(pipe.ql, pipe2.ql))
-    del pipe2
+    ms2, same_labels = None, None
+    if not args.no_compare:
+        pipe2 = Pipeline(vq, X, T, cfg, bank, other, s)
+        with torch.cuda.stream(s):
+            for _ in range(args.warmup):
+                pipe2.step()
+        torch.cuda.synchronize()
+        st2 = torch.cuda.Event(enable_timing=True)
+        sp2 = torch.cuda.Event(enable_timing=True)
+        st2.record(s)
+        with torch.cuda.stream(s):
+            for i in range(K):
+                pipe2.step()
+        sp2.record(s)
+        torch.cuda.synchronize()
+        ms2 = st2.elapsed_time(sp2) / K
+        same_labels = bool(torch.equal(pipe.ql, pipe2.ql))
+        del pipe2
 
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev)
@@ -244,7 +275,7 @@ def run_gpu(args, rank, world):
         "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
-        "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
+        "config": {"workload": f"{cfg['H']}x{cfg['W']} query, D=512, k=128, 128x128 template, F=10 "
                                "(full + 3x3), 10 Lloyd steps; whole hot path per step",
                    "prec": args.prec, "query_px": L, "l2": "inputs larger than L2 (8 GiB features)",
                    "parallelism": f"replicas x{world}"},
@@ -253,10 +284,11 @@ def run_gpu(args, rank, world):
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "clocks": clocks, "e2e": e2e,
-        f"{other}_path": {"value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
-                          "ms_per_step": round(ms2, 4),
-                          "speedup_bf16_over_fp32": round((ms2 / ms) if other == "fp32" else (ms / ms2), 3),
-                          "labels_identical": same_labels},
+        f"{other}_path": None if ms2 is None else {
+            "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+            "ms_per_step": round(ms2, 4),
+            "speedup_bf16_over_fp32": round((ms2 / ms) if other == "fp32" else (ms / ms2), 3),
+            "labels_identical": same_labels},
         "gpu_launches": kernels_per_step(cfg, args.prec) * K,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -383,13 +415,17 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--query-size", type=int, default=HEADLINE["H"],
+                    help="query side (profiling captures on a smaller case)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other precision on the same inputs")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))

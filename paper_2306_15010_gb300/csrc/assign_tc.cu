@@ -430,7 +430,6 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     v[2 * cc] = *reinterpret_cast<const float4 *>(box + (((2 * cb) ^ sw) << 4));
                     v[2 * cc + 1] = *reinterpret_cast<const float4 *>(box + (((2 * cb + 1) ^ sw) << 4));
                 }
-                mbar_arrive(&empty_f[sf]);       // release orders the reads above before the box is refilled
                 uint32_t hw[8], lw[8];
 #pragma unroll
                 for (int cc = 0; cc < 2; ++cc) {
@@ -455,6 +454,10 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                         for (int q = 0; q < 4; ++q) hw[4 * cc + q] = lw[4 * cc + q] = 0u;
                     }
                 }
+                // the box is released only once its values have been consumed: an arrive issued
+                // right after the shared-memory loads let the next TMA copy overwrite the box
+                // before those loads had returned (wrong labels at full size)
+                mbar_arrive(&empty_f[sf]);
                 const uint32_t col = lane_base + a_col0 + sa * 64 + 8 * qt;
                 tc_st8(col, hw);
                 tc_st8(col + 32, lw);

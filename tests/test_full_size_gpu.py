@@ -1,0 +1,101 @@
+"""The whole path at the headline size (2048 x 2048 query, D = 512, k = 128, 128 x 128
+template, F = 10), run the way bench.py times it, against the FP64 oracle on what the
+oracle can compute one by one.
+
+* codebook: bit-identical to the oracle's fit of the same template (BF16 and FP32 paths);
+* template labels: every pixel against the oracle (outside the 1e-6 near-tie band);
+* query labels: BF16 == FP32 on every pixel outside the band, and both against the oracle on
+  a seeded sample plus every pixel where the two paths disagree;
+* template counts: exact; heatmap: sampled windows against the oracle's score of the GPU
+  labels within 1e-5 of max |H|, and the reported argmax is a maximum of the heatmap.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    from paper_2306_15010_gb300 import build
+    build.build()
+    import paper_2306_15010_gb300 as vq
+    import bench
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cfg = dict(bench.HEADLINE)
+    q, T, info, bank = bench.make_workload(dev, cfg)
+    s = torch.cuda.Stream(device=dev)
+    out = {}
+    for prec in ("bf16", "fp32"):
+        pipe = bench.Pipeline(vq, q.X, T, cfg, bank, prec, s)
+        with torch.cuda.stream(s):
+            pipe.step()
+            pipe.step()
+        torch.cuda.synchronize()
+        assert vq.vqnnf_last_device_error() == 0
+        out[prec] = {k: getattr(pipe, k).clone() for k in ("C", "tl", "ql", "tc", "heat", "am")}
+        del pipe
+    return cfg, q, T, bank, out
+
+
+def test_codebook_bit_exact(run):
+    cfg, q, T, bank, out = run
+    C_ref = oracle.fit_codebook(T.cpu().numpy(), cfg["k"], cfg["iters"], cfg["fit_seed"])
+    for prec in ("bf16", "fp32"):
+        assert np.array_equal(out[prec]["C"].cpu().numpy(), C_ref), prec
+
+
+def test_template_labels_and_counts(run):
+    cfg, q, T, bank, out = run
+    C = out["fp32"]["C"].cpu().numpy()
+    ref, d1, d2 = oracle.assign(T.cpu().numpy(), C, return_dist=True)
+    band = oracle.relative_gap(d1, d2) < 1e-6
+    for prec in ("bf16", "fp32"):
+        got = out[prec]["tl"].cpu().numpy().astype(np.int32)
+        assert int(((got != ref) & ~band).sum()) == 0, prec
+        tc = oracle.filter_counts(got, cfg["k"], bank)
+        assert np.array_equal(out[prec]["tc"].cpu().numpy(), tc), prec
+
+
+def test_query_labels(run):
+    cfg, q, T, bank, out = run
+    C = out["fp32"]["C"].cpu().numpy()
+    lb = out["bf16"]["ql"].view(-1)
+    lf = out["fp32"]["ql"].view(-1)
+    diff = (lb != lf).nonzero().view(-1)
+    rng = np.random.default_rng(7)
+    sample = torch.as_tensor(rng.choice(lb.numel(), 4096, replace=False), device=lb.device)
+    idx = torch.unique(torch.cat([diff[:20000], sample]))
+    X = q.X.view(-1, cfg["D"])[idx].cpu().numpy()
+    ref, d1, d2 = oracle.assign(X[None], C, return_dist=True)
+    ref, band = ref[0], (oracle.relative_gap(d1, d2) < 1e-6)[0]
+    for name, lab in (("bf16", lb), ("fp32", lf)):
+        got = lab[idx].cpu().numpy().astype(np.int32)
+        assert int(((got != ref) & ~band).sum()) == 0, name
+    # every disagreement between the two paths lies in the near-tie band
+    assert diff.numel() <= 20000
+    in_diff = torch.isin(idx, diff).cpu().numpy()
+    assert bool(band[in_diff].all())
+
+
+def test_heatmap_sampled_windows(run):
+    cfg, q, T, bank, out = run
+    k, th, tw = cfg["k"], cfg["th"], cfg["tw"]
+    for prec in ("bf16", "fp32"):
+        ql = out[prec]["ql"].cpu().numpy().astype(np.int32)
+        tc = out[prec]["tc"].cpu().numpy()
+        heat = out[prec]["heat"]
+        HO, WO = heat.shape
+        rng = np.random.default_rng(11)
+        win = np.stack([rng.integers(0, HO, 256), rng.integers(0, WO, 256)], 1)
+        am = out[prec]["am"].cpu().numpy()
+        win = np.concatenate([win, am[None]], 0)
+        ref = oracle.score_at(ql, k, bank, tc, win)
+        got = heat.cpu().numpy()[win[:, 0], win[:, 1]]
+        scale = float(heat.abs().max())
+        assert np.max(np.abs(got - ref)) <= 1e-5 * scale, prec
+        assert float(heat[am[0], am[1]]) == float(heat.max()), prec
