@@ -36,6 +36,16 @@ sys.path.insert(0, ROOT)
 HEADLINE = dict(H=2048, W=2048, D=512, k=128, th=128, tw=128, grid=3, iters=10, M=128,
                 n_sp=20000, q_seed=1001, t_seed=2001, fit_seed=3001)
 METRIC = "query Mpix/s at 2048^2, D=512, k=128: BF16 vs FP32 path, % of roofline"
+OP_ASSIGN, OP_SCORE = 1, 3
+
+# DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum), from the ncu capture summarised in
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,196,549,000 + 5,988,608 bytes),
+# scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
+# it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
+TC_TRAFFIC_PER_PX = (2196549000 + 5988608) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "1fc4d73920c77bde8ae08ba47f47877cfc16e80949355b4330ab3f35ae80ef32"
+
 
 
 def _peaks():
@@ -119,6 +129,22 @@ class Clocks:
                 "samples": len(inside), "window": window}
 
 
+def reduce_max_ms(ms: float, device="cpu") -> float:
+    """The job's step time: the maximum of the ranks' step times (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms: float, world: int, query_px: int) -> float:
+    """Whole-job throughput in Mpix/s: every rank processes one query per step (weak scaling)."""
+    return world * query_px / (ms * 1e-3) / 1e6
+
+
 def make_workload(dev, cfg):
     import synth
     q = synth.query_map(cfg["H"], cfg["W"], cfg["D"], M=cfg["M"], n_sp=cfg["n_sp"],
@@ -149,7 +175,10 @@ class Pipeline:
         self.am = torch.empty(2, dtype=torch.int32, device=dev)
         self.stats = torch.zeros(4, dtype=torch.int64, device=dev)
 
-    def step(self, ev=None):
+    def step(self, ev=None, kev=None):
+        """One pass of the hot path.  ev: 4 events marking the segment boundaries; kev: 4 events
+        recorded by the library immediately around the query's contraction kernel and the
+        score kernel (vqnnf_set_kernel_events)."""
         vq, c, s = self.vq, self.cfg, self.s
         if ev is not None:
             ev[0].record(s)
@@ -159,12 +188,20 @@ class Pipeline:
         vq.vqnnf_filter_responses(self.tl, c["k"], self.bank, counts=self.tc, stream=s)
         if ev is not None:
             ev[1].record(s)
+        if kev is not None:
+            vq.vqnnf_set_kernel_events(OP_ASSIGN, kev[0], kev[1])
         vq.vqnnf_assign(self.X, self.C, self.prec, labels=self.ql, stats=self.stats,
                         ws=self.ws_a, stream=s)
+        if kev is not None:
+            vq.vqnnf_set_kernel_events(OP_ASSIGN, None, None)
         if ev is not None:
             ev[2].record(s)
+        if kev is not None:
+            vq.vqnnf_set_kernel_events(OP_SCORE, kev[2], kev[3])
         vq.vqnnf_score(self.ql, c["k"], c["th"], c["tw"], self.bank, self.tc, heatmap=self.heat,
                        argmax_yx=self.am, ws=self.ws_s, stream=s)
+        if kev is not None:
+            vq.vqnnf_set_kernel_events(OP_SCORE, None, None)
         if ev is not None:
             ev[3].record(s)
 
@@ -211,6 +248,10 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    kevs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for kv in kevs:                      # create the CUDA events the library records into
+        for e in kv:
+            e.record(s)
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -221,7 +262,7 @@ def run_gpu(args, rank, world):
     start.record(s)
     with torch.cuda.stream(s):
         for i in range(K):
-            pipe.step(evs[i])
+            pipe.step(evs[i], kevs[i])
     stop.record(s)
     torch.cuda.synchronize()
     t_off = time.time()
@@ -230,12 +271,11 @@ def run_gpu(args, rank, world):
     ms = start.elapsed_time(stop) / K
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = reduce_max_ms(ms, dev)
         dist.barrier()
     seg = np.array([[e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])]
                     for e in evs]).mean(0)
+    kern = np.array([[kv[0].elapsed_time(kv[1]), kv[2].elapsed_time(kv[3])] for kv in kevs]).mean(0)
     stats = pipe.stats.cpu().tolist()
     am = pipe.am.cpu().tolist()
     clocks = clk.summary(t_on, t_off)
@@ -267,9 +307,10 @@ def run_gpu(args, rank, world):
     if rank != 0:
         return None
     L = cfg["H"] * cfg["W"]
-    value = world * L / (ms * 1e-3) / 1e6
+    value = job_value(ms, world, L)
     peaks, peak_src = _peaks()
-    roof = roofline(cfg, args.prec, seg[1], peaks, peak_src)
+    roof = roofline(cfg, args.prec, kern[0], peaks, peak_src)
+    roof_score = roofline_score(cfg, kern[1], peaks)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpix/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -281,9 +322,12 @@ def run_gpu(args, rank, world):
                    "parallelism": f"replicas x{world}"},
         "segments_ms": {"template_side": round(seg[0], 4), "query_assign": round(seg[1], 4),
                         "query_score": round(seg[2], 4)},
+        "kernels_ms": {"query_contraction": round(float(kern[0]), 4), "score": round(float(kern[1]), 4)},
+        "query_only": {"value": round(world * L / ((seg[1] + seg[2]) * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+                       "note": "query assign + integral image + score per query, template side amortised"},
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
-        "roofline": roof, "clocks": clocks, "e2e": e2e,
+        "roofline": roof, "roofline_score": roof_score, "clocks": clocks, "e2e": e2e,
         f"{other}_path": None if ms2 is None else {
             "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
             "ms_per_step": round(ms2, 4),
@@ -296,25 +340,53 @@ def run_gpu(args, rank, world):
     return line
 
 
-def roofline(cfg, prec, assign_ms, peaks, src):
+def _tc_traffic(L):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2306_15010_gb300", "csrc", "assign_tc.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return round(TC_TRAFFIC_PER_PX * L) if sha == TC_TRAFFIC_SRC_SHA256 else None
+
+
+def roofline(cfg, prec, kernel_ms, peaks, src):
+    """The dominant kernel, the query's distance contraction, timed alone (library events)."""
     L, D, k = cfg["H"] * cfg["W"], cfg["D"], cfg["k"]
     if prec == "bf16":
         # HBM-bound: the contraction must read every FP32 feature once and write a label
         bytes_ = L * (D * 4 + 1)
-        ach = bytes_ / (assign_ms * 1e-3) / 1e9
+        ach = bytes_ / (kernel_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(ach / peak, 4), "traffic": None,
-                "kernel": "query assign call: codebook prep + tcgen05 contraction + re-scoring",
-                "algorithmic_bytes_per_px": D * 4 + 1, "peak_source": src}
+                "frac": round(ach / peak, 4), "traffic": _tc_traffic(L),
+                "kernel": "assign_tc_kernel (tcgen05 BF16 contraction + interval test), query launch",
+                "kernel_ms": round(float(kernel_ms), 4),
+                "algorithmic_bytes_per_px": D * 4 + 1, "peak_source": src + " (burst copy)"}
     # FP32 SIMT: bound by the FP32 FMA pipes, 152 SMs x 128 lanes x 2 flop x max SM clock
     flops = 2.0 * L * D * k
-    ach = flops / (assign_ms * 1e-3) / 1e12
+    ach = flops / (kernel_ms * 1e-3) / 1e12
     peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "TFLOP/s",
             "frac": round(ach / peak, 4), "traffic": None,
-            "kernel": "query assign (FP32 SIMT contraction + re-scoring)",
+            "kernel": "assign_fp32_kernel (FP32 SIMT contraction), query launch",
+            "kernel_ms": round(float(kernel_ms), 4),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+
+
+def roofline_score(cfg, kernel_ms, peaks):
+    """Score kernel: integer ALU work of Eq. 2 over the integral image, per window and cluster
+    for a g x g grid + full window bank: (g+1)^2 corner loads, 3 g^2 + 3 adds for the cell and
+    window box sums, 2 per filter for |t - q|, 1 per filter for the sum over clusters."""
+    k, th, tw, g = cfg["k"], cfg["th"], cfg["tw"], cfg["grid"]
+    F = g * g + 1
+    V = (cfg["H"] - th + 1) * (cfg["W"] - tw + 1)
+    ops_per = (g + 1) ** 2 + 3 * g * g + 3 + 3 * F
+    ops = float(V) * k * ops_per
+    ach = ops / (kernel_ms * 1e-3) / 1e12
+    peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "Tops/s",
+            "frac": round(ach / peak, 4), "traffic": None, "kernel": "score_grid_kernel",
+            "kernel_ms": round(float(kernel_ms), 4), "algorithmic_ops_per_window_cluster": ops_per,
+            "peak_source": "derived: 152 SMs x 128 INT32/FP32 lanes x max SM clock"}
 
 
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev):

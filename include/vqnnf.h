@@ -180,6 +180,17 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
                          float *heatmap, int32_t *argmax_yx,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Profiling aid (the paper has no counterpart).  After
+ * vqnnf_set_kernel_events(op, start, stop) with op = VQNNF_OP_ASSIGN or VQNNF_OP_SCORE and
+ * two CUDA event handles (cudaEvent_t, created and owned by the caller, timing enabled),
+ * every later call of that operation records `start` on its stream immediately before it
+ * enqueues its main kernel (the distance contraction of vqnnf_assign, the score kernel of
+ * vqnnf_score) and `stop` immediately after, so that cudaEventElapsedTime(start, stop) is
+ * that kernel's duration.  Two NULL handles switch it off.  The setting is process-wide
+ * (guarded by a lock) and applies to calls enqueued after it; the events must stay alive
+ * while set.  Returns VQNNF_EINVAL for another op or when only one handle is NULL. */
+vqnnf_status vqnnf_set_kernel_events(int op, void *start_event, void *stop_event);
+
 /* Human-readable name of a status code (static string). */
 const char *vqnnf_status_str(vqnnf_status s);
 

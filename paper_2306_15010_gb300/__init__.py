@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     vqnnf_filter_responses,
     vqnnf_last_device_error,
     vqnnf_score,
+    vqnnf_set_kernel_events,
     vqnnf_version,
     vqnnf_workspace_bytes,
     Bank,

@@ -28,6 +28,7 @@ SIGNATURES = {
     "vqnnf_score": (_i, [_vp, _i, _i, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "vqnnf_status_str": (ctypes.c_char_p, [_i]),
     "vqnnf_last_device_error": (_i, [_vp]),
+    "vqnnf_set_kernel_events": (_i, [_i, _vp, _vp]),
     "vqnnf_version": (_i, []),
 }
 

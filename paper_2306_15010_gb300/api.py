@@ -241,6 +241,16 @@ def vqnnf_score(q_labels: torch.Tensor, k: int, th: int, tw: int, bank, t_counts
     return heatmap, argmax_yx
 
 
+def vqnnf_set_kernel_events(op: int, start=None, stop=None) -> None:
+    """Profiling aid: record the torch.cuda.Event pair (start, stop) immediately around the main
+    kernel of every later call of ``op`` (OP_ASSIGN: the distance contraction; OP_SCORE: the
+    score kernel); None, None switches it off.  The events must have been recorded once (so
+    that their CUDA handles exist) and stay alive while set."""
+    h0 = 0 if start is None else int(start.cuda_event)
+    h1 = 0 if stop is None else int(stop.cuda_event)
+    _lib.check("vqnnf_set_kernel_events", _lib.load().vqnnf_set_kernel_events(int(op), h0 or None, h1 or None))
+
+
 def vqnnf_last_device_error(stream=None) -> int:
     """Synchronise the stream and return (and clear) the device error status code."""
     return int(_lib.load().vqnnf_last_device_error(_stream(stream)))

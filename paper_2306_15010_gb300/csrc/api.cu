@@ -95,6 +95,24 @@ bool check_prec(int prec, int D)
     return false;
 }
 
+// Profiling events set by vqnnf_set_kernel_events, per operation: {start, stop}.
+std::mutex g_ev_mu;
+cudaEvent_t g_ev[4][2] = {};
+
+}  // namespace
+
+cudaError_t vqnnf::record_kernel_event(int op, int which, cudaStream_t s)
+{
+    cudaEvent_t ev;
+    {
+        std::lock_guard<std::mutex> lk(g_ev_mu);
+        ev = g_ev[op][which];
+    }
+    return ev ? cudaEventRecord(ev, s) : cudaSuccess;
+}
+
+namespace {
+
 // Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).
 vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
                         uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s)
@@ -102,10 +120,11 @@ vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int 
     cudaError_t e = cudaMemsetAsync(w.fl.count, 0, 64 * sizeof(unsigned), s);
     if (e == cudaSuccess) e = launch_prep_codebook(C, k, D, prec, w.prep, s);
     if (e == cudaSuccess) {
-        if (prec == VQNNF_PREC_BF16)
-            e = launch_assign_bf16(X, n, D, k, w.prep, labels, w.fl, s);
-        else
-            e = launch_assign_fp32(X, n, D, k, w.prep, labels, w.fl, s);
+        e = record_kernel_event(VQNNF_OP_ASSIGN, 0, s);
+        if (e == cudaSuccess)
+            e = prec == VQNNF_PREC_BF16 ? launch_assign_bf16(X, n, D, k, w.prep, labels, w.fl, s)
+                                        : launch_assign_fp32(X, n, D, k, w.prep, labels, w.fl, s);
+        if (e == cudaSuccess) e = record_kernel_event(VQNNF_OP_ASSIGN, 1, s);
     }
     if (e == cudaSuccess) e = launch_rescore(X, n, D, C, k, labels, w.fl, s);
     if (e == cudaSuccess && stats) e = launch_finish_stats(w.fl, stats, s);
@@ -400,6 +419,16 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
     const int HO = H - th + 1, WO = W - tw + 1;
     return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, t_counts, heatmap, sw.amax,
                                   argmax_yx, s));
+}
+
+vqnnf_status vqnnf_set_kernel_events(int op, void *start_event, void *stop_event)
+{
+    if (op != VQNNF_OP_ASSIGN && op != VQNNF_OP_SCORE) return VQNNF_EINVAL;
+    if ((start_event == nullptr) != (stop_event == nullptr)) return VQNNF_EINVAL;
+    std::lock_guard<std::mutex> lk(g_ev_mu);
+    g_ev[op][0] = static_cast<cudaEvent_t>(start_event);
+    g_ev[op][1] = static_cast<cudaEvent_t>(stop_event);
+    return VQNNF_OK;
 }
 
 vqnnf_status vqnnf_last_device_error(void *stream)

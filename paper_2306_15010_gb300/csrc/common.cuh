@@ -45,6 +45,10 @@ cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, i
                            uint8_t *labels, FlagList fl, cudaStream_t s);
 cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s);
 
+// Records the caller's profiling event `which` (0 = start, 1 = stop) of operation `op` on s,
+// when vqnnf_set_kernel_events has set one; otherwise does nothing.
+cudaError_t record_kernel_event(int op, int which, cudaStream_t s);
+
 // Device error word of the tensor-core translation unit (bounded waits).
 cudaError_t read_and_clear_tc_error(int *out);
 

@@ -499,6 +499,7 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
         e = cudaMemsetAsync(amax, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
+    if ((e = record_kernel_event(VQNNF_OP_SCORE, 0, s)) != cudaSuccess) return e;
     bool done = false;
 #define VQNNF_GRID_CASE(GG, FF)                                                         \
     if (!done && gs.G == GG && gs.full == FF) {                                         \
@@ -521,6 +522,7 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
+    if ((e = record_kernel_event(VQNNF_OP_SCORE, 1, s)) != cudaSuccess) return e;
     if (argmax_yx && amax) {
         argmax_finish_kernel<<<1, 1, 0, s>>>(amax, WO, argmax_yx);
         e = cudaGetLastError();

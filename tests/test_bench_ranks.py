@@ -1,0 +1,50 @@
+"""bench.py's multi-rank logic on CPU with two gloo ranks: the job's step time is the maximum
+over ranks, the value is the whole job's throughput, and the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        ms = bench.reduce_max_ms(3.0 + 2.0 * rank)          # rank 0: 3 ms, rank 1: 5 ms
+        val = bench.job_value(ms, world, 4_194_304)
+        args = type("A", (), {"steps": 1, "warmup": 0})()
+        ref = bench.run_reference(args, rank, world) if rank != 0 else "rank0"
+        dist.barrier()
+        out[rank] = (ms, val, ref is None or ref == "rank0")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_max_and_value():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    for r in range(world):
+        ms, val, ref_ok = out[r]
+        assert ms == pytest.approx(5.0)
+        assert val == pytest.approx(2 * 4_194_304 / 5e-3 / 1e6)
+        assert ref_ok
+
+
+def test_single_process_identity():
+    import bench
+    assert not dist.is_initialized()
+    assert bench.reduce_max_ms(7.25) == 7.25
+    assert bench.job_value(5.0, 1, 1_000_000) == pytest.approx(200.0)
