@@ -74,56 +74,107 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
 }
 
 // c_j[i] = fl32( (sum over members, pixel order, FP64) / count ); empty clusters keep c_j.
-// One warp per (cluster, 32 dimensions).  Each lane streams its own column of the member
-// rows through a shared-memory ring (cp.async, UR rows ahead), so the in-order FP64
-// additions are not serialised behind scattered-row load latency.
-constexpr int UR = 64;       // ring depth (member rows in flight per lane)
-constexpr int UIDX = 1024;   // member indices staged per block
+//
+// The FP64 pipe of this GPU is narrow, so the in-order FP64 sum is not evaluated as such.
+// Every member value is an FP32 number, i.e. an integer multiple of a power of two; in units
+// of 2^-80 the values with 2^-57 <= |x| < 2^46 (and zero) are exact 128-bit integers, whose
+// sum is exact and associative, so it is split over the 8 warps of the block.  If moreover
+// every partial sum of the in-order FP64 evaluation fits in 53 significant bits, none of its
+// additions rounds and its result IS the exact sum.  Sufficient: the top bit of sum |x| (a
+// bound of every partial sum) and the lowest set bit over all members' values are at most 52
+// positions apart.  A (cluster, dimension) pair that fails this (or holds a value outside the
+// range) is summed in FP64 in pixel order by its lane, as before.  Both branches therefore
+// equal the in-order FP64 sum bit for bit.
+constexpr int UW = 8;        // warps per (cluster, 32 dimensions)
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+struct Fixed {
+    unsigned __int128 pos, neg, mag;   // sums of the positive and negative parts, of |x|
+    int low;                           // lowest set bit position over the values (units 2^-80)
+    bool bad;                          // a value outside the exact range
+};
+
+__device__ __forceinline__ void fixed_add(Fixed &f, float x)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src)
-                 : "memory");
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t E = (b >> 23) & 0xFFu;
+    const uint32_t frac = b & 0x7FFFFFu;
+    if (E == 0u && frac == 0u) return;                     // +-0 adds nothing
+    if (E < 70u || E > 172u) { f.bad = true; return; }      // |x| < 2^-57 or >= 2^46 (inf, nan)
+    const uint32_t M = frac | 0x800000u;
+    const int sh = (int)E - 70;                           // x = M * 2^(sh - 80)
+    const unsigned __int128 X = (unsigned __int128)M << sh;
+    if (b >> 31) f.neg += X;
+    else f.pos += X;
+    f.mag += X;
+    f.low = min(f.low, sh + __ffs((int)M) - 1);
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__global__ void __launch_bounds__(32) update_kernel(const float *__restrict__ T, int D, int k,
-                                                    const int *__restrict__ cnt, const int *__restrict__ off,
-                                                    const int *__restrict__ members, float *__restrict__ C)
+__device__ __forceinline__ int top_bit(unsigned __int128 v)
 {
-    __shared__ float ring[UR][32];
-    __shared__ int idx[UIDX];
+    const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+    return hi ? 127 - __clzll((long long)hi) : (lo ? 63 - __clzll((long long)lo) : -1);
+}
+
+__global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict__ T, int D, int k,
+                                                         const int *__restrict__ cnt, const int *__restrict__ off,
+                                                         const int *__restrict__ members, float *__restrict__ C)
+{
+    __shared__ unsigned __int128 spos[UW][32], sneg[UW][32], smag[UW][32];
+    __shared__ int slow[UW][32];
+    __shared__ unsigned char sbad[UW][32];
     const int j = blockIdx.y;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
     const int c = cnt[j];
-    if (c == 0) return;
+    if (c == 0) return;                                  // uniform over the block
     const int *m = members + off[j];
-    const int ic = i < D ? i : D - 1;           // clamped column (every address in bounds)
-    double s = 0.0;
-    for (int q0 = 0; q0 < c; q0 += UIDX) {
-        const int nq = min(UIDX, c - q0);
-        __syncwarp();
-        for (int t = lane; t < nq; t += 32) idx[t] = m[q0 + t];
-        __syncwarp();
-        int qi = 0;                              // next row to issue
-        for (; qi < nq && qi < UR; ++qi) {
-            cp_async4(&ring[qi % UR][lane], T + (size_t)idx[qi] * D + ic);
-            cp_commit();
-        }
-        for (int q = 0; q < nq; ++q) {
-            if (qi - q == UR) cp_wait<UR - 1>();
-            else cp_wait<0>();
-            s += (double)ring[q % UR][lane];     // strictly in member (pixel) order
-            if (qi < nq) {
-                cp_async4(&ring[qi % UR][lane], T + (size_t)idx[qi] * D + ic);
-                cp_commit();
-                ++qi;
-            }
-        }
+    const int ic = i < D ? i : D - 1;                    // clamped column (every address in bounds)
+    Fixed f;
+    f.pos = f.neg = f.mag = 0;
+    f.low = 1 << 30;
+    f.bad = false;
+    int q = w;
+    for (; q + 3 * UW < c; q += 4 * UW) {                // four member rows in flight per warp
+        const float x0 = __ldg(T + (size_t)m[q] * D + ic);
+        const float x1 = __ldg(T + (size_t)m[q + UW] * D + ic);
+        const float x2 = __ldg(T + (size_t)m[q + 2 * UW] * D + ic);
+        const float x3 = __ldg(T + (size_t)m[q + 3 * UW] * D + ic);
+        fixed_add(f, x0);
+        fixed_add(f, x1);
+        fixed_add(f, x2);
+        fixed_add(f, x3);
+    }
+    for (; q < c; q += UW) fixed_add(f, __ldg(T + (size_t)m[q] * D + ic));
+    spos[w][lane] = f.pos;
+    sneg[w][lane] = f.neg;
+    smag[w][lane] = f.mag;
+    slow[w][lane] = f.low;
+    sbad[w][lane] = f.bad ? 1 : 0;
+    __syncthreads();
+    if (w != 0) return;
+    unsigned __int128 pos = 0, neg = 0, mag = 0;
+    int low = 1 << 30;
+    bool bad = false;
+#pragma unroll
+    for (int u = 0; u < UW; ++u) {
+        pos += spos[u][lane];
+        neg += sneg[u][lane];
+        mag += smag[u][lane];
+        low = min(low, slow[u][lane]);
+        bad |= sbad[u][lane] != 0;
+    }
+    double s;
+    if (mag == 0) {
+        s = 0.0;                                         // only zeros: the FP64 sum is +0
+    } else if (!bad && top_bit(mag) - low <= 52) {
+        // exact: |sum| >> low has at most 53 significant bits
+        const bool negative = neg > pos;
+        const unsigned __int128 d = negative ? neg - pos : pos - neg;
+        const double v = (double)(uint64_t)(d >> low);
+        s = ldexp(negative ? -v : v, low - 80);
+    } else {
+        s = 0.0;                                         // rare: the in-order FP64 evaluation
+        for (int q2 = 0; q2 < c; ++q2) s += (double)__ldg(T + (size_t)m[q2] * D + ic);
     }
     if (i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
 }
@@ -141,10 +192,9 @@ cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8
                                 int *off, int *members, float *C, cudaStream_t s)
 {
     stable_sort_kernel<<<1, 1024, 0, s>>>(lab, l, k, cnt, off, members);
-    // one warp per (32 dimensions, cluster): a large cluster's in-order FP64 chains spread
-    // over many SMs (FP64 throughput per SM is small)
+    // one block of UW warps per (32 dimensions, cluster)
     dim3 g((D + 31) / 32, k);
-    update_kernel<<<g, 32, 0, s>>>(T, D, k, cnt, off, members, C);
+    update_kernel<<<g, 32 * UW, 0, s>>>(T, D, k, cnt, off, members, C);
     return cudaGetLastError();
 }
 

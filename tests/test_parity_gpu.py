@@ -118,6 +118,25 @@ def test_fit_codebook_bit_exact(vq, prec, h, w, D, k, iters):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_fit_codebook_exact_sum_edge_values(vq, prec):
+    """Centroid sums with values the exact fixed-point route cannot take (below 2^-57,
+    spans over 52 bits, subnormals), negatives and signed zeros: still bit-identical."""
+    r = np.random.default_rng(5)
+    l, D, k = 700, 64, 6
+    T = r.normal(0.5, 0.3, (l, D)).astype(np.float32)
+    T[r.random((l, D)) < 0.05] = 0.0
+    T[r.random((l, D)) < 0.02] = -0.0
+    T[r.random((l, D)) < 0.01] *= np.float32(2.0 ** -50)        # spans over 52 bits
+    T[r.random((l, D)) < 0.005] = np.float32(1e-30)             # below the exact range
+    T[r.random((l, D)) < 0.002] = np.float32(3e-42)             # subnormal
+    T[:, :8] = np.abs(T[:, :8])                                 # some all-positive columns
+    T = T.reshape(35, 20, D)
+    C = vq.vqnnf_fit_codebook(_dev(T), k, 4, 9, prec)
+    C_ref = oracle.fit_codebook(T, k, 4, 9)
+    assert np.array_equal(C.cpu().numpy().view(np.uint32), C_ref.view(np.uint32))
+
+
 def test_fit_zero_iters_gathers_seeded_init(vq):
     r = np.random.default_rng(6)
     T = r.random((30, 31, 8)).astype(np.float32)
