@@ -20,56 +20,82 @@ __global__ void gather_init_kernel(const float *__restrict__ T, int D, int k, In
     for (int i = threadIdx.x; i < D; i += blockDim.x) C[(size_t)j * D + i] = src[i];
 }
 
-// Stable counting sort of the labels by cluster (one block of 1024 threads).
+// Stable counting sort of the labels by cluster (one block of 32 warps).
 //   cnt[k], off[k+1], members[l] (pixel indices in increasing order within a cluster)
+// Warp w owns the contiguous pixel range [w L, (w+1) L), L = ceil(l / 32) rounded up to 32.
+// Pass 1 counts each cluster's pixels per warp (match_any: one leader per label value),
+// then one exclusive prefix in (cluster, warp) order gives every warp's first slot per
+// cluster; pass 2 repeats the walk and writes each pixel at its slot + rank.
 __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__restrict__ lab,
                                                            int l, int k, int *cnt, int *off,
                                                            int *members)
 {
-    __shared__ int hist[kMaxK];
-    __shared__ int base[kMaxK];
-    __shared__ int wc[32][kMaxK];   // per-warp counts of the current chunk
+    __shared__ int wc[32][kMaxK];   // per-warp counts, then per-warp running slots
+    __shared__ int tot[kMaxK];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    for (int j = t; j < k; j += blockDim.x) hist[j] = 0;
-    __syncthreads();
-    for (int p = t; p < l; p += blockDim.x) atomicAdd(&hist[lab[p]], 1);
-    __syncthreads();
-    if (t == 0) {
-        int s = 0;
-        for (int j = 0; j < k; ++j) {
-            base[j] = s;
-            off[j] = s;
-            cnt[j] = hist[j];
-            s += hist[j];
-        }
-        off[k] = s;
+    const unsigned lt = (1u << lane) - 1u;
+    const int L = ((l + 31) / 32 + 31) / 32 * 32;
+    const int p0 = w * L, p1 = min(l, p0 + L);
+    for (int j = lane; j < k; j += 32) wc[w][j] = 0;
+    __syncwarp();
+    for (int pb = p0; pb < p1; pb += 32) {
+        const int p = pb + lane;
+        const bool in = p < p1;
+        const int l0 = (int)lab[in ? p : p1 - 1];             // clamped address
+        const int lb = in ? l0 : -1 - lane;                   // unique dummies never match
+        const unsigned same = __match_any_sync(0xffffffffu, lb);
+        if (in && __popc(same & lt) == 0) wc[w][lb] += __popc(same);
+        __syncwarp();
     }
     __syncthreads();
-    for (int c0 = 0; c0 < l; c0 += blockDim.x) {
-        for (int q = t; q < 32 * kMaxK; q += blockDim.x)
-            if ((q & (kMaxK - 1)) < k) (&wc[0][0])[q] = 0;
-        __syncthreads();
-        const int p = c0 + t;
-        const bool ok = p < l;
-        const int l0 = (int)lab[ok ? p : l - 1];          // clamped address
-        const int lb = ok ? l0 : -1 - lane;               // unique dummies never match
-        const unsigned same = __match_any_sync(0xffffffffu, lb);
-        const int rank = __popc(same & ((1u << lane) - 1u));
-        if (ok && rank == 0) wc[w][lb] = __popc(same);
-        __syncthreads();
-        // exclusive prefix over warps for every cluster; base advances by the chunk total
-        for (int j = t; j < k; j += blockDim.x) {
-            int s = base[j];
-            for (int q = 0; q < 32; ++q) {
-                const int c = wc[q][j];
-                wc[q][j] = s;
-                s += c;
+    // totals per cluster, exclusive prefix over clusters (warp 0), then over warps per cluster
+    for (int j = t; j < k; j += blockDim.x) {
+        int s = 0;
+        for (int q = 0; q < 32; ++q) s += wc[q][j];
+        tot[j] = s;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int carry = 0;
+        for (int j0 = 0; j0 < k; j0 += 32) {
+            const int j = j0 + lane;
+            const int v = j < k ? tot[j] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            base[j] = s;
+            if (j < k) {
+                off[j] = carry + x - v;
+                cnt[j] = v;
+                tot[j] = carry + x - v;                       // first slot of cluster j
+            }
+            carry += __shfl_sync(0xffffffffu, x, 31);
         }
-        __syncthreads();
-        if (ok) members[wc[w][lb] + rank] = p;
-        __syncthreads();
+        if (lane == 0) off[k] = carry;
+    }
+    __syncthreads();
+    for (int j = t; j < k; j += blockDim.x) {
+        int s = tot[j];
+        for (int q = 0; q < 32; ++q) {
+            const int c = wc[q][j];
+            wc[q][j] = s;
+            s += c;
+        }
+    }
+    __syncthreads();
+    for (int pb = p0; pb < p1; pb += 32) {
+        const int p = pb + lane;
+        const bool in = p < p1;
+        const int l0 = (int)lab[in ? p : p1 - 1];
+        const int lb = in ? l0 : -1 - lane;
+        const unsigned same = __match_any_sync(0xffffffffu, lb);
+        const int rank = __popc(same & lt);
+        if (in) members[wc[w][lb] + rank] = p;
+        __syncwarp();
+        if (in && rank == 0) wc[w][lb] += __popc(same);
+        __syncwarp();
     }
 }
 
