@@ -13,10 +13,12 @@
 //
 // Build, in bands of BH rows so that every warp sweeps few rows:
 //   (1) row carries: per row, the count of every cluster left of every 64-column strip;
-//   (2) band sums: per band, the column sums of the row prefixes (exact int32);
+//   (2) band sums: per (band, strip), the column sums of the row prefixes (exact int32) =
+//       the band's carries plus the prefix along x of the band's per-column label counts;
 //   (3) exclusive prefix of the band sums over bands = S at every band's first row;
 //   (4) one warp per (band, strip, 8 clusters) sweeps its band from there and writes S;
 //       each lane owns two columns, the row prefix inside the strip is ballots + popcounts.
+//       Adjacent warps take adjacent strips, so the rows they write are contiguous runs.
 //
 // Score: one block per (window row, 512 windows).  The corner rows of its windows are
 // staged in shared memory 8 clusters at a time by bulk copies (one per row segment,
@@ -62,10 +64,52 @@ __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, 
     }
 }
 
+// Band sums: one block per (band, strip).  bandsum[(b * k + j) * P + x] for the strip's
+// columns x = sum over the band's rows y of #{x' < x : label(y, x') = j}
+//          = sum_y carry(y, strip, j) + #{(y, x') : y in band, strip start <= x' < x, label = j}.
+__global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict__ lab, int H, int W,
+                                                       int k, int P, int nS, const int *__restrict__ carry,
+                                                       int *__restrict__ bandsum)
+{
+    extern __shared__ int cc[];                          // [SW][k] label counts per column
+    const int s = blockIdx.x, b = blockIdx.y;
+    const int x0 = s * SW, y0 = b * BH, y1 = min(H, y0 + BH);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < SW * k; q += blockDim.x) cc[q] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < (y1 - y0) * SW; q += blockDim.x) {
+        const int y = y0 + q / SW, xx = q % SW, x = x0 + xx;
+        if (x < W) {
+            const int lb = lab[(size_t)y * W + x];
+            if (lb < k) atomicAdd(&cc[xx * k + lb], 1);
+        }
+    }
+    __syncthreads();
+    // per cluster: the band's carry sum, then an inclusive warp scan of the 64 column counts
+    // (two per lane) shifted by one column
+    for (int j = w; j < k; j += blockDim.x >> 5) {
+        int csum = 0;
+        for (int y = y0 + lane; y < y1; y += 32) csum += carry[((size_t)y * nS + s) * k + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+        const int a0 = cc[(2 * lane) * k + j], a1 = cc[(2 * lane + 1) * k + j];
+        int v = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        const int ex = v - a0 - a1;                      // counts of the columns left of 2 lane
+        const int x = x0 + 2 * lane;
+        if (x < P)
+            *reinterpret_cast<int2 *>(&bandsum[((size_t)b * k + j) * P + x]) =
+                make_int2(csum + ex, csum + ex + a0);
+    }
+}
+
 // One warp per (band, strip, cluster group); lane l owns the two S columns 2l and 2l + 1 of
-// its 64-column strip (one 4-byte store per lane for the 16-bit table).  WRITE = false:
-// accumulate the band's column sums into bandsum.  WRITE = true: start from the band's
-// prefix and write its S rows.
+// its 64-column strip (one 4-byte store per lane for the 16-bit table).  Starts from the
+// band's prefix and writes its S rows.
 template <typename T>
 __device__ __forceinline__ void store_pair(T *dst, int a, int b);
 template <>
@@ -79,18 +123,18 @@ __device__ __forceinline__ void store_pair<uint32_t>(uint32_t *dst, int a, int b
     *reinterpret_cast<uint2 *>(dst) = make_uint2((uint32_t)a, (uint32_t)b);
 }
 
-template <typename T, bool WRITE>
-__global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict__ lab, int H, int W,
-                                                       int k, int P, int nS, int nB,
-                                                       const int *__restrict__ carry,
-                                                       int *__restrict__ bandsum, T *__restrict__ S)
+template <typename T>
+__global__ void __launch_bounds__(256) sat_write_kernel(const uint8_t *__restrict__ lab, int H, int W,
+                                                        int k, int P, int nS, int nB,
+                                                        const int *__restrict__ carry,
+                                                        const int *__restrict__ bandsum, T *__restrict__ S)
 {
     const int lane = threadIdx.x & 31;
     const int ncg = (k + CGW - 1) / CGW;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= (long long)nB * nS * ncg) return;
-    const int cg = (int)(gw % ncg);
-    const int s = (int)((gw / ncg) % nS);
+    const int s = (int)(gw % nS);                        // adjacent warps: adjacent strips
+    const int cg = (int)((gw / nS) % ncg);
     const int b = (int)(gw / ((long long)ncg * nS));
     const int x = s * SW + 2 * lane;      // first of the two S columns owned by this lane
     const bool xin = x < P;               // P is even, so x + 1 < P as well
@@ -100,27 +144,33 @@ __global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict
 #pragma unroll
     for (int q = 0; q < CGW; ++q) {
         const int j = cg * CGW + q;
-        if (WRITE) {
-            const int jc = min(j, k - 1), xc = min(x, P - 2);      // clamped addresses
-            const int2 v = *reinterpret_cast<const int2 *>(&bandsum[((size_t)b * k + jc) * P + xc]);
-            const bool in = j < k && xin;
-            acc0[q] = in ? v.x : 0;
-            acc1[q] = in ? v.y : 0;
-            if (b == 0 && in) store_pair<T>(&S[(size_t)j * P + x], 0, 0);   // row 0 of S
-        } else {
-            acc0[q] = 0;
-            acc1[q] = 0;
-        }
+        const int jc = min(j, k - 1), xc = min(x, P - 2);      // clamped addresses
+        const int2 v = *reinterpret_cast<const int2 *>(&bandsum[((size_t)b * k + jc) * P + xc]);
+        const bool in = j < k && xin;
+        acc0[q] = in ? v.x : 0;
+        acc1[q] = in ? v.y : 0;
+        if (b == 0 && in) store_pair<T>(&S[(size_t)j * P + x], 0, 0);   // row 0 of S
+    }
+    const int jl = min(cg * CGW + (lane & (CGW - 1)), k - 1);
+    const bool jlin = lane < CGW && cg * CGW + lane < k;
+    // labels and carry of the next row are loaded one row ahead
+    const int xa = x, xb = x + 1;
+    int la_n = 0, lb_n = 0, c_n = 0;
+    if (y0 < y1) {
+        const uint8_t *row = lab + (size_t)y0 * W;
+        la_n = (int)row[min(xa, W - 1)];
+        lb_n = (int)row[min(xb, W - 1)];
+        c_n = carry[((size_t)y0 * nS + s) * k + jl];
     }
     for (int y = y0; y < y1; ++y) {
-        // labels at the lane's two columns (clamped addresses, -1 past the row)
-        const uint8_t *row = lab + (size_t)y * W;
-        const int xa = x, xb = x + 1;
-        const int la0 = (int)row[min(xa, W - 1)], lb0 = (int)row[min(xb, W - 1)];
-        const int la = xa < W ? la0 : -1, lb = xb < W ? lb0 : -1;
-        const int jc = min(cg * CGW + (lane & (CGW - 1)), k - 1);
-        const int c0 = carry[((size_t)y * nS + s) * k + jc];
-        const int cj = (lane < CGW && cg * CGW + lane < k) ? c0 : 0;
+        const int la = xa < W ? la_n : -1, lb = xb < W ? lb_n : -1;
+        const int cj = jlin ? c_n : 0;
+        if (y + 1 < y1) {
+            const uint8_t *row = lab + (size_t)(y + 1) * W;
+            la_n = (int)row[min(xa, W - 1)];
+            lb_n = (int)row[min(xb, W - 1)];
+            c_n = carry[((size_t)(y + 1) * nS + s) * k + jl];
+        }
 #pragma unroll
         for (int q = 0; q < CGW; ++q) {
             const int j = cg * CGW + q;
@@ -130,15 +180,7 @@ __global__ void __launch_bounds__(128) sat_band_kernel(const uint8_t *__restrict
             const int r0 = __shfl_sync(0xffffffffu, cj, q) + __popc(ba & lt) + __popc(bb & lt);
             acc0[q] += r0;
             acc1[q] += r0 + (la == j ? 1 : 0);
-            if (WRITE && j < k && xin) store_pair<T>(&S[((size_t)(y + 1) * k + j) * P + x], acc0[q], acc1[q]);
-        }
-    }
-    if (!WRITE) {
-#pragma unroll
-        for (int q = 0; q < CGW; ++q) {
-            const int j = cg * CGW + q;
-            if (j < k && xin)
-                *reinterpret_cast<int2 *>(&bandsum[((size_t)b * k + j) * P + x]) = make_int2(acc0[q], acc1[q]);
+            if (j < k && xin) store_pair<T>(&S[((size_t)(y + 1) * k + j) * P + x], acc0[q], acc1[q]);
         }
     }
 }
@@ -479,12 +521,15 @@ cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, in
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     if (e != cudaSuccess) return e;
     row_carry_kernel<<<H, 256, hsmem, s>>>(lab, W, k, nS, carry);
-    const long long nwarps = (long long)nB * nS * ((k + CGW - 1) / CGW);
-    const unsigned blocks = (unsigned)((nwarps + 3) / 4);
-    sat_band_kernel<T, false><<<blocks, 128, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
+    const size_t csmem = sizeof(int) * (size_t)SW * k;
+    e = cudaFuncSetAttribute(band_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+    if (e != cudaSuccess) return e;
+    band_sum_kernel<<<dim3(nS, nB), 256, csmem, s>>>(lab, H, W, k, P, nS, carry, bandsum);
     const long long kP = (long long)k * P;
     band_prefix_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, s>>>(bandsum, nB, kP);
-    sat_band_kernel<T, true><<<blocks, 128, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
+    const long long nwarps = (long long)nB * nS * ((k + CGW - 1) / CGW);
+    const unsigned blocks = (unsigned)((nwarps + 7) / 8);
+    sat_write_kernel<T><<<blocks, 256, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
     return cudaGetLastError();
 }
 
