@@ -104,14 +104,14 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
 // The FP64 pipe of this GPU is narrow, so the in-order FP64 sum is not evaluated as such.
 // Every member value is an FP32 number, i.e. an integer multiple of a power of two; in units
 // of 2^-80 the values with 2^-57 <= |x| < 2^46 (and zero) are exact 128-bit integers, whose
-// sum is exact and associative, so it is split over the 8 warps of the block.  If moreover
+// sum is exact and associative, so it is split over the 16 warps of the block.  If moreover
 // every partial sum of the in-order FP64 evaluation fits in 53 significant bits, none of its
 // additions rounds and its result IS the exact sum.  Sufficient: the top bit of sum |x| (a
 // bound of every partial sum) and the lowest set bit over all members' values are at most 52
 // positions apart.  A (cluster, dimension) pair that fails this (or holds a value outside the
 // range) is summed in FP64 in pixel order by its lane, as before.  Both branches therefore
 // equal the in-order FP64 sum bit for bit.
-constexpr int UW = 8;        // warps per (cluster, 32 dimensions)
+constexpr int UW = 16;       // warps per (cluster, 32 dimensions)
 
 struct Fixed {
     unsigned __int128 pos, neg, mag;   // sums of the positive and negative parts, of |x|
@@ -160,15 +160,12 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
     f.low = 1 << 30;
     f.bad = false;
     int q = w;
-    for (; q + 3 * UW < c; q += 4 * UW) {                // four member rows in flight per warp
-        const float x0 = __ldg(T + (size_t)m[q] * D + ic);
-        const float x1 = __ldg(T + (size_t)m[q + UW] * D + ic);
-        const float x2 = __ldg(T + (size_t)m[q + 2 * UW] * D + ic);
-        const float x3 = __ldg(T + (size_t)m[q + 3 * UW] * D + ic);
-        fixed_add(f, x0);
-        fixed_add(f, x1);
-        fixed_add(f, x2);
-        fixed_add(f, x3);
+    for (; q + 7 * UW < c; q += 8 * UW) {                // eight member rows in flight per warp
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = __ldg(T + (size_t)m[q + u * UW] * D + ic);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) fixed_add(f, x[u]);
     }
     for (; q < c; q += UW) fixed_add(f, __ldg(T + (size_t)m[q] * D + ic));
     spos[w][lane] = f.pos;
@@ -181,7 +178,7 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
     unsigned __int128 pos = 0, neg = 0, mag = 0;
     int low = 1 << 30;
     bool bad = false;
-#pragma unroll
+#pragma unroll 2
     for (int u = 0; u < UW; ++u) {
         pos += spos[u][lane];
         neg += sneg[u][lane];

@@ -71,11 +71,18 @@ __global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict
                                                        int k, int P, int nS, const int *__restrict__ carry,
                                                        int *__restrict__ bandsum)
 {
-    extern __shared__ int cc[];                          // [SW][k] label counts per column
+    extern __shared__ int cc[];                          // [SW][k] label counts per column, then [k] carry sums
+    int *csum_s = cc + SW * k;
     const int s = blockIdx.x, b = blockIdx.y;
     const int x0 = s * SW, y0 = b * BH, y1 = min(H, y0 + BH);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < SW * k; q += blockDim.x) cc[q] = 0;
+    // the band's carry sums, cluster-major (consecutive threads read consecutive clusters)
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        int cs = 0;
+        for (int y = y0; y < y1; ++y) cs += carry[((size_t)y * nS + s) * k + j];
+        csum_s[j] = cs;
+    }
     __syncthreads();
     for (int q = threadIdx.x; q < (y1 - y0) * SW; q += blockDim.x) {
         const int y = y0 + q / SW, xx = q % SW, x = x0 + xx;
@@ -85,13 +92,10 @@ __global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict
         }
     }
     __syncthreads();
-    // per cluster: the band's carry sum, then an inclusive warp scan of the 64 column counts
-    // (two per lane) shifted by one column
+    // per cluster: an inclusive warp scan of the 64 column counts (two per lane) shifted by
+    // one column, on top of the band's carry sum
     for (int j = w; j < k; j += blockDim.x >> 5) {
-        int csum = 0;
-        for (int y = y0 + lane; y < y1; y += 32) csum += carry[((size_t)y * nS + s) * k + j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+        const int csum = csum_s[j];
         const int a0 = cc[(2 * lane) * k + j], a1 = cc[(2 * lane + 1) * k + j];
         int v = a0 + a1;
 #pragma unroll
@@ -521,7 +525,7 @@ cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, in
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     if (e != cudaSuccess) return e;
     row_carry_kernel<<<H, 256, hsmem, s>>>(lab, W, k, nS, carry);
-    const size_t csmem = sizeof(int) * (size_t)SW * k;
+    const size_t csmem = sizeof(int) * ((size_t)SW * k + k);
     e = cudaFuncSetAttribute(band_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
     if (e != cudaSuccess) return e;
     band_sum_kernel<<<dim3(nS, nB), 256, csmem, s>>>(lab, H, W, k, P, nS, carry, bandsum);
