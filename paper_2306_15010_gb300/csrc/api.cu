@@ -242,6 +242,7 @@ vqnnf_status compile_bank(const vqnnf_filter *bank, int F, int th, int tw, BankS
         return VQNNF_OK;
     const int ncell = F - (full_f >= 0 ? 1 : 0);
     if (ncell != G * G) return VQNNF_OK;
+    if (!score_grid_fits(bs.ncol)) return VQNNF_OK;       // template wider than the grid kernel stages
     int seen[16] = {0};
     GridSpec g;
     memset(&g, 0, sizeof(g));

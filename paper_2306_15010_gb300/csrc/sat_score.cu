@@ -242,7 +242,7 @@ constexpr int STH = 128;          // threads per block
 constexpr int WPT = 4;            // windows per thread
 constexpr int TXW = STH * WPT;    // windows per block along x
 constexpr int CH = 4;             // clusters per staged chunk
-constexpr int NBUF = 3;           // staging buffers of the grid kernel
+constexpr int NBUF = 2;           // staging buffers of the grid kernel
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
 {
@@ -260,10 +260,11 @@ __device__ __forceinline__ int box(int s11, int s10, int s01, int s00)
 }
 
 // Thread 0 issues the bulk copies of one chunk of corner rows: for cluster c of the chunk
-// and corner row rr, the ncol elements of S starting at column x0.
+// and corner row rr, the ncol elements of S starting at column x0, staged pitch elements apart.
 template <typename T>
 __device__ __forceinline__ void issue_chunk(T *dst, const T *__restrict__ S, int k, int P, int y, int x0,
-                                            int j0, int ncol, const int *roff, int nrow, uint64_t *bar)
+                                            int j0, int ncol, int pitch, const int *roff, int nrow,
+                                            uint64_t *bar)
 {
     const int cmax = min(CH, k - j0);
     const uint32_t row_bytes = (uint32_t)(ncol * sizeof(T));
@@ -271,11 +272,11 @@ __device__ __forceinline__ void issue_chunk(T *dst, const T *__restrict__ S, int
     ptx::mbar_expect_tx(bar, row_bytes * (uint32_t)(cmax * nrow));
     for (int c = 0; c < cmax; ++c)
         for (int rr = 0; rr < nrow; ++rr)
-            ptx::bulk_g2s(dst + (size_t)(c * nrow + rr) * ncol,
+            ptx::bulk_g2s(dst + (size_t)(c * nrow + rr) * pitch,
                           S + ((size_t)(y + roff[rr]) * k + (j0 + c)) * P + x0, row_bytes, bar);
 }
 
-template <typename T, int G, bool FULL>
+template <typename T, int G, bool FULL, int NCOLP>
 __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S, int P, int k,
                                                          int HO, int WO, GridSpec gs,
                                                          const int32_t *__restrict__ tcounts,
@@ -289,8 +290,10 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
     constexpr int NR = G + 1;
     constexpr int NSLOT = G * G + (FULL ? 1 : 0);
     extern __shared__ __align__(128) uint8_t smem_raw[];
+    // staged rows are NCOLP elements apart (a compile-time pitch >= ncol), so that every
+    // corner load of the inner loop is a per-thread column pointer plus an immediate offset
     const int ncol = gs.ncol;
-    const size_t chunk_elems = (size_t)CH * NR * ncol;
+    constexpr int chunk_elems = CH * NR * NCOLP;
     T *bufs = reinterpret_cast<T *>(smem_raw);                               // [NBUF][chunk]
     int *tc = reinterpret_cast<int *>(bufs + NBUF * chunk_elems);           // [NSLOT][k]
     unsigned *cmask = reinterpret_cast<unsigned *>(tc + NSLOT * k);          // [k]
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
         ptx::fence_barrier_init();
         int c = 0;
         for (; c < NBUF - 1 && c < nchunk; ++c)
-            issue_chunk<T>(bufs + c * chunk_elems, S, k, P, y, x0, c * CH, ncol, gs.by, NR, &full[c]);
+            issue_chunk<T>(bufs + c * chunk_elems, S, k, P, y, x0, c * CH, ncol, NCOLP, gs.by, NR, &full[c]);
         *n_issued = c;
     }
     __syncthreads();
@@ -343,20 +346,24 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
             if (use > 0)
                 ok = ptx::mbar_wait_bounded(&empty[nb], (use - 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
             if (ok) {
-                issue_chunk<T>(bufs + nb * chunk_elems, S, k, P, y, x0, (ch + NBUF - 1) * CH, ncol, gs.by,
-                               NR, &full[nb]);
+                issue_chunk<T>(bufs + nb * chunk_elems, S, k, P, y, x0, (ch + NBUF - 1) * CH, ncol, NCOLP,
+                               gs.by, NR, &full[nb]);
                 *n_issued = ch + NBUF;
             }
         }
         ok = __all_sync(0xffffffffu, ok && ptx::mbar_wait_bounded(&full[b], (ch / NBUF) & 1, &g_score_error,
                                                                   (int)VQNNF_ETIMEOUT));
         if (!ok) break;
-        const T *cur = bufs + b * chunk_elems;
+        const T *cur = bufs + b * chunk_elems + threadIdx.x;
         const int cmax = min(CH, k - ch * CH);
-        for (int c = 0; c < cmax; ++c) {
+        const T *pc[NR];                                  // this thread's column of each corner column
+#pragma unroll
+        for (int cc = 0; cc < NR; ++cc) pc[cc] = cur + off[cc];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (c >= cmax) break;
             const int j = ch * CH + c;
             const unsigned m = cmask[j];                    // same for every thread: uniform branches
-            const T *base = cur + (size_t)c * NR * ncol + threadIdx.x;
 #pragma unroll
             for (int q = 0; q < NSLOT; ++q) {
                 if (!(m & (1u << q))) continue;
@@ -367,9 +374,8 @@ __global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S
                 const int c1 = (FULL && q == NSLOT - 1) ? G : q % G + 1;
 #pragma unroll
                 for (int w = 0; w < WPT; ++w) {
-                    const T *p = base + w * STH;
-                    const int n = box<T>((int)p[r1 * ncol + off[c1]], (int)p[r1 * ncol + off[c0]],
-                                         (int)p[r0 * ncol + off[c1]], (int)p[r0 * ncol + off[c0]]);
+                    const int o0 = (c * NR + r0) * NCOLP + w * STH, o1 = (c * NR + r1) * NCOLP + w * STH;
+                    const int n = box<T>((int)pc[c1][o1], (int)pc[c0][o1], (int)pc[c1][o0], (int)pc[c0][o0]);
                     acc[w][q] = (int)__sad(t, n, (unsigned)acc[w][q]) - n;
                 }
             }
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(STH) score_generic_kernel(const T *__restrict_
         ptx::mbar_init(&bar[0], 1);
         ptx::mbar_init(&bar[1], 1);
         ptx::fence_barrier_init();
-        issue_chunk<T>(buf0, S, k, P, y, x0, 0, ncol, bs.roff, nrow, &bar[0]);
+        issue_chunk<T>(buf0, S, k, P, y, x0, 0, ncol, ncol, bs.roff, nrow, &bar[0]);
     }
     __syncthreads();
     long long l1[WPT][kMaxFilters];
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(STH) score_generic_kernel(const T *__restrict_
     for (int ch = 0; ch < nchunk; ++ch) {
         T *cur = (ch & 1) ? buf1 : buf0;
         if (threadIdx.x == 0 && ch + 1 < nchunk)
-            issue_chunk<T>((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, bs.roff, nrow,
+            issue_chunk<T>((ch & 1) ? buf0 : buf1, S, k, P, y, x0, (ch + 1) * CH, ncol, ncol, bs.roff, nrow,
                            &bar[(ch + 1) & 1]);
         ok = ptx::mbar_wait_bounded(&bar[ch & 1], (ch >> 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
         if (!__syncthreads_and(ok)) { ok = false; break; }
@@ -505,11 +511,19 @@ cudaError_t launch_grid(const T *S, int P, int k, int HO, int WO, const GridSpec
     BankSpec none;
     none.F = 0;
     const size_t smem = score_smem_bytes_for(sizeof(T), none, gs, k);
-    cudaError_t e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((WO + TXW - 1) / TXW, HO);
-    score_grid_kernel<T, G, FULL><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+    cudaError_t e;
+    if (gs.ncol <= TXW + 128) {
+        e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL, TXW + 128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        score_grid_kernel<T, G, FULL, TXW + 128><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+    } else {
+        e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL, TXW + 256>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        score_grid_kernel<T, G, FULL, TXW + 256><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+    }
     return cudaGetLastError();
 }
 
@@ -581,12 +595,17 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
 
 }  // namespace
 
+// Staged row pitch of the grid kernel for a window strip of ncol columns (template width up
+// to 256; wider templates take the generic kernel).
+int score_grid_pitch(int ncol) { return ncol <= TXW + 128 ? TXW + 128 : TXW + 256; }
+bool score_grid_fits(int ncol) { return ncol <= TXW + 256; }
+
 size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs, int k)
 {
     if (gs.G > 0) {
         const int NR = gs.G + 1;
         const int NSLOT = gs.G * gs.G + (gs.full ? 1 : 0);
-        return elem * (size_t)NBUF * CH * NR * gs.ncol + sizeof(int) * ((size_t)NSLOT * k + k + 1) +
+        return elem * (size_t)NBUF * CH * NR * score_grid_pitch(gs.ncol) + sizeof(int) * ((size_t)NSLOT * k + k + 1) +
                sizeof(uint64_t) * 2 * NBUF + 16 + 16;
     }
     return elem * (size_t)2 * CH * bs.nrow * bs.ncol + sizeof(int) * ((size_t)bs.F * k + 1) + 32;

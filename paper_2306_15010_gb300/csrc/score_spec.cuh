@@ -50,6 +50,7 @@ int sat_pitch(int W);
 int sat_strips(int W);
 int sat_bands(int H);
 int score_ncol(int tw);
+bool score_grid_fits(int ncol);   // the grid kernel stages at most TXW + 256 columns
 size_t sat_slack_elems(int tw);
 cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, bool u16, int *carry, int *bandsum,
                        void *S, cudaStream_t s);
