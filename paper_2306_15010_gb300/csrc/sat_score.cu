@@ -241,7 +241,7 @@ __global__ void filter_responses_kernel(const uint8_t *__restrict__ lab, int w, 
 constexpr int STH = 128;          // threads per block
 constexpr int WPT = 4;            // windows per thread
 constexpr int TXW = STH * WPT;    // windows per block along x
-constexpr int CH = 4;             // clusters per staged chunk
+constexpr int CH = 2;             // clusters per staged chunk
 constexpr int NBUF = 2;           // staging buffers of the grid kernel
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
@@ -277,7 +277,7 @@ __device__ __forceinline__ void issue_chunk(T *dst, const T *__restrict__ S, int
 }
 
 template <typename T, int G, bool FULL, int NCOLP>
-__global__ void __launch_bounds__(STH) score_grid_kernel(const T *__restrict__ S, int P, int k,
+__global__ void __launch_bounds__(STH, 6) score_grid_kernel(const T *__restrict__ S, int P, int k,
                                                          int HO, int WO, GridSpec gs,
                                                          const int32_t *__restrict__ tcounts,
                                                          float *__restrict__ heat,
