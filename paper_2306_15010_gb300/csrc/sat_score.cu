@@ -241,8 +241,8 @@ __global__ void filter_responses_kernel(const uint8_t *__restrict__ lab, int w, 
 constexpr int STH = 128;          // threads per block
 constexpr int WPT = 4;            // windows per thread
 constexpr int TXW = STH * WPT;    // windows per block along x
-constexpr int CH = 2;             // clusters per staged chunk
-constexpr int NBUF = 2;           // staging buffers of the grid kernel
+constexpr int CH = 1;             // clusters per staged chunk
+constexpr int NBUF = 4;           // staging buffers of the grid kernel
 
 __device__ __forceinline__ unsigned long long pack_key(float v, unsigned idx)
 {
