@@ -27,7 +27,7 @@ namespace {
 constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
 
 // ----------------------------------------------------------------------------------
-// Codebook preparation (FP64): reference point, centred copies and bound terms.
+// Codebook preparation: reference point, centred copies and bound terms.
 // ----------------------------------------------------------------------------------
 // The reference point m only has to be the same FP32 vector for every use (the bound holds
 // for any m); the codebook mean keeps the centred norms small.  Four interleaved FP32 partial
@@ -52,62 +52,117 @@ __global__ void __launch_bounds__(256) prep_mean_kernel(const float *__restrict_
     }
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 h)
+// Error-free transformations in FP32 (Knuth's TwoSum; the FMA product error).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    return *reinterpret_cast<uint16_t *>(&h);
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    const float av = __fsub_rn(s, bv);
+    e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
 }
 
-// One block per centroid.  Sums are reduced in a fixed tree order (deterministic).
+// BF16 rounding (to nearest, ties to even) of the exact value v = f + e, where f = fl32(v):
+// identical to rounding f except when f sits exactly halfway between two BF16 values and
+// e != 0, where the exact value lies on the side of e.
+__device__ __forceinline__ uint32_t bf16_round_exact(float f, float e)
+{
+    const uint32_t bits = __float_as_uint(f);
+    if ((bits & 0xFFFFu) == 0x8000u && e != 0.0f) {
+        const uint32_t down = bits & 0xFFFF0000u;          // toward zero
+        const bool away = (e > 0.0f) == (f > 0.0f);
+        return (away ? down + 0x10000u : down) >> 16;
+    }
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+__device__ __forceinline__ float bf16_value(uint32_t h) { return __uint_as_float(h << 16); }
+
+// One block per centroid, FP32 error-free arithmetic (the FP64 pipe of this GPU is narrow):
+// c* = c - m exactly as cf + d32 (TwoSum), the BF16 splits hi = bf16(c*), lo = bf16(c* - hi)
+// of the exact values, ||c*||^2 as a compensated sum of the exact squares (FMA products),
+// and upper bounds of the other norms (sums of squares inflated by their summation bound).
+// The block reduction has a fixed tree order (deterministic).
 __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restrict__ C, int k,
                                                             int D, int prec, CodebookPrep p)
 {
     const int j = blockIdx.x;
-    __shared__ double red[6][256];
-    double s_c2 = 0, s_cc2 = 0, s_d32 = 0, s_hi2 = 0, s_lo2 = 0, s_d16 = 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __shared__ float red[8][8];
+    float S = 0.f, Sc = 0.f, Q = 0.f;                 // ||c*||^2: main sum, its compensation, small terms
+    float s_cc2 = 0.f, s_d32 = 0.f, s_hi2 = 0.f, s_lo2 = 0.f, s_d16 = 0.f;
     for (int i = threadIdx.x; i < D; i += blockDim.x) {
-        double cs = (double)C[(size_t)j * D + i] - (double)p.mean[i];   // exact in FP64
-        float cf = (float)cs;
+        const float c = C[(size_t)j * D + i], m = p.mean[i];
+        float cf, d32;
+        two_sum(c, -m, cf, d32);                      // c - m = cf + d32 exactly
         p.cc[(size_t)j * D + i] = cf;
-        __nv_bfloat16 hi = __double2bfloat16(cs);
-        double r = cs - (double)__bfloat162float(hi);
-        __nv_bfloat16 lo = __double2bfloat16(r);
-        double d16 = r - (double)__bfloat162float(lo);
-        p.chi[(size_t)j * D + i] = bf16_bits(hi);
-        p.clo[(size_t)j * D + i] = bf16_bits(lo);
-        double hif = (double)__bfloat162float(hi), lof = (double)__bfloat162float(lo);
-        double d32 = cs - (double)cf;
-        s_c2 += cs * cs;
-        s_cc2 += (double)cf * (double)cf;
-        s_d32 += d32 * d32;
-        s_hi2 += hif * hif;
-        s_lo2 += lof * lof;
-        s_d16 += d16 * d16;
+        const uint32_t hb = bf16_round_exact(cf, d32);
+        const float hf = bf16_value(hb);
+        float rf, rd;
+        two_sum(__fsub_rn(cf, hf), d32, rf, rd);      // r = c* - hi = rf + rd (cf - hf is exact)
+        const uint32_t lb = bf16_round_exact(rf, rd);
+        const float lf = bf16_value(lb);
+        const float d16 = fabsf(__fsub_rn(rf, lf)) + fabsf(rd);   // >= |r - lo| (rf - lf exact)
+        p.chi[(size_t)j * D + i] = (uint16_t)hb;
+        p.clo[(size_t)j * D + i] = (uint16_t)lb;
+        // c*^2 = cf^2 + 2 cf d32 + d32^2, cf^2 = pp + pe exactly
+        const float pp = __fmul_rn(cf, cf), pe = fmaf(cf, cf, -pp);
+        float t, te;
+        two_sum(S, pp, t, te);
+        S = t;
+        Sc += te;
+        Q += pe + 2.0f * cf * d32 + d32 * d32;
+        s_cc2 = fmaf(cf, cf, s_cc2);
+        s_d32 = fmaf(d32, d32, s_d32);
+        s_hi2 = fmaf(hf, hf, s_hi2);
+        s_lo2 = fmaf(lf, lf, s_lo2);
+        s_d16 = fmaf(d16, d16, s_d16);
     }
-    red[0][threadIdx.x] = s_c2;
-    red[1][threadIdx.x] = s_cc2;
-    red[2][threadIdx.x] = s_d32;
-    red[3][threadIdx.x] = s_hi2;
-    red[4][threadIdx.x] = s_lo2;
-    red[5][threadIdx.x] = s_d16;
+    // warp then block tree: (S, Sc) added as double-floats, the rest plainly
+    float v8[8] = {S, Sc, Q, s_cc2, s_d32, s_hi2, s_lo2, s_d16};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float o8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o8[q] = __shfl_xor_sync(0xffffffffu, v8[q], o);
+        float t, te;
+        two_sum(v8[0], o8[0], t, te);
+        v8[0] = t;
+        v8[1] = v8[1] + o8[1] + te;
+#pragma unroll
+        for (int q = 2; q < 8; ++q) v8[q] += o8[q];
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[w][q] = v8[q];
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int q = 0; q < 6; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        float tot[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tot[q] = red[0][q];
+        for (int u2 = 1; u2 < nw; ++u2) {
+            float t, te;
+            two_sum(tot[0], red[u2][0], t, te);
+            tot[0] = t;
+            tot[1] = tot[1] + red[u2][1] + te;
+#pragma unroll
+            for (int q = 2; q < 8; ++q) tot[q] += red[u2][q];
+        }
         const double u = kU32;
-        const double g64 = (double)(D + 2) * 1.1102230246251565e-16;  // FP64 sum error
-        const double c2 = red[0][0];
-        const float n32 = (float)c2;
-        const double en = fabs((double)n32 - c2) + c2 * g64;
-        const double margin = 1.0 + 1e-6;
-        const double nc = sqrt(red[0][0]) * margin;      // ||c*||
-        const double ncc = sqrt(red[1][0]) * margin;     // ||fl32(c*)||
-        const double nd32 = sqrt(red[2][0]) * margin;    // ||c* - fl32(c*)||
-        const double nhi = sqrt(red[3][0]) * margin;
-        const double nlo = sqrt(red[4][0]) * margin;
-        const double nd16 = sqrt(red[5][0]) * margin;
+        // ||c*||^2: the compensated sum is within (2u + 2 D u^2) of the exact value (plus the
+        // small terms' own rounding, relative u^2 D); n32 rounds it once more
+        const float n32 = __fadd_rn(tot[0], tot[1] + tot[2]);
+        const double c2 = (double)n32;
+        const double en = 4.0 * u * c2 + 1e-37;                 // >= |n32 - ||c*||^2|
+        // other norms: sums of D non-negative terms are within gamma_D of the exact value
+        const double up = 1.0 + (2.0 * D + 8.0) * u;
+        const double margin = 1.0 + 4.0 * u;
+        const double nc = sqrt((c2 + en) * up) * margin;        // ||c*||
+        const double ncc = sqrt((double)tot[3] * up) * margin;  // ||fl32(c*)||
+        const double nd32 = sqrt((double)tot[4] * up) * margin; // ||c* - fl32(c*)||
+        const double nhi = sqrt((double)tot[5] * up) * margin;
+        const double nlo = sqrt((double)tot[6] * up) * margin;
+        const double nd16 = sqrt((double)tot[7] * up) * margin;
         double a, v;
         if (prec == VQNNF_PREC_FP32) {
             const double gD = (double)D * u / (1.0 - (double)D * u);
@@ -335,13 +390,6 @@ __device__ __forceinline__ float warp_sum(float v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
 }
 
 __device__ __forceinline__ void df_warp_sum(float &hi, float &lo)
