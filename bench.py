@@ -303,6 +303,7 @@ def run_gpu(args, rank, world):
 
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev)
+    paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
 
     if rank != 0:
         return None
@@ -328,6 +329,7 @@ def run_gpu(args, rank, world):
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "roofline_score": roof_score, "clocks": clocks, "e2e": e2e,
+        "paper_bank": paper,
         f"{other}_path": None if ms2 is None else {
             "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
             "ms_per_step": round(ms2, 4),
@@ -387,6 +389,38 @@ def roofline_score(cfg, kernel_ms, peaks):
             "frac": round(ach / peak, 4), "traffic": None, "kernel": "score_grid_kernel",
             "kernel_ms": round(float(kernel_ms), 4), "algorithmic_ops_per_window_cluster": ops_per,
             "peak_source": "derived: 152 SMs x 128 INT32/FP32 lanes x max SM clock"}
+
+
+def run_paper_bank(vq, pipe, cfg, s, dev, reps=5):
+    """The paper's own filter bank (F_{2,3-rect}: Gaussian + Haar 2x/2y/3x/3y, S = 3 sub-scales,
+    15 multi-rectangle filters, equal-weight reading) scored on this step's query NNF; the
+    score kernel (generic bank path) timed alone with library-recorded events."""
+    import torch
+    import synth
+    th, tw, k, H, W = cfg["th"], cfg["tw"], cfg["k"], cfg["H"], cfg["W"]
+    bank = vq.Bank(synth.paper_bank(th, tw, "2,3-rect", 3, "equal"))
+    ws = vq.Workspace(vq.vqnnf_workspace_bytes(3, H, W, 0, k, th, tw, bank.F), dev)
+    heat = torch.empty_like(pipe.heat)
+    am = torch.empty(2, dtype=torch.int32, device=dev)
+    with torch.cuda.stream(s):
+        tc = vq.vqnnf_filter_responses(pipe.tl, k, bank, stream=s)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps + 1)]
+    for e in ev:
+        for x in e:
+            x.record(s)
+    torch.cuda.synchronize()
+    for i in range(reps + 1):
+        ev[i][0].record(s)
+        vq.vqnnf_set_kernel_events(OP_SCORE, ev[i][1], ev[i][2])
+        vq.vqnnf_score(pipe.ql, k, th, tw, bank, tc, heatmap=heat, argmax_yx=am, ws=ws, stream=s)
+        vq.vqnnf_set_kernel_events(OP_SCORE, None, None)
+        ev[i][3].record(s)
+    torch.cuda.synchronize()
+    call = sorted(e[0].elapsed_time(e[3]) for e in ev[1:])[reps // 2]
+    kern = sorted(e[1].elapsed_time(e[2]) for e in ev[1:])[reps // 2]
+    return {"bank": "F_{2,3-rect}, S=3 (15 filters, 33 rectangles), equal-weight Gaussian reading",
+            "score_call_ms": round(call, 4), "score_kernel_ms": round(kern, 4),
+            "argmax_yx": am.cpu().tolist(), "kernel": "score_generic_kernel"}
 
 
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev):
@@ -496,6 +530,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--query-size", type=int, default=HEADLINE["H"],
                     help="query side (profiling captures on a smaller case)")
+    ap.add_argument("--no-paper-bank", action="store_true",
+                    help="skip scoring with the paper's own filter bank")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision on the same inputs")
     args = ap.parse_args()

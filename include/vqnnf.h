@@ -158,7 +158,9 @@ vqnnf_status vqnnf_assign_noalloc(const float *X, int H, int W, int D, const flo
 /* Template representation vectors (Sec. 3.3, R(tau)): for every filter f and cluster j,
  *   counts[f * k + j] = sum over rects of weight * #{pixels labelled j in the rect}
  * with the window placed at the template's origin.
- *   labels  device, h x w uint8 template NNF, every label < k;  bank: host, F >= 1 filters
+ *   labels  device, h x w uint8 template NNF, every label < k;  bank: host, 1 <= F <= 32
+ *           filters with at most 192 rectangles in total (else VQNNF_EUNSUPPORTED); the
+ *           counts must fit int32 (|weight| * rectangle area summed over a filter)
  *   counts  device, F x k int32, written */
 vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,
                                     const vqnnf_filter *bank, int F, int32_t *counts,

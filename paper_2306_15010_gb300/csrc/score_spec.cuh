@@ -7,7 +7,7 @@
 namespace vqnnf {
 
 constexpr int kMaxFilters = 32;
-constexpr int kMaxRects = 64;
+constexpr int kMaxRects = 192;
 constexpr int kMaxRows = 2 * kMaxRects;
 
 // One weighted half-open rectangle; ry0 / ry1 index the bank's distinct row offsets.

@@ -209,3 +209,70 @@ def grid_bank(th: int, tw: int, g: int, *, full: bool = True):
             bank.append({"rects": [(x0, y0, x1, y1, 1)], "w_f": 1.0,
                          "area": float((x1 - x0) * (y1 - y0))})
     return bank
+
+
+def paper_bank(th: int, tw: int, filters: str = "2,3-rect", S: int = 3, gauss: str = "equal",
+               quant: int = 4096):
+    """The coarse filter bank of the paper's experiments (Sec. 3.2.2, Sec. 4.2 "Filtering",
+    Supp. "Modulating Filter Response Granularity" c): 3 x 3 coarse filters at sub-scales
+    s = 1..S, each a weighted sum of its 9 bin boxes, as integer-weighted rectangles.
+
+    Scale s covers the central (tw // s) x (th // s) region of the window, cut into 3 x 3 bins
+    with floor boundaries.  Filter sets: "gauss" = {Gaussian}, "2-rect" = {Gaussian, Haar-2x,
+    Haar-2y}, "3-rect" = {Gaussian, Haar-3x, Haar-3y}, "2,3-rect" = all five.  Haar kernels on
+    the 3 x 3 bin grid (a reading; the paper prints no layout): 2x = columns (+1, 0, -1),
+    3x = columns (+1, -2, +1), 2y / 3y the same over rows, each multiplied by the Gaussian.
+    Weights w_{s,f} = w_f / s with w_f = 1 (Gaussian) and 0.25 (Haar); the normalising area is
+    the scale's region (Eq. 1: the receptive field).
+
+    gauss = "equal": the paper's stated intent for its sigma = 2 kernel ("equal weights to all
+    the bins"), so every bin weight is the Haar sign pattern; gauss = "exp": the kernel
+    exp(-(i^2 + j^2) / (2 sigma^2)), sigma = 2, at bin offsets i, j in {-1, 0, 1}, with the bin
+    weights rounded to integers at scale `quant` (the filter's w_f is divided by `quant`).
+    """
+    import math
+    sets = {"gauss": ["gauss"], "2-rect": ["gauss", "haar2x", "haar2y"],
+            "3-rect": ["gauss", "haar3x", "haar3y"],
+            "2,3-rect": ["gauss", "haar2x", "haar2y", "haar3x", "haar3y"]}
+    names = sets[filters]
+    pat = {"gauss": lambda i, j: 1, "haar2x": lambda i, j: -j, "haar2y": lambda i, j: -i,
+           "haar3x": lambda i, j: 1 if j else -2, "haar3y": lambda i, j: 1 if i else -2}
+    bank = []
+    for s in range(1, S + 1):
+        ws, hs = tw // s, th // s
+        xo, yo = (tw - ws) // 2, (th - hs) // 2
+        bx = [xo + (q * ws) // 3 for q in range(4)]
+        by = [yo + (q * hs) // 3 for q in range(4)]
+        for name in names:
+            wgt = {}
+            for i in (-1, 0, 1):
+                for j in (-1, 0, 1):
+                    h = pat[name](i, j)
+                    if gauss == "exp":
+                        wgt[(i, j)] = int(round(quant * h * math.exp(-(i * i + j * j) / 8.0)))
+                    else:
+                        wgt[(i, j)] = h
+            rects = []
+            cols_equal = all(wgt[(-1, j)] == wgt[(0, j)] == wgt[(1, j)] for j in (-1, 0, 1))
+            rows_equal = all(wgt[(i, -1)] == wgt[(i, 0)] == wgt[(i, 1)] for i in (-1, 0, 1))
+            if cols_equal and rows_equal:
+                rects.append((bx[0], by[0], bx[3], by[3], wgt[(0, 0)]))
+            elif cols_equal:
+                for j in (-1, 0, 1):
+                    if wgt[(0, j)]:
+                        rects.append((bx[j + 1], by[0], bx[j + 2], by[3], wgt[(0, j)]))
+            elif rows_equal:
+                for i in (-1, 0, 1):
+                    if wgt[(i, 0)]:
+                        rects.append((bx[0], by[i + 1], bx[3], by[i + 2], wgt[(i, 0)]))
+            else:
+                for i in (-1, 0, 1):
+                    for j in (-1, 0, 1):
+                        if wgt[(i, j)]:
+                            rects.append((bx[j + 1], by[i + 1], bx[j + 2], by[i + 2], wgt[(i, j)]))
+            w_f = (1.0 if name == "gauss" else 0.25) / s
+            if gauss == "exp":
+                w_f /= quant
+            bank.append({"rects": rects, "w_f": w_f, "area": float(ws * hs)})
+    return bank
+

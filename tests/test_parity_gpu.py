@@ -200,6 +200,28 @@ def test_score_from_oracle_labels(vq, bank_name, H, W, th, tw, k):
     _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
 
 
+@pytest.mark.parametrize("filters,S,gauss", [("2,3-rect", 3, "equal"), ("2,3-rect", 3, "exp"),
+                                             ("2-rect", 2, "exp"), ("gauss", 1, "equal"),
+                                             ("3-rect", 4, "equal")])
+def test_score_paper_bank(vq, filters, S, gauss):
+    """The paper's coarse Gaussian / Haar filters at sub-scales (multi-rectangle, signed
+    integer weights) through the generic score kernel, against the oracle's direct counts."""
+    H, W, th, tw, k = 90, 150, 36, 44, 9
+    r = np.random.default_rng(31)
+    q = synth.query_map(H, W, 4, M=6, n_sp=90, seed=7)
+    ql = (q.sp_id.numpy() * 5 % k).astype(np.int32)
+    ql[r.random(ql.shape) < 0.05] = r.integers(0, k)
+    t = ql[20:20 + th, 61:61 + tw].copy()
+    bank = synth.paper_bank(th, tw, filters, S, gauss)
+    tc = oracle.filter_counts(t, k, bank)
+    got_tc = vq.vqnnf_filter_responses(_dev(t.astype(np.uint8)), k, bank)
+    assert np.array_equal(got_tc.cpu().numpy(), tc)
+    ref, _ = oracle.score(ql, k, th, tw, bank, tc)
+    heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank, _dev(tc.astype(np.int32)))
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+    assert tuple(am.cpu().tolist()) == (20, 61) or ref[20, 61] == ref.max()
+
+
 def test_score_k1_and_whole_query(vq):
     ql = np.zeros((50, 40), np.int32)
     bank = synth.grid_bank(10, 8, 3)
