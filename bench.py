@@ -451,7 +451,7 @@ def run_paper_bank(vq, pipe, cfg, s, dev, reps=5):
     kern = sorted(e[1].elapsed_time(e[2]) for e in ev[1:])[reps // 2]
     return {"bank": "F_{2,3-rect}, S=3 (15 filters, 33 rectangles), equal-weight Gaussian reading",
             "score_call_ms": round(call, 4), "score_kernel_ms": round(kern, 4),
-            "argmax_yx": am.cpu().tolist(), "kernel": "score_generic_kernel"}
+            "argmax_yx": am.cpu().tolist(), "kernel": "score_wgrid_kernel (weighted 3 x 3 grids, one per sub-scale)"}
 
 
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev):

@@ -173,6 +173,77 @@ void kmeans_init_indices(long long l, int k, uint64_t seed, int32_t *out)
 // ----------------------------------------------------------------------------------
 // Filter banks.
 // ----------------------------------------------------------------------------------
+// Weighted-grid detection: the filters fall into at most four groups by bounding box; within
+// a group, the distinct column and row boundaries of its rectangles (at most four each) cut
+// the box into a 3 x 3 grid (repeated last boundaries give empty cells), every rectangle is a
+// union of whole cells, and each filter becomes its cell weights.  Counts and per-window L1
+// sums must stay inside int32.
+void detect_wgrid(const vqnnf_filter *bank, int F, const BankSpec &bs, WGridSpec &ws)
+{
+    memset(&ws, 0, sizeof(ws));
+    int gbox[kMaxWGrids][4];
+    int ng = 0;
+    for (int f = 0; f < F; ++f) {
+        int bb[4] = {1 << 30, 1 << 30, -1, -1};
+        for (int r = 0; r < bank[f].n_rects; ++r) {
+            const vqnnf_rect &rc = bank[f].rects[r];
+            bb[0] = std::min(bb[0], rc.x0); bb[1] = std::min(bb[1], rc.y0);
+            bb[2] = std::max(bb[2], rc.x1); bb[3] = std::max(bb[3], rc.y1);
+        }
+        int g = 0;
+        while (g < ng && !(gbox[g][0] == bb[0] && gbox[g][1] == bb[1] && gbox[g][2] == bb[2] && gbox[g][3] == bb[3]))
+            ++g;
+        if (g == ng) {
+            if (ng == kMaxWGrids) return;
+            for (int q = 0; q < 4; ++q) gbox[ng][q] = bb[q];
+            ++ng;
+        }
+        if (ws.nf[g] == kMaxWFilters) { ws.nf[0] = 0; return; }
+        ws.filt[g][ws.nf[g]++] = f;
+    }
+    for (int g = 0; g < ng; ++g) {
+        int xs[2 * kMaxRects], ys[2 * kMaxRects], nx = 0, ny = 0;
+        for (int q = 0; q < ws.nf[g]; ++q) {
+            const vqnnf_filter &fl = bank[ws.filt[g][q]];
+            for (int r = 0; r < fl.n_rects; ++r) {
+                xs[nx++] = fl.rects[r].x0; xs[nx++] = fl.rects[r].x1;
+                ys[ny++] = fl.rects[r].y0; ys[ny++] = fl.rects[r].y1;
+            }
+        }
+        std::sort(xs, xs + nx);
+        nx = int(std::unique(xs, xs + nx) - xs);
+        std::sort(ys, ys + ny);
+        ny = int(std::unique(ys, ys + ny) - ys);
+        if (nx > 4 || ny > 4) { memset(&ws, 0, sizeof(ws)); return; }
+        for (int q = 0; q < 4; ++q) {
+            ws.bx[g][q] = xs[std::min(q, nx - 1)];
+            ws.by[g][q] = ys[std::min(q, ny - 1)];
+        }
+        for (int q = 0; q < ws.nf[g]; ++q) {
+            const int f = ws.filt[g][q];
+            const vqnnf_filter &fl = bank[f];
+            long long absw = 0;
+            for (int r = 0; r < fl.n_rects; ++r) {
+                const vqnnf_rect &rc = fl.rects[r];
+                const int a = int(std::lower_bound(xs, xs + nx, rc.x0) - xs);
+                const int b = int(std::lower_bound(xs, xs + nx, rc.x1) - xs);
+                const int c = int(std::lower_bound(ys, ys + ny, rc.y0) - ys);
+                const int d = int(std::lower_bound(ys, ys + ny, rc.y1) - ys);
+                for (int rr = c; rr < d; ++rr)
+                    for (int cc = a; cc < b; ++cc) ws.w[g][q][rr * 3 + cc] += rc.weight;
+                absw += (long long)std::abs(rc.weight) * (rc.x1 - rc.x0) * (rc.y1 - rc.y0);
+            }
+            // |R| <= absw per cluster; sum_j |t - R| <= 2 absw (t and R are sums over the
+            // same pixels with the same weights)
+            if (2 * absw >= (1ll << 31)) { memset(&ws, 0, sizeof(ws)); return; }
+            ws.coef[g][q] = bs.coef[f];
+        }
+    }
+    ws.NG = ng;
+    ws.ncol = bs.ncol;
+    if (!score_grid_fits(bs.ncol)) ws.NG = 0;
+}
+
 vqnnf_status compile_bank(const vqnnf_filter *bank, int F, int th, int tw, BankSpec &bs,
                           GridSpec &gs)
 {
@@ -407,10 +478,14 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
         return VQNNF_ENOMEM;
     BankSpec bs;
     GridSpec gs;
+    WGridSpec wg;
     vqnnf_status st = compile_bank(bank, F, th, tw, bs, gs);
     if (st != VQNNF_OK) return st;
+    memset(&wg, 0, sizeof(wg));
+    if (gs.G == 0) detect_wgrid(bank, F, bs, wg);
     const bool u16 = sat_is_u16(th, tw);
-    const size_t smem = score_smem_bytes_for(u16 ? 2 : 4, bs, gs, k);
+    const size_t smem = wg.NG > 0 ? score_wgrid_smem_bytes(u16 ? 2 : 4, wg, k)
+                                  : score_smem_bytes_for(u16 ? 2 : 4, bs, gs, k);
     if (smem > (size_t)device_smem_optin()) return VQNNF_EUNSUPPORTED;
     cudaStream_t s = as_stream(stream);
     WsCursor c{static_cast<char *>(ws), 0};
@@ -418,7 +493,7 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
     cudaError_t e = launch_sat(q_labels, H, W, k, sw.u16, sw.carry, sw.bandsum, sw.S, s);
     if (e != cudaSuccess) return from_cuda(e);
     const int HO = H - th + 1, WO = W - tw + 1;
-    return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, t_counts, heatmap, sw.amax,
+    return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, wg, t_counts, heatmap, sw.amax,
                                   argmax_yx, s));
 }
 

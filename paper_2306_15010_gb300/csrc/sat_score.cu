@@ -417,6 +417,142 @@ __global__ void __launch_bounds__(STH, 6) score_grid_kernel(const T *__restrict_
     }
 }
 
+// Weighted-grid bank (WGridSpec): grid by grid, one pass over the clusters stages that grid's
+// four corner rows; per cluster and window the 16 corners give the 9 cell counts, each of the
+// grid's filters is their integer weighting R, and |t - R| is summed exactly per filter.  The
+// weights and coefficients are kernel parameters indexed at compile time.  After each grid's
+// pass its filters' sums enter the float heatmap accumulator (fixed order).
+template <typename T, int NG, int NCOLP>
+__global__ void __launch_bounds__(STH, 6) score_wgrid_kernel(const T *__restrict__ S, int P, int k,
+                                                          int HO, int WO, WGridSpec ws,
+                                                          const int32_t *__restrict__ tcounts,
+                                                          float *__restrict__ heat,
+                                                          unsigned long long *amax)
+{
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    const int ncol = ws.ncol;
+    constexpr int chunk_elems = 4 * NCOLP;                    // one cluster, four corner rows
+    T *bufs = reinterpret_cast<T *>(smem_raw);                 // [NBUF][chunk]
+    int *tc = reinterpret_cast<int *>(bufs + NBUF * chunk_elems);   // [NG][5][k]
+    uint64_t *full = reinterpret_cast<uint64_t *>(tc + NG * kMaxWFilters * k + ((NG * kMaxWFilters * k) & 1));
+    uint64_t *empty = full + NBUF;
+    int *n_issued = reinterpret_cast<int *>(empty + NBUF);
+    const int y = blockIdx.y;
+    const int x0 = blockIdx.x * TXW;
+    const int lane = threadIdx.x & 31;
+    const int nchunk = NG * k;                                 // chunk ci: grid ci / k, cluster ci % k
+    for (int q = threadIdx.x; q < NG * kMaxWFilters * k; q += blockDim.x) {
+        const int gf = q / k, j = q % k, g = gf / kMaxWFilters, f = gf % kMaxWFilters;
+        tc[q] = f < ws.nf[g] ? tcounts[(size_t)ws.filt[g][f] * k + j] : 0;
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < NBUF; ++b) {
+            ptx::mbar_init(&full[b], 1);
+            ptx::mbar_init(&empty[b], STH / 32);
+        }
+        ptx::fence_barrier_init();
+        int c = 0;
+        for (; c < NBUF - 1 && c < nchunk; ++c)
+            issue_chunk<T>(bufs + c * chunk_elems, S, k, P, y, x0, c % k, ncol, NCOLP, ws.by[c / k], 4, &full[c]);
+        *n_issued = c;
+    }
+    __syncthreads();
+    float hs[WPT];
+#pragma unroll
+    for (int w = 0; w < WPT; ++w) hs[w] = 0.f;
+    bool ok = true;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int nf = ws.nf[g];
+        int acc[WPT][kMaxWFilters];
+#pragma unroll
+        for (int w = 0; w < WPT; ++w)
+#pragma unroll
+            for (int f = 0; f < kMaxWFilters; ++f) acc[w][f] = 0;
+        int off[4];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) off[cc] = ws.bx[g][cc];
+        for (int j = 0; ok && j < k; ++j) {
+            const int ch = g * k + j;
+            const int b = ch % NBUF;
+            if (threadIdx.x == 0 && ch + NBUF - 1 < nchunk) {
+                const int nb = (ch + NBUF - 1) % NBUF;
+                const int use = (ch + NBUF - 1) / NBUF;
+                if (use > 0)
+                    ok = ptx::mbar_wait_bounded(&empty[nb], (use - 1) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
+                if (ok) {
+                    const int cn = ch + NBUF - 1;
+                    issue_chunk<T>(bufs + nb * chunk_elems, S, k, P, y, x0, cn % k, ncol, NCOLP, ws.by[cn / k], 4,
+                                   &full[nb]);
+                    *n_issued = cn + 1;
+                }
+            }
+            ok = __all_sync(0xffffffffu, ok && ptx::mbar_wait_bounded(&full[b], (ch / NBUF) & 1, &g_score_error,
+                                                                      (int)VQNNF_ETIMEOUT));
+            if (!ok) break;
+            const T *cur = bufs + b * chunk_elems + threadIdx.x;
+            int t[kMaxWFilters];
+#pragma unroll
+            for (int f = 0; f < kMaxWFilters; ++f) t[f] = tc[(g * kMaxWFilters + f) * k + j];
+#pragma unroll
+            for (int w = 0; w < WPT; ++w) {
+                int cr[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) cr[r][cc] = (int)cur[off[cc] + r * NCOLP + w * STH];
+                int n[9];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        n[r * 3 + cc] = box<T>(cr[r + 1][cc + 1], cr[r + 1][cc], cr[r][cc + 1], cr[r][cc]);
+#pragma unroll
+                for (int f = 0; f < kMaxWFilters; ++f) {
+                    if (f >= nf) break;
+                    int R = 0;
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) R += ws.w[g][f][c] * n[c];
+                    acc[w][f] += abs(t[f] - R);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(&empty[b]))
+                                        : "memory");
+        }
+#pragma unroll
+        for (int f = 0; f < kMaxWFilters; ++f) {
+            if (f >= nf) break;
+#pragma unroll
+            for (int w = 0; w < WPT; ++w) hs[w] = fmaf(ws.coef[g][f], (float)acc[w][f], hs[w]);
+        }
+    }
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) {
+        const int issued = *n_issued;
+        for (int c = max(0, issued - NBUF); c < issued; ++c)
+            ptx::mbar_wait_bounded(&full[c % NBUF], (c / NBUF) & 1, &g_score_error, (int)VQNNF_ETIMEOUT);
+    }
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int w = 0; w < WPT; ++w) {
+        const int x = x0 + threadIdx.x + w * STH;
+        const float h = -hs[w];
+        if (ok && x < WO) {
+            heat[(size_t)y * WO + x] = h;
+            const unsigned long long key = pack_key(h, (unsigned)(y * WO + x));
+            best = key > best ? key : best;
+        }
+    }
+    if (amax) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if ((threadIdx.x & 31) == 0 && best) atomicMax(amax, best);
+    }
+}
+
 // Generic bank: any weighted half-open rectangles.  Corner rows are the distinct row
 // offsets of the bank; each rectangle reads its four corners from shared memory.
 template <typename T>
@@ -551,9 +687,30 @@ cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, in
     return cudaGetLastError();
 }
 
+template <typename T, int NG>
+cudaError_t launch_wgrid(const T *S, int P, int k, int HO, int WO, const WGridSpec &ws, const int32_t *tc,
+                         float *heat, unsigned long long *amax, cudaStream_t s)
+{
+    const size_t smem = score_wgrid_smem_bytes(sizeof(T), ws, k);
+    dim3 grid((WO + TXW - 1) / TXW, HO);
+    cudaError_t e;
+    if (ws.ncol <= TXW + 128) {
+        e = cudaFuncSetAttribute(score_wgrid_kernel<T, NG, TXW + 128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        score_wgrid_kernel<T, NG, TXW + 128><<<grid, STH, smem, s>>>(S, P, k, HO, WO, ws, tc, heat, amax);
+    } else {
+        e = cudaFuncSetAttribute(score_wgrid_kernel<T, NG, TXW + 256>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        score_wgrid_kernel<T, NG, TXW + 256><<<grid, STH, smem, s>>>(S, P, k, HO, WO, ws, tc, heat, amax);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankSpec &bs,
-                           const GridSpec &gs, const int32_t *tc, float *heat,
+                           const GridSpec &gs, const WGridSpec &ws, const int32_t *tc, float *heat,
                            unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s)
 {
     const int P = sat_pitch(W);
@@ -573,6 +730,15 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
     VQNNF_GRID_CASE(2, true) VQNNF_GRID_CASE(3, false) VQNNF_GRID_CASE(3, true)
     VQNNF_GRID_CASE(4, false) VQNNF_GRID_CASE(4, true)
 #undef VQNNF_GRID_CASE
+    if (!done && ws.NG > 0) {
+        switch (ws.NG) {
+        case 1: e = launch_wgrid<T, 1>(S, P, k, HO, WO, ws, tc, heat, amax, s); break;
+        case 2: e = launch_wgrid<T, 2>(S, P, k, HO, WO, ws, tc, heat, amax, s); break;
+        case 3: e = launch_wgrid<T, 3>(S, P, k, HO, WO, ws, tc, heat, amax, s); break;
+        default: e = launch_wgrid<T, 4>(S, P, k, HO, WO, ws, tc, heat, amax, s); break;
+        }
+        done = true;
+    }
     if (!done) {
         GridSpec none;
         none.G = 0;
@@ -599,6 +765,13 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
 // to 256; wider templates take the generic kernel).
 int score_grid_pitch(int ncol) { return ncol <= TXW + 128 ? TXW + 128 : TXW + 256; }
 bool score_grid_fits(int ncol) { return ncol <= TXW + 256; }
+
+size_t score_wgrid_smem_bytes(size_t elem, const WGridSpec &ws, int k)
+{
+    return elem * (size_t)NBUF * 4 * score_grid_pitch(ws.ncol) + sizeof(int) * ((size_t)ws.NG * kMaxWFilters * k + 1) +
+           sizeof(uint64_t) * 2 * NBUF + 16 + 16;
+}
+
 
 size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs, int k)
 {
@@ -634,13 +807,13 @@ cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, con
 }
 
 cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, const BankSpec &bs,
-                         const GridSpec &gs, const int32_t *tc, float *heat,
+                         const GridSpec &gs, const WGridSpec &ws, const int32_t *tc, float *heat,
                          unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s)
 {
-    return u16 ? launch_score_t<uint16_t>(static_cast<const uint16_t *>(S), W, k, HO, WO, bs, gs, tc, heat,
-                                          amax, argmax_yx, s)
-               : launch_score_t<uint32_t>(static_cast<const uint32_t *>(S), W, k, HO, WO, bs, gs, tc, heat,
-                                          amax, argmax_yx, s);
+    return u16 ? launch_score_t<uint16_t>(static_cast<const uint16_t *>(S), W, k, HO, WO, bs, gs, ws, tc,
+                                          heat, amax, argmax_yx, s)
+               : launch_score_t<uint32_t>(static_cast<const uint32_t *>(S), W, k, HO, WO, bs, gs, ws, tc,
+                                          heat, amax, argmax_yx, s);
 }
 
 cudaError_t read_and_clear_score_error(int *out)

@@ -44,7 +44,25 @@ struct GridSpec {
     float coef[kMaxFilters];
 };
 
+// Weighted-grid bank: every filter is an integer weighting of the 3 x 3 cells of one of up to
+// four grids (cells cut by column boundaries bx[g][0..3] and row boundaries by[g][0..3]; a
+// boundary may repeat, giving empty cells), at most five filters per grid.  The coarse
+// Gaussian / Haar filters of the paper at sub-scales have this form.
+constexpr int kMaxWGrids = 4;
+constexpr int kMaxWFilters = 5;
+struct WGridSpec {
+    int NG;                                   // 0 = not a weighted-grid bank
+    int ncol;
+    int nf[kMaxWGrids];
+    int bx[kMaxWGrids][4];
+    int by[kMaxWGrids][4];
+    int w[kMaxWGrids][kMaxWFilters][9];       // cell weights, cell r * 3 + c
+    int filt[kMaxWGrids][kMaxWFilters];       // bank index of the filter
+    float coef[kMaxWGrids][kMaxWFilters];     // w_f / A_f
+};
+
 size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs, int k);
+size_t score_wgrid_smem_bytes(size_t elem, const WGridSpec &ws, int k);
 bool sat_is_u16(int th, int tw);
 int sat_pitch(int W);
 int sat_strips(int W);
@@ -57,7 +75,7 @@ cudaError_t launch_sat(const uint8_t *lab, int H, int W, int k, bool u16, int *c
 cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, const BankSpec &bs,
                                     int32_t *counts, cudaStream_t s);
 cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, const BankSpec &bs,
-                         const GridSpec &gs, const int32_t *tc, float *heat,
+                         const GridSpec &gs, const WGridSpec &ws, const int32_t *tc, float *heat,
                          unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s);
 cudaError_t read_and_clear_score_error(int *out);
 
