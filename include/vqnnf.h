@@ -182,6 +182,36 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
                          float *heatmap, int32_t *argmax_yx,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Soft-VQ heatmap (training path): the differentiable reading of Algorithm 1, Eq. 1 and
+ * Eq. 2.  Every pixel is soft-assigned, p_j(x) = softmax_j(-||x - c_j||^2 / tau); the soft
+ * counts of cell f of a G x G grid over the template window (floor boundaries, Sec. 3.2.1)
+ * are the sums of p over the cell, T_fj for the template and Q_fj(y, x) for the query window
+ * at (y, x); the heatmap is Eq. 2 with the L1 norm over clusters,
+ *     heat[b][y][x] = - sum_f (wf[f] / A_f) sum_j | T_fj - Q_fj(b, y, x) |,
+ * A_f the cell area, wf learnable.  All FP32.
+ *   Qf    device, B x H x W x D float32 (HWC per query);  Tf: device, th x tw x D;
+ *   C     device, k x D;  tau > 0;  1 <= G <= 4;  wf: device, G*G float32
+ *   heat  device, B x (H - th + 1) x (W - tw + 1) float32, written
+ *   ws    device workspace of vqnnf_soft_workspace_bytes() bytes, 256-byte aligned; it keeps
+ *         the template soft counts, the query cell sums and the per-filter L1 maps for the
+ *         backward call with the same arguments (the softmax itself is recomputed there).
+ * Limits: k <= 128, D <= 512, k * D <= 32768, B * k <= 65535 (else VQNNF_EUNSUPPORTED). */
+size_t vqnnf_soft_workspace_bytes(int B, int H, int W, int D, int k, int th, int tw, int G);
+vqnnf_status vqnnf_soft_forward(const float *Qf, int B, int H, int W, const float *Tf, int th, int tw,
+                                int D, const float *C, int k, float tau, int G, const float *wf,
+                                float *heat, void *ws, size_t ws_bytes, void *stream);
+
+/* Gradients of L = sum heat * dheat after vqnnf_soft_forward with the same arguments and
+ * workspace: dQf (B x H x W x D), dC (k x D: query and template soft assignments both
+ * contribute) and dwf (G*G), all device float32, written.  |.| has subgradient sign(0) = 0;
+ * dL/dT accumulates with float atomics, so the centroid gradient may differ in the last bits
+ * between runs. */
+vqnnf_status vqnnf_soft_backward(const float *Qf, int B, int H, int W, const float *Tf, int th,
+                                 int tw, int D, const float *C, int k, float tau, int G,
+                                 const float *wf, const float *dheat, float *dQf, float *dC,
+                                 float *dwf, void *ws, size_t ws_bytes, void *stream);
+
 /* Profiling aid (the paper has no counterpart).  After
  * vqnnf_set_kernel_events(op, start, stop) with op = VQNNF_OP_ASSIGN or VQNNF_OP_SCORE and
  * two CUDA event handles (cudaEvent_t, created and owned by the caller, timing enabled),

@@ -19,3 +19,4 @@ from .api import (  # noqa: F401
     Workspace,
 )
 from ._lib import VqnnfError  # noqa: F401
+from .soft import SoftHeatmap, soft_heatmap, soft_workspace_bytes  # noqa: F401

@@ -29,6 +29,11 @@ SIGNATURES = {
     "vqnnf_status_str": (ctypes.c_char_p, [_i]),
     "vqnnf_last_device_error": (_i, [_vp]),
     "vqnnf_set_kernel_events": (_i, [_i, _vp, _vp]),
+    "vqnnf_soft_workspace_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i, _i]),
+    "vqnnf_soft_forward": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _vp, _i, ctypes.c_float, _i, _vp, _vp,
+                                _vp, ctypes.c_size_t, _vp]),
+    "vqnnf_soft_backward": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _vp, _i, ctypes.c_float, _i, _vp, _vp,
+                                 _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "vqnnf_version": (_i, []),
 }
 

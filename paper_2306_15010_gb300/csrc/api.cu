@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "score_spec.cuh"
+#include "soft_spec.cuh"
 
 using namespace vqnnf;
 
@@ -495,6 +496,58 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
     const int HO = H - th + 1, WO = W - tw + 1;
     return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, wg, t_counts, heatmap, sw.amax,
                                   argmax_yx, s));
+}
+
+// ------------------------------------------------------------------ soft-VQ heatmap
+static vqnnf_status soft_check(const void *Qf, int B, int H, int W, const void *Tf, int th, int tw, int D,
+                               const void *C, int k, float tau, int G, SoftGrid &sg)
+{
+    if (!Qf || !Tf || !C || B < 1 || H < 1 || W < 1 || th < 1 || tw < 1 || th > H || tw > W || D < 1 ||
+        k < 1 || !(tau > 0.f) || !std::isfinite(tau))
+        return VQNNF_EINVAL;
+    if (k > kSoftMaxK || D > 512 || (long long)k * D > 32768 || (long long)B * k > 65535 ||
+        (long long)B * k * H * W >= (1ll << 40))
+        return VQNNF_EUNSUPPORTED;
+    if (!soft_grid(th, tw, G, sg)) return G < 1 || G > kSoftMaxG ? VQNNF_EUNSUPPORTED : VQNNF_EINVAL;
+    return VQNNF_OK;
+}
+
+size_t vqnnf_soft_workspace_bytes(int B, int H, int W, int D, int k, int th, int tw, int G)
+{
+    SoftGrid sg;
+    if (B < 1 || H < 1 || W < 1 || th < 1 || tw < 1 || th > H || tw > W || k < 1 || D < 1 ||
+        !soft_grid(th, tw, G, sg))
+        return 0;
+    return soft_workspace_bytes(B, H, W, D, k, th, tw, sg);
+}
+
+vqnnf_status vqnnf_soft_forward(const float *Qf, int B, int H, int W, const float *Tf, int th, int tw, int D,
+                                const float *C, int k, float tau, int G, const float *wf, float *heat,
+                                void *ws, size_t ws_bytes, void *stream)
+{
+    SoftGrid sg;
+    vqnnf_status st = soft_check(Qf, B, H, W, Tf, th, tw, D, C, k, tau, G, sg);
+    if (st != VQNNF_OK) return st;
+    if (!wf || !heat || !ws || !aligned(ws, 256)) return VQNNF_EINVAL;
+    if (ws_bytes < soft_workspace_bytes(B, H, W, D, k, th, tw, sg)) return VQNNF_ENOMEM;
+    WsCursor c{static_cast<char *>(ws), 0};
+    SoftWs w = carve_soft(c, B, H, W, D, k, th, tw, sg);
+    return from_cuda(soft_forward(Qf, B, H, W, Tf, th, tw, D, C, k, tau, sg, wf, heat, w, as_stream(stream)));
+}
+
+vqnnf_status vqnnf_soft_backward(const float *Qf, int B, int H, int W, const float *Tf, int th, int tw, int D,
+                                 const float *C, int k, float tau, int G, const float *wf, const float *dheat,
+                                 float *dQf, float *dC, float *dwf, void *ws, size_t ws_bytes, void *stream)
+{
+    SoftGrid sg;
+    vqnnf_status st = soft_check(Qf, B, H, W, Tf, th, tw, D, C, k, tau, G, sg);
+    if (st != VQNNF_OK) return st;
+    if (!wf || !dheat || !dQf || !dC || !dwf || !ws || !aligned(ws, 256)) return VQNNF_EINVAL;
+    if (ws_bytes < soft_workspace_bytes(B, H, W, D, k, th, tw, sg)) return VQNNF_ENOMEM;
+    WsCursor c{static_cast<char *>(ws), 0};
+    SoftWs w = carve_soft(c, B, H, W, D, k, th, tw, sg);
+    return from_cuda(soft_backward(Qf, B, H, W, Tf, th, tw, D, C, k, tau, sg, wf, dheat, dQf, dC, dwf, w,
+                                   as_stream(stream)));
 }
 
 vqnnf_status vqnnf_set_kernel_events(int op, void *start_event, void *stop_event)

@@ -1,0 +1,63 @@
+"""Soft-VQ heatmap and gradients on the GPU (through torch.autograd and the C ABI) against the
+FP64 oracle (oracle/soft.py).  Tolerances: FP32 soft assignment and direct cell sums give the
+heatmap to ~1e-6 relative (bar: 1e-4 of max |H|); gradients to 1e-3 of their largest entry
+(sign(Q - T) can flip only where Q and T agree to FP32 rounding)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import soft as osoft
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vq():
+    from paper_2306_15010_gb300 import build
+    build.build()
+    import paper_2306_15010_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _case(B, H, W, D, k, th, tw, seed):
+    r = np.random.default_rng(seed)
+    C = r.normal(0, 1, (k, D)).astype(np.float32)
+    lab = r.integers(0, k, (B, H, W))
+    Q = (C[lab] + r.normal(0, 0.6, (B, H, W, D))).astype(np.float32)
+    T = (Q[0, 2:2 + th, 3:3 + tw] + r.normal(0, 0.2, (th, tw, D))).astype(np.float32)
+    return Q, T, C
+
+
+@pytest.mark.parametrize("B,H,W,D,k,th,tw,G,tau", [
+    (2, 40, 37, 12, 10, 16, 14, 3, 0.3),
+    (1, 64, 64, 16, 8, 21, 24, 3, 0.1),      # the FD instance of the differentiation workload
+    (1, 48, 52, 256, 64, 18, 20, 3, 0.1),    # the workload's D and k
+    (3, 20, 23, 5, 3, 9, 8, 2, 1.0),
+])
+def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
+    Q, T, C = _case(B, H, W, D, k, th, tw, seed=B * 100 + H)
+    r = np.random.default_rng(9)
+    wf = r.uniform(0.5, 1.5, G * G).astype(np.float32)
+    Gw = r.normal(0, 1, (B, H - th + 1, W - tw + 1)).astype(np.float32)
+    Qd = torch.tensor(Q, device="cuda", requires_grad=True)
+    Cd = torch.tensor(C, device="cuda", requires_grad=True)
+    wd = torch.tensor(wf, device="cuda", requires_grad=True)
+    heat = vq.soft_heatmap(Qd, torch.tensor(T, device="cuda"), Cd, wd, tau, G)
+    (heat * torch.tensor(Gw, device="cuda")).sum().backward()
+    ref = osoft.soft_forward(Q, T, C, tau, G, wf)["heat"]
+    got = heat.detach().cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    dQ, dC, dw = osoft.soft_backward(Q, T, C, tau, G, wf, Gw)
+    for name, g, rr in (("dQ", Qd.grad, dQ), ("dC", Cd.grad, dC), ("dw", wd.grad, dw)):
+        g = g.cpu().numpy()
+        assert np.abs(g - rr).max() <= 1e-3 * np.abs(rr).max(), name
+
+
+def test_soft_limits(vq):
+    Q, T, C = _case(1, 12, 12, 4, 3, 6, 6, seed=1)
+    t = lambda a: torch.tensor(a, device="cuda")
+    with pytest.raises(vq.VqnnfError):
+        vq.soft_heatmap(t(Q), t(T), t(np.zeros((129, 4), np.float32)), t(np.ones(9, np.float32)), 0.1, 3)
+    with pytest.raises(vq.VqnnfError):
+        vq.soft_heatmap(t(Q), t(T), t(C), t(np.ones(25, np.float32)), 0.1, 5)
