@@ -333,6 +333,7 @@ def run_gpu(args, rank, world):
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev)
     paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
+    soft_vq = None if args.no_soft else run_soft(vq, dev)
 
     if rank != 0:
         return None
@@ -360,7 +361,7 @@ def run_gpu(args, rank, world):
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "roofline_score": roof_score, "clocks": clocks, "e2e": e2e,
-        "paper_bank": paper,
+        "paper_bank": paper, "soft_vq": soft_vq,
         f"{other}_path": None if ms2 is None else {
             "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
             "ms_per_step": round(ms2, 4),
@@ -452,6 +453,42 @@ def run_paper_bank(vq, pipe, cfg, s, dev, reps=5):
     return {"bank": "F_{2,3-rect}, S=3 (15 filters, 33 rectangles), equal-weight Gaussian reading",
             "score_call_ms": round(call, 4), "score_kernel_ms": round(kern, 4),
             "argmax_yx": am.cpu().tolist(), "kernel": "score_wgrid_kernel (weighted 3 x 3 grids, one per sub-scale)"}
+
+
+def run_soft(vq, dev, reps=3):
+    """The training path: soft-VQ heatmap of 8 queries 512 x 512, D = 256, k = 64, 3 x 3 cell
+    filters (learnable weights, 1 at start), tau = 0.1; forward and backward (gradients for the
+    query features, the centroids and the weights of L = sum heat * N(0,1) weights)."""
+    import torch
+    import synth
+    B, H, W, D, k, th, tw, G, tau = 8, 512, 512, 256, 64, 64, 64, 3, 0.1
+    Q = torch.stack([synth.query_map(H, W, D, M=64, n_sp=1250, seed=4000 + i, device=dev).X for i in range(B)])
+    T, _ = synth.crop_template(synth.query_map(H, W, D, M=64, n_sp=1250, seed=4000, device=dev), th, tw, seed=4100)
+    T = T.to(dev).contiguous()
+    g = torch.Generator(device="cpu").manual_seed(4200)
+    C = (torch.rand((k, D), generator=g) * 0.8 + 0.1).to(dev)
+    Gw = torch.randn((B, H - th + 1, W - tw + 1), generator=g).to(dev)
+    Q.requires_grad_(True)
+    C.requires_grad_(True)
+    wf = torch.ones(G * G, device=dev, requires_grad=True)
+    fw, bw = [], []
+    for r in range(reps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        heat = vq.soft_heatmap(Q, T, C, wf, tau, G)
+        e[1].record()
+        (heat * Gw).sum().backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if r:
+            fw.append(e[0].elapsed_time(e[1]))
+            bw.append(e[1].elapsed_time(e[2]))
+        Q.grad = C.grad = wf.grad = None
+    f_ms, b_ms = sorted(fw)[reps // 2], sorted(bw)[reps // 2]
+    return {"workload": "8 queries 512x512, D=256, k=64, 64x64 template, 3x3 cells (F=9), tau=0.1",
+            "forward_ms": round(f_ms, 3), "backward_ms": round(b_ms, 3),
+            "train_step_mpix_s": round(B * H * W / ((f_ms + b_ms) * 1e-3) / 1e6, 2),
+            "note": "backward includes the autograd engine's elementwise product and sum of the loss"}
 
 
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev):
@@ -561,6 +598,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--query-size", type=int, default=HEADLINE["H"],
                     help="query side (profiling captures on a smaller case)")
+    ap.add_argument("--no-soft", action="store_true", help="skip the soft-VQ training-path timing")
     ap.add_argument("--no-paper-bank", action="store_true",
                     help="skip scoring with the paper's own filter bank")
     ap.add_argument("--no-compare", action="store_true",
