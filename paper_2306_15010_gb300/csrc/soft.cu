@@ -27,20 +27,24 @@
 namespace vqnnf {
 namespace {
 
-constexpr int PT = 64;            // pixels per tile of the soft-assignment kernels
-constexpr int DCH = 32;           // feature dimensions staged per chunk
-constexpr int KQ = kSoftMaxK / 4; // centroids per thread (four threads per pixel)
+constexpr int PT = 64;             // pixels per tile of the soft-assignment kernels
+constexpr int DCH = 32;            // feature dimensions staged per chunk
+constexpr int KI = kSoftMaxK / 16; // centroids per thread: thread (pg, cl) holds j = cl + 16 i
+constexpr int PPT = 4;             // pixels per thread: pg * 4 .. pg * 4 + 3
 
-// Distances of a 64-pixel tile to all k centroids, four threads per pixel (thread 4p + q holds
-// centroids q, q + 4, ...), then the softmax over the pixel's k logits.  X rows are pixels.
+// Distances of a 64-pixel tile to all k centroids and the softmax over each pixel's k logits.
+// Thread t = 16 pg + cl owns pixels 4 pg .. 4 pg + 3 and centroids cl, cl + 16, ...; the 16
+// threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.
 __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long long n, long long p0, int D,
                                              const float *__restrict__ C, int k, float tau, float (*xs)[DCH + 1],
-                                             float (*cs)[DCH + 1], float *pr)
+                                             float (*cs)[DCH + 1], float (*pr)[KI])
 {
-    const int t = threadIdx.x, p = t >> 2, q = t & 3;
-    float acc[KQ];
+    const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
+    float acc[PPT][KI];
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) acc[i] = 0.f;
+    for (int r = 0; r < PPT; ++r)
+#pragma unroll
+        for (int i = 0; i < KI; ++i) acc[r][i] = 0.f;
     for (int d0 = 0; d0 < D; d0 += DCH) {
         __syncthreads();
         for (int e = t; e < PT * DCH; e += blockDim.x) {
@@ -53,86 +57,111 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
             cs[j][dd] = d0 + dd < D ? C[(size_t)j * D + d0 + dd] : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int dd = 0; dd < DCH; ++dd) {
-            const float x = xs[p][dd];
+            float xv[PPT], cv[KI];
 #pragma unroll
-            for (int i = 0; i < KQ; ++i) {
-                const int j = q + 4 * i;
-                if (j < k) {
-                    const float df = x - cs[j][dd];
-                    acc[i] = fmaf(df, df, acc[i]);
+            for (int r = 0; r < PPT; ++r) xv[r] = xs[pg * PPT + r][dd];
+#pragma unroll
+            for (int i = 0; i < KI; ++i) cv[i] = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : 0.f;
+#pragma unroll
+            for (int r = 0; r < PPT; ++r)
+#pragma unroll
+                for (int i = 0; i < KI; ++i) {
+                    const float df = xv[r] - cv[i];
+                    acc[r][i] = fmaf(df, df, acc[r][i]);
                 }
-            }
         }
     }
-    float dmin = FLT_MAX;
-#pragma unroll
-    for (int i = 0; i < KQ; ++i)
-        if (q + 4 * i < k) dmin = fminf(dmin, acc[i]);
-    dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 1));
-    dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, 2));
-    float s = 0.f;
     const float it = 1.0f / tau;
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-        const float e = q + 4 * i < k ? expf((dmin - acc[i]) * it) : 0.f;
-        acc[i] = e;
-        s += e;
-    }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    const float inv = 1.0f / s;
+    for (int r = 0; r < PPT; ++r) {
+        float dmin = FLT_MAX;
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) pr[i] = acc[i] * inv;
+        for (int i = 0; i < KI; ++i)
+            if (cl + 16 * i < k) dmin = fminf(dmin, acc[r][i]);
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+            const float e = cl + 16 * i < k ? expf((dmin - acc[r][i]) * it) : 0.f;
+            acc[r][i] = e;
+            s += e;
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const float inv = 1.0f / s;
+#pragma unroll
+        for (int i = 0; i < KI; ++i) pr[r][i] = acc[r][i] * inv;
+    }
 }
 
-// p planar: P[(item * k + j) * npi + pixel]
+// p planar: P[(item * k + j) * npi + pixel], written through a shared-memory transpose so that
+// consecutive threads store consecutive pixels of one plane.
 __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
                                                      int D, const float *__restrict__ C, int k, float tau,
                                                      float *__restrict__ P)
 {
-    __shared__ float xs[PT][DCH + 1];
-    __shared__ float cs[kSoftMaxK][DCH + 1];
+    extern __shared__ float sm[];
+    float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
+    float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
+    float *ps = sm + (PT + kSoftMaxK) * (DCH + 1);             // [k][PT + 1]
     const long long p0 = (long long)blockIdx.x * PT;
-    float pr[KQ];
+    float pr[PPT][KI];
     tile_softmax(X, n, p0, D, C, k, tau, xs, cs, pr);
-    const int p = threadIdx.x >> 2, q = threadIdx.x & 3;
-    const long long g = p0 + p;
-    if (g >= n) return;
-    const long long item = g / npi, pix = g % npi;
+    const int pg = threadIdx.x >> 4, cl = threadIdx.x & 15;
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-        const int j = q + 4 * i;
-        if (j < k) P[(item * k + j) * npi + pix] = pr[i];
+    for (int r = 0; r < PPT; ++r)
+#pragma unroll
+        for (int i = 0; i < KI; ++i)
+            if (cl + 16 * i < k) ps[(cl + 16 * i) * (PT + 1) + pg * PPT + r] = pr[r][i];
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * PT; e += blockDim.x) {
+        const int j = e / PT, pp = e % PT;
+        const long long g = p0 + pp;
+        if (g < n) P[((g / npi) * k + j) * npi + g % npi] = ps[j * (PT + 1) + pp];
     }
 }
 
-// Row sums of width w: RW[row][x] = sum_{dx < w} P[row][x + dx], x <= W - w (one block per
-// row of a plane).
+constexpr int SEG = 8;             // consecutive outputs per thread in the box passes
+
+// Row sums of width w: RW[row][x] = sum_{dx < w} P[row][x + dx], x <= W - w.  Thread: SEG
+// consecutive x, the first window summed directly, the next ones by sliding it.
 __global__ void row_box_kernel(const float *__restrict__ P, int W, int w, float *__restrict__ RW)
 {
-    const long long row = blockIdx.x;
+    const long long row = blockIdx.x;                          // rows in grid.x (> 65535 of them)
+    const int x0 = (blockIdx.y * blockDim.x + threadIdx.x) * SEG;
+    if (x0 > W - w) return;
     const float *src = P + row * W;
-    for (int x = threadIdx.x; x <= W - w; x += blockDim.x) {
-        float s = 0.f;
-        for (int dx = 0; dx < w; ++dx) s += src[x + dx];
+    float s = 0.f;
+    for (int dx = 0; dx < w; ++dx) s += src[x0 + dx];
+    const int xe = min(x0 + SEG, W - w + 1);
+    RW[row * W + x0] = s;
+    for (int x = x0 + 1; x < xe; ++x) {
+        s += src[x + w - 1] - src[x - 1];
         RW[row * W + x] = s;
     }
 }
 
-// Column sums of height h: BX[plane][y][x] = sum_{dy < h} RW[plane][y + dy][x], y <= H - h.
+// Column sums of height h: BX[plane][y][x] = sum_{dy < h} RW[plane][y + dy][x], y <= H - h,
+// x <= wlim; thread: SEG consecutive y.
 __global__ void col_box_kernel(const float *__restrict__ RW, int H, int W, int h, int wlim,
                                float *__restrict__ BX)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y0 = blockIdx.y * SEG;
     const long long plane = blockIdx.z;
-    if (x > wlim || y > H - h) return;
-    const float *src = RW + (plane * H + y) * W + x;
+    if (x > wlim || y0 > H - h) return;
+    const float *src = RW + plane * H * W + x;
     float s = 0.f;
-    for (int dy = 0; dy < h; ++dy) s += src[(size_t)dy * W];
-    BX[(plane * H + y) * W + x] = s;
+    for (int dy = 0; dy < h; ++dy) s += src[(size_t)(y0 + dy) * W];
+    const int ye = min(y0 + SEG, H - h + 1);
+    BX[(plane * H + y0) * W + x] = s;
+    for (int y = y0 + 1; y < ye; ++y) {
+        s += src[(size_t)(y + h - 1) * W] - src[(size_t)(y - 1) * W];
+        BX[(plane * H + y) * W + x] = s;
+    }
 }
 
 // Template soft counts: T[f * k + j] = sum over cell f of Pt[j][v] (one block per (f, j)).
@@ -183,14 +212,15 @@ __global__ void __launch_bounds__(128) soft_heat_kernel(const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------------- backward
-// dL/dw_f = -(1/A_f) sum_{b,y,x} dheat L1_f   (one block per filter, fixed-order tree)
+// dL/dw_f = -(1/A_f) sum_{b,y,x} dheat L1_f   (64 blocks per filter, float atomics)
 __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__restrict__ L1, int B, int HO,
                                int WO, SoftGrid sg, float *__restrict__ dwf)
 {
     const int f = blockIdx.x, F = sg.F;
     const long long per = (long long)HO * WO;
     float s = 0.f;
-    for (long long e = threadIdx.x; e < (long long)B * per; e += blockDim.x) {
+    for (long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x; e < (long long)B * per;
+         e += (long long)gridDim.y * blockDim.x) {
         const long long b = e / per, r = e % per;
         s = fmaf(dheat[e], L1[((size_t)b * F + f) * per + r], s);
     }
@@ -202,7 +232,7 @@ __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__r
         float t = 0.f;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
         const SoftCell c = sg.cell[f];
-        dwf[f] = -t / (float)((c.y1 - c.y0) * (c.x1 - c.x0));
+        atomicAdd(&dwf[f], -t / (float)((c.y1 - c.y0) * (c.x1 - c.x0)));
     }
 }
 
@@ -244,6 +274,8 @@ __global__ void __launch_bounds__(128) soft_gather_kernel(const float *__restric
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
     for (int f = 0; f < kSoftMaxG * kSoftMaxG; ++f) {
+        if (f >= sg.F) break;
+        if (sg.cell[f].s != s) continue;                      // uniform over the block
         float v = dt[f];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[f][wp] = v;
@@ -256,31 +288,47 @@ __global__ void __launch_bounds__(128) soft_gather_kernel(const float *__restric
     }
 }
 
-// R2[row][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[row][x'] (rows y' <= H - h)
+// R2[row][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[row][x'] (rows y' <= H - h);
+// thread: SEG consecutive ux, sliding window.
 __global__ void adj_row_kernel(const float *__restrict__ Z, int H, int W, int h, int w, float *__restrict__ R2)
 {
     const long long row = blockIdx.x;                         // plane * H + y'
     if ((int)(row % H) > H - h) return;
+    const int u0 = (blockIdx.y * blockDim.x + threadIdx.x) * SEG;
+    if (u0 >= W) return;
     const float *src = Z + row * W;
-    for (int ux = threadIdx.x; ux < W; ux += blockDim.x) {
-        const int lo = max(0, ux - w + 1), hi = min(ux, W - w);
-        float s = 0.f;
-        for (int xp = lo; xp <= hi; ++xp) s += src[xp];
+    const int xm = W - w;
+    float s = 0.f;
+    for (int xp = max(0, u0 - w + 1); xp <= min(u0, xm); ++xp) s += src[xp];
+    R2[row * W + u0] = s;
+    const int ue = min(u0 + SEG, W);
+    for (int ux = u0 + 1; ux < ue; ++ux) {
+        if (ux <= xm) s += src[ux];
+        if (ux - w >= 0 && ux - w <= xm) s -= src[ux - w];
         R2[row * W + ux] = s;
     }
 }
 
-// G[plane][uy][ux] (+)= sum over y' in [uy - h + 1, uy] within [0, H - h] of R2[plane][y'][ux]
+// G[plane][uy][ux] (+)= sum over y' in [uy - h + 1, uy] within [0, H - h] of R2[plane][y'][ux];
+// thread: SEG consecutive uy, sliding window.
 __global__ void adj_col_kernel(const float *__restrict__ R2, int H, int W, int h, bool first, float *__restrict__ Gp)
 {
-    const int ux = blockIdx.x * blockDim.x + threadIdx.x, uy = blockIdx.y;
+    const int ux = blockIdx.x * blockDim.x + threadIdx.x, v0 = blockIdx.y * SEG;
     const long long plane = blockIdx.z;
-    if (ux >= W) return;
-    const int lo = max(0, uy - h + 1), hi = min(uy, H - h);
+    if (ux >= W || v0 >= H) return;
+    const float *src = R2 + plane * H * W + ux;
+    const int ym = H - h;
     float s = 0.f;
-    for (int yp = lo; yp <= hi; ++yp) s += R2[(plane * H + yp) * W + ux];
-    const size_t o = (plane * H + uy) * W + ux;
-    Gp[o] = first ? s : Gp[o] + s;
+    for (int yp = max(0, v0 - h + 1); yp <= min(v0, ym); ++yp) s += src[(size_t)yp * W];
+    const int ve = min(v0 + SEG, H);
+    for (int uy = v0; uy < ve; ++uy) {
+        if (uy > v0) {
+            if (uy <= ym) s += src[(size_t)uy * W];
+            if (uy - h >= 0 && uy - h <= ym) s -= src[(size_t)(uy - h) * W];
+        }
+        const size_t o = (plane * H + uy) * W + ux;
+        Gp[o] = first ? s : Gp[o] + s;
+    }
 }
 
 // Template pixel gradients: Gt[j][v] = sum over cells f containing v of dT_fj.
@@ -309,94 +357,141 @@ __global__ void __launch_bounds__(256) soft_back_kernel(const float *__restrict_
     extern __shared__ float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
     float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
-    float *as = sm + (PT + kSoftMaxK) * (DCH + 1);             // [PT][k + 1]
+    float *as = sm + (PT + kSoftMaxK) * (DCH + 1);             // [PT][k + 1]: g, then a
+    float *asum_s = as + PT * (kSoftMaxK + 1);                  // [PT]
     const long long p0 = (long long)blockIdx.x * PT;
-    float pr[KQ];
+    float pr[PPT][KI];
     tile_softmax(X, n, p0, D, C, k, tau, xs, cs, pr);
-    const int p = threadIdx.x >> 2, q = threadIdx.x & 3;
-    const long long g = p0 + p;
-    const bool in = g < n;
-    const long long item = in ? g / npi : 0, pix = in ? g % npi : 0;
-    float gv[KQ];
-    float s = 0.f;
-#pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-        const int j = q + 4 * i;
-        gv[i] = (in && j < k) ? Gp[(item * k + j) * npi + pix] : 0.f;
-        s = fmaf(pr[i], gv[i], s);
+    const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
+    // g of the tile's pixels, coalesced along pixels of each plane
+    for (int e = t; e < k * PT; e += blockDim.x) {
+        const int j = e / PT, pp = e % PT;
+        const long long g = p0 + pp;
+        as[pp * (k + 1) + j] = g < n ? Gp[((g / npi) * k + j) * npi + g % npi] : 0.f;
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    __syncthreads();
     const float it = 1.0f / tau;
-    float asum = 0.f;
 #pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-        const int j = q + 4 * i;
-        if (j < k) {
-            const float a = in ? -it * pr[i] * (gv[i] - s) : 0.f;
-            as[p * (k + 1) + j] = a;
-            asum += a;
-            if (in) A[g * k + j] = a;
+    for (int r = 0; r < PPT; ++r) {
+        const int pp = pg * PPT + r;
+        float gv[KI], s = 0.f;
+#pragma unroll
+        for (int i = 0; i < KI; ++i) {
+            gv[i] = cl + 16 * i < k ? as[pp * (k + 1) + cl + 16 * i] : 0.f;
+            s = fmaf(pr[r][i], gv[i], s);
         }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        float asum = 0.f;
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < KI; ++i)
+            if (cl + 16 * i < k) {
+                const float a = -it * pr[r][i] * (gv[i] - s);
+                as[pp * (k + 1) + cl + 16 * i] = a;
+                asum += a;
+            }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) asum += __shfl_xor_sync(0xffffffffu, asum, o);
+        if (cl == 0) asum_s[pp] = asum;
     }
-    asum += __shfl_xor_sync(0xffffffffu, asum, 1);
-    asum += __shfl_xor_sync(0xffffffffu, asum, 2);
+    __syncthreads();
+    for (int e = t; e < PT * k; e += blockDim.x) {
+        const int pp = e / k, j = e % k;
+        const long long g = p0 + pp;
+        if (g < n) A[g * k + j] = as[pp * (k + 1) + j];
+    }
     if (!dX) return;                                          // uniform over the block
+    // dX tile per chunk: thread owns pixels 2 u, 2 u + 1 and dims 4 v .. 4 v + 3 of the chunk
+    const int u = t >> 3, v = t & 7;
     for (int d0 = 0; d0 < D; d0 += DCH) {
         __syncthreads();
-        for (int e = threadIdx.x; e < PT * DCH; e += blockDim.x) {
+        for (int e = t; e < PT * DCH; e += blockDim.x) {
             const int pp = e / DCH, dd = e % DCH;
             const long long gg = p0 + pp;
             xs[pp][dd] = (gg < n && d0 + dd < D) ? X[gg * D + d0 + dd] : 0.f;
         }
-        for (int e = threadIdx.x; e < k * DCH; e += blockDim.x) {
+        for (int e = t; e < k * DCH; e += blockDim.x) {
             const int j = e / DCH, dd = e % DCH;
             cs[j][dd] = d0 + dd < D ? C[(size_t)j * D + d0 + dd] : 0.f;
         }
         __syncthreads();
-        for (int dd = q; dd < DCH; dd += 4) {
-            float ac = 0.f;
-            for (int j = 0; j < k; ++j) ac = fmaf(as[p * (k + 1) + j], cs[j][dd], ac);
-            if (in && d0 + dd < D) dX[g * D + d0 + dd] = 2.0f * (asum * xs[p][dd] - ac);
+        float ac[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        for (int j = 0; j < k; ++j) {
+            const float a0 = as[(2 * u) * (k + 1) + j], a1 = as[(2 * u + 1) * (k + 1) + j];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float cv = cs[j][4 * v + c];
+                ac[0][c] = fmaf(a0, cv, ac[0][c]);
+                ac[1][c] = fmaf(a1, cv, ac[1][c]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int pp = 2 * u + r;
+            const long long g = p0 + pp;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int d = d0 + 4 * v + c;
+                if (g < n && d < D) dX[g * D + d] = 2.0f * (asum_s[pp] * xs[pp][4 * v + c] - ac[r][c]);
+            }
         }
     }
 }
 
-// Partial centroid gradients over a pixel slice: part[slice][j D + d] = sum_u a_j(u) x_u[d],
-// part[slice][k D + j] = sum_u a_j(u).
+// Partial centroid gradients over a pixel slice, one output tile of 32 centroids x 64 dims per
+// block (thread: 2 centroids x 4 dims in registers): part[slice][j D + d] = sum_u a_j(u) x_u[d];
+// the j-tile's first d-tile also writes part[slice][k D + j] = sum_u a_j(u).
 __global__ void __launch_bounds__(256) dc_partial_kernel(const float *__restrict__ A, const float *__restrict__ X,
                                                          long long n, int D, int k, int nslice,
                                                          float *__restrict__ part)
 {
-    extern __shared__ float sm[];
-    float *acc = sm;                                          // [k D + k]
-    float *at = acc + k * D + k;                              // [32][k]
-    float *xt = at + 32 * k;                                  // [32][D]
-    const int kD = k * D;
-    for (int o = threadIdx.x; o < kD + k; o += blockDim.x) acc[o] = 0.f;
+    __shared__ float at[32][33];
+    __shared__ float xt[32][65];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;        // centroids 2 ty, 2 ty + 1; dims 4 tx..
+    const int j0 = blockIdx.x * 32, d0 = blockIdx.y * 64;
+    const int slice = blockIdx.z;
     const long long per = (n + nslice - 1) / nslice;
-    const long long u0 = (long long)blockIdx.x * per, u1 = min(n, u0 + per);
+    const long long u0 = (long long)slice * per, u1 = min(n, u0 + per);
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float as0 = 0.f, as1 = 0.f;
     for (long long t0 = u0; t0 < u1; t0 += 32) {
         const int m = (int)min(32LL, u1 - t0);
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * k; e += blockDim.x) at[e] = e / k < m ? A[(t0 + e / k) * k + e % k] : 0.f;
-        for (int e = threadIdx.x; e < 32 * D; e += blockDim.x) xt[e] = e / D < m ? X[(t0 + e / D) * D + e % D] : 0.f;
-        __syncthreads();
-        for (int o = threadIdx.x; o < kD; o += blockDim.x) {
-            const int j = o / D, d = o % D;
-            float s = 0.f;
-#pragma unroll 8
-            for (int u = 0; u < 32; ++u) s = fmaf(at[u * k + j], xt[u * D + d], s);
-            acc[o] += s;
+        for (int e = t; e < 32 * 32; e += blockDim.x) {
+            const int uu = e >> 5, jj = e & 31;
+            at[uu][jj] = (uu < m && j0 + jj < k) ? A[(t0 + uu) * k + j0 + jj] : 0.f;
         }
-        for (int j = threadIdx.x; j < k; j += blockDim.x) {
-            float s = 0.f;
-            for (int u = 0; u < 32; ++u) s += at[u * k + j];
-            acc[kD + j] += s;
+        for (int e = t; e < 32 * 64; e += blockDim.x) {
+            const int uu = e >> 6, dd = e & 63;
+            xt[uu][dd] = (uu < m && d0 + dd < D) ? X[(t0 + uu) * D + d0 + dd] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int uu = 0; uu < 32; ++uu) {
+            const float a0 = at[uu][2 * ty], a1 = at[uu][2 * ty + 1];
+            as0 += a0;
+            as1 += a1;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float xv = xt[uu][4 * tx + c];
+                acc[0][c] = fmaf(a0, xv, acc[0][c]);
+                acc[1][c] = fmaf(a1, xv, acc[1][c]);
+            }
         }
     }
-    __syncthreads();
-    for (int o = threadIdx.x; o < kD + k; o += blockDim.x) part[(size_t)blockIdx.x * (kD + k) + o] = acc[o];
+    float *o = part + (size_t)slice * ((size_t)k * D + k);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int j = j0 + 2 * ty + r;
+        if (j >= k) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int d = d0 + 4 * tx + c;
+            if (d < D) o[(size_t)j * D + d] = acc[r][c];
+        }
+        if (blockIdx.y == 0 && tx == 0) o[(size_t)k * D + j] = r ? as1 : as0;
+    }
 }
 
 // dC[j][d] = -2 sum_slices part[.][j D + d] + 2 (sum_slices part[.][k D + j]) C[j][d], over the
@@ -485,15 +580,20 @@ cudaError_t soft_forward(const float *Qf, int B, int H, int W, const float *Tf, 
                          SoftWs &w, cudaStream_t s)
 {
     const long long nq = (long long)B * H * W, nt = (long long)th * tw;
-    soft_p_kernel<<<(unsigned)((nq + PT - 1) / PT), 256, 0, s>>>(Qf, nq, (long long)H * W, D, C, k, tau, w.P);
-    soft_p_kernel<<<(unsigned)((nt + PT - 1) / PT), 256, 0, s>>>(Tf, nt, nt, D, C, k, tau, w.Pt);
+    const size_t psm = sizeof(float) * ((PT + kSoftMaxK) * (DCH + 1) + kSoftMaxK * (PT + 1));
+    cudaError_t e = cudaFuncSetAttribute(soft_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    if (e != cudaSuccess) return e;
+    soft_p_kernel<<<(unsigned)((nq + PT - 1) / PT), 256, psm, s>>>(Qf, nq, (long long)H * W, D, C, k, tau, w.P);
+    soft_p_kernel<<<(unsigned)((nt + PT - 1) / PT), 256, psm, s>>>(Tf, nt, nt, D, C, k, tau, w.Pt);
     const long long planes = (long long)B * k;
-    for (int iw = 0; iw < sg.nw; ++iw)
-        row_box_kernel<<<(unsigned)(planes * H), 128, 0, s>>>(w.P, W, sg.wid[iw], w.RW + (size_t)iw * planes * H * W);
+    for (int iw = 0; iw < sg.nw; ++iw) {
+        dim3 g((unsigned)(planes * H), (W + 128 * SEG - 1) / (128 * SEG));
+        row_box_kernel<<<g, 128, 0, s>>>(w.P, W, sg.wid[iw], w.RW + (size_t)iw * planes * H * W);
+    }
     for (int is = 0; is < sg.ns; ++is) {
         const int iw = sg.size_w[is];
         for (int b = 0; b < B; ++b) {
-            dim3 g((W + 127) / 128, H, k);
+            dim3 g((W + 127) / 128, (H + SEG - 1) / SEG, k);
             col_box_kernel<<<g, 128, 0, s>>>(w.RW + ((size_t)iw * planes + (size_t)b * k) * H * W, H, W,
                                              sg.hgt[sg.size_h[is]], W - sg.wid[iw],
                                              w.BX + ((size_t)b * sg.ns + is) * k * H * W);
@@ -512,19 +612,22 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
 {
     const int HO = H - th + 1, WO = W - tw + 1;
     const long long nq = (long long)B * H * W, nt = (long long)th * tw;
-    soft_dw_kernel<<<sg.F, 256, 0, s>>>(dheat, w.L1, B, HO, WO, sg, dwf);
-    cudaError_t e = cudaMemsetAsync(w.dT, 0, sizeof(float) * sg.F * k, s);
+    cudaError_t e = cudaMemsetAsync(dwf, 0, sizeof(float) * sg.F, s);
+    if (e != cudaSuccess) return e;
+    soft_dw_kernel<<<dim3(sg.F, 64), 256, 0, s>>>(dheat, w.L1, B, HO, WO, sg, dwf);
+    e = cudaMemsetAsync(w.dT, 0, sizeof(float) * sg.F * k, s);
     if (e != cudaSuccess) return e;
     const long long planes = (long long)B * k;
     for (int is = 0; is < sg.ns; ++is) {
         const int h = sg.hgt[sg.size_h[is]], wd = sg.wid[sg.size_w[is]];
         dim3 g1((W + 127) / 128, H, (unsigned)planes);
         soft_gather_kernel<<<g1, 128, 0, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.Z, w.dT);
-        adj_row_kernel<<<(unsigned)(planes * H), 128, 0, s>>>(w.Z, H, W, h, wd, w.R2);
-        dim3 g3((W + 127) / 128, H, (unsigned)planes);
+        dim3 g2((unsigned)(planes * H), (W + 128 * SEG - 1) / (128 * SEG));
+        adj_row_kernel<<<g2, 128, 0, s>>>(w.Z, H, W, h, wd, w.R2);
+        dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
         adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
     }
-    const size_t bsm = sizeof(float) * ((PT + kSoftMaxK) * (DCH + 1) + PT * (k + 1));
+    const size_t bsm = sizeof(float) * ((PT + kSoftMaxK) * (DCH + 1) + PT * (kSoftMaxK + 1) + PT);
     e = cudaFuncSetAttribute(soft_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
     if (e != cudaSuccess) return e;
     soft_back_kernel<<<(unsigned)((nq + PT - 1) / PT), 256, bsm, s>>>(Qf, nq, (long long)H * W, D, C, k, tau, w.G,
@@ -532,12 +635,9 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
     // template side: pixel gradients from dT, then its softmax backward (no feature gradient)
     tmpl_grad_kernel<<<(unsigned)((k * nt + 255) / 256), 256, 0, s>>>(w.dT, th, tw, k, sg, w.G);
     soft_back_kernel<<<(unsigned)((nt + PT - 1) / PT), 256, bsm, s>>>(Tf, nt, nt, D, C, k, tau, w.G, w.At, nullptr);
-    const size_t psm = sizeof(float) * ((size_t)k * D + k + 32 * (size_t)k + 32 * (size_t)D);
-    e = cudaFuncSetAttribute(dc_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
-    if (e != cudaSuccess) return e;
-    dc_partial_kernel<<<kSoftSlices, 256, psm, s>>>(w.A, Qf, nq, D, k, kSoftSlices, w.part);
-    dc_partial_kernel<<<kSoftSlices, 256, psm, s>>>(w.At, Tf, nt, D, k, kSoftSlices,
-                                                    w.part + (size_t)kSoftSlices * (k * D + k));
+    dim3 gp((k + 31) / 32, (D + 63) / 64, kSoftSlices);
+    dc_partial_kernel<<<gp, 256, 0, s>>>(w.A, Qf, nq, D, k, kSoftSlices, w.part);
+    dc_partial_kernel<<<gp, 256, 0, s>>>(w.At, Tf, nt, D, k, kSoftSlices, w.part + (size_t)kSoftSlices * (k * D + k));
     dc_reduce_kernel<<<(k * D + 255) / 256, 256, 0, s>>>(w.part, 2 * kSoftSlices, D, k, C, dC);
     return cudaGetLastError();
 }
