@@ -196,8 +196,8 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
  *   ws    device workspace of vqnnf_soft_workspace_bytes() bytes, 256-byte aligned; it keeps
  *         the template soft counts, the query cell sums and the per-filter L1 maps for the
  *         backward call with the same arguments (the softmax itself is recomputed there).
- * Limits: k <= 128, D <= 512, k * D <= 32768, B * k <= 65535, H <= 65535, B * k * H < 2^31,
- * B * k * H * W < 2^40 (else VQNNF_EUNSUPPORTED). */
+ * Limits: k <= 128, D <= 512, k * D <= 32768, B * k <= 65535, H <= 65535, W <= 12288,
+ * B * k * H < 2^31, B * k * H * W < 2^40 (else VQNNF_EUNSUPPORTED). */
 size_t vqnnf_soft_workspace_bytes(int B, int H, int W, int D, int k, int th, int tw, int G);
 vqnnf_status vqnnf_soft_forward(const float *Qf, int B, int H, int W, const float *Tf, int th, int tw,
                                 int D, const float *C, int k, float tau, int G, const float *wf,

@@ -506,7 +506,7 @@ static vqnnf_status soft_check(const void *Qf, int B, int H, int W, const void *
         k < 1 || !(tau > 0.f) || !std::isfinite(tau))
         return VQNNF_EINVAL;
     if (k > kSoftMaxK || D > 512 || (long long)k * D > 32768 || (long long)B * k > 65535 ||
-        H > 65535 || (long long)B * k * H >= (1ll << 31) || (long long)B * k * H * W >= (1ll << 40))
+        H > 65535 || W > 12288 || (long long)B * k * H >= (1ll << 31) || (long long)B * k * H * W >= (1ll << 40))
         return VQNNF_EUNSUPPORTED;
     if (!soft_grid(th, tw, G, sg)) return G < 1 || G > kSoftMaxG ? VQNNF_EUNSUPPORTED : VQNNF_EINVAL;
     return VQNNF_OK;

@@ -29,12 +29,26 @@ namespace {
 
 constexpr int PT = 64;             // pixels per tile of the soft-assignment kernels
 constexpr int DCH = 32;            // feature dimensions staged per chunk
-constexpr int KI = kSoftMaxK / 16; // centroids per thread: thread (pg, cl) holds j = cl + 16 i
 constexpr int PPT = 4;             // pixels per thread: pg * 4 .. pg * 4 + 3
+// KI (template parameter): centroids per thread, thread (pg, cl) holds j = cl + 16 i, i < KI;
+// 16 KI >= k (2, 4 or 8)
+
+// Planar offset of pixel p0 + pp of cluster plane j, P[(item * k + j) * npi + pixel], from the
+// tile's first item and offset (one 64-bit division per tile, not per element).
+__device__ __forceinline__ long long planar_index(long long it0, long long of0, int pp, int j, int k, long long npi)
+{
+    long long it = it0, of = of0 + pp;
+    if (of >= npi) {                                          // the tile straddles items
+        it += of / npi;
+        of %= npi;
+    }
+    return (it * k + j) * npi + of;
+}
 
 // Distances of a 64-pixel tile to all k centroids and the softmax over each pixel's k logits.
 // Thread t = 16 pg + cl owns pixels 4 pg .. 4 pg + 3 and centroids cl, cl + 16, ...; the 16
 // threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.
+template <int KI>
 __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long long n, long long p0, int D,
                                              const float *__restrict__ C, int k, float tau, float (*xs)[DCH + 1],
                                              float (*cs)[DCH + 1], float (*pr)[KI])
@@ -99,6 +113,7 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
 
 // p planar: P[(item * k + j) * npi + pixel], written through a shared-memory transpose so that
 // consecutive threads store consecutive pixels of one plane.
+template <int KI>
 __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
                                                      int D, const float *__restrict__ C, int k, float tau,
                                                      float *__restrict__ P)
@@ -106,10 +121,10 @@ __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X
     extern __shared__ float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
     float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
-    float *ps = sm + (PT + kSoftMaxK) * (DCH + 1);             // [k][PT + 1]
+    float *ps = sm + (PT + 16 * KI) * (DCH + 1);             // [k][PT + 1]
     const long long p0 = (long long)blockIdx.x * PT;
     float pr[PPT][KI];
-    tile_softmax(X, n, p0, D, C, k, tau, xs, cs, pr);
+    tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
     const int pg = threadIdx.x >> 4, cl = threadIdx.x & 15;
 #pragma unroll
     for (int r = 0; r < PPT; ++r)
@@ -117,10 +132,10 @@ __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X
         for (int i = 0; i < KI; ++i)
             if (cl + 16 * i < k) ps[(cl + 16 * i) * (PT + 1) + pg * PPT + r] = pr[r][i];
     __syncthreads();
+    const long long it0 = p0 / npi, of0 = p0 - it0 * npi;
     for (int e = threadIdx.x; e < k * PT; e += blockDim.x) {
         const int j = e / PT, pp = e % PT;
-        const long long g = p0 + pp;
-        if (g < n) P[((g / npi) * k + j) * npi + g % npi] = ps[j * (PT + 1) + pp];
+        if (p0 + pp < n) P[planar_index(it0, of0, pp, j, k, npi)] = ps[j * (PT + 1) + pp];
     }
 }
 
@@ -236,76 +251,97 @@ __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__r
     }
 }
 
-// Size class s: Z[(b k + j)][y'][x'] = sum over cells f of class s with window (y' - y0_f,
-// x' - x0_f) valid of m_fj = -(w_f/A_f) dheat sign(Q_fj - T_fj); Q_fj(window) is BX at (y', x').
-// Also dT_fj += -m_fj (block sums, then one atomic per block and filter).
-__global__ void __launch_bounds__(128) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
+// Size class s (cells of height h, width w), one block per (plane b k + j, GROWS rows y' <= H - h):
+//   Z[x'] = sum over cells f of class s with window (y' - y0_f, x' - x0_f) valid of
+//           m_fj = -(w_f / A_f) dheat sign(Q_fj - T_fj), Q_fj(window) = BX[y'][x'], x' <= W - w,
+// kept in shared memory, then the row pass of the adjoint box sum
+//   R2[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[x']   (direct sums).
+// Also dT_fj += -m_fj (block sums, then one atomic per block and filter).  The class's cells
+// (at most G * G) are staged in shared memory first, so the per-pixel loop has uniform guards
+// and its dheat loads do not wait on one another.
+constexpr int GROWS = 4;           // rows per block of the gradient gather
+template <int MC>                  // MC >= number of cells in class s
+__global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
                                                           const float *__restrict__ T, const float *__restrict__ wf,
                                                           int H, int W, int k, int HO, int WO, SoftGrid sg, int s,
-                                                          float *__restrict__ Z, float *__restrict__ dT)
+                                                          float *__restrict__ R2, float *__restrict__ dT)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    const int bj = blockIdx.z, b = bj / k, j = bj % k;
+    extern __shared__ float zrow[];                           // [GROWS][W]
+    __shared__ int c_y0[MC], c_x0[MC], c_f[MC];
+    __shared__ float c_t[MC], c_coef[MC];
+    __shared__ int n_cell;
+    __shared__ float red[MC][8];
     const int h = sg.hgt[sg.size_h[s]], w = sg.wid[sg.size_w[s]];
-    float dt[kSoftMaxG * kSoftMaxG];
-#pragma unroll
-    for (int f = 0; f < kSoftMaxG * kSoftMaxG; ++f) dt[f] = 0.f;
-    const bool in = x <= W - w && y <= H - h;
-    float z = 0.f;
-    if (in) {
-        const float q = BX[((size_t)(b * sg.ns + s) * k + j) * H * W + (size_t)y * W + x];
-#pragma unroll
-        for (int f = 0; f < kSoftMaxG * kSoftMaxG; ++f) {
-            if (f >= sg.F) break;
+    const int nrow = H - h + 1, nrb = (nrow + GROWS - 1) / GROWS;
+    const long long bj = blockIdx.x / nrb;
+    const int yb = (int)(blockIdx.x % nrb) * GROWS, b = (int)(bj / k), j = (int)(bj % k);
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int f = 0; f < sg.F && n < MC; ++f) {
             const SoftCell c = sg.cell[f];
             if (c.s != s) continue;
-            const int wy = y - c.y0, wx = x - c.x0;
-            if (wy < 0 || wy >= HO || wx < 0 || wx >= WO) continue;
-            const float t = T[f * k + j];
-            const float sg_ = q > t ? 1.f : (q < t ? -1.f : 0.f);
-            const float m = -(wf[f] / (float)((c.y1 - c.y0) * (c.x1 - c.x0))) *
-                            dheat[((size_t)b * HO + wy) * WO + wx] * sg_;
-            z += m;
-            dt[f] -= m;
+            c_y0[n] = c.y0;
+            c_x0[n] = c.x0;
+            c_f[n] = f;
+            c_t[n] = T[f * k + j];
+            c_coef[n] = -(wf[f] / (float)((c.y1 - c.y0) * (c.x1 - c.x0)));
+            ++n;
         }
-        Z[(size_t)bj * H * W + (size_t)y * W + x] = z;
-    }
-    __shared__ float red[kSoftMaxG * kSoftMaxG][4];
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-    for (int f = 0; f < kSoftMaxG * kSoftMaxG; ++f) {
-        if (f >= sg.F) break;
-        if (sg.cell[f].s != s) continue;                      // uniform over the block
-        float v = dt[f];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[f][wp] = v;
+        n_cell = n;
     }
     __syncthreads();
-    if (threadIdx.x < sg.F && sg.cell[threadIdx.x].s == s) {
-        const int f = threadIdx.x;
-        const float v = red[f][0] + red[f][1] + red[f][2] + red[f][3];
-        if (v != 0.f) atomicAdd(&dT[f * k + j], v);
-    }
-}
-
-// R2[row][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[row][x'] (rows y' <= H - h);
-// thread: SEG consecutive ux, sliding window.
-__global__ void adj_row_kernel(const float *__restrict__ Z, int H, int W, int h, int w, float *__restrict__ R2)
-{
-    const long long row = blockIdx.x;                         // plane * H + y'
-    if ((int)(row % H) > H - h) return;
-    const int u0 = (blockIdx.y * blockDim.x + threadIdx.x) * SEG;
-    if (u0 >= W) return;
-    const float *src = Z + row * W;
+    const int nc = n_cell;
+    float dt[MC];
+#pragma unroll
+    for (int c = 0; c < MC; ++c) dt[c] = 0.f;
     const int xm = W - w;
-    float s = 0.f;
-    for (int xp = max(0, u0 - w + 1); xp <= min(u0, xm); ++xp) s += src[xp];
-    R2[row * W + u0] = s;
-    const int ue = min(u0 + SEG, W);
-    for (int ux = u0 + 1; ux < ue; ++ux) {
-        if (ux <= xm) s += src[ux];
-        if (ux - w >= 0 && ux - w <= xm) s -= src[ux - w];
-        R2[row * W + ux] = s;
+    const int nr = min(GROWS, nrow - yb);
+    for (int e = threadIdx.x; e < nr * (xm + 1); e += blockDim.x) {
+        const int r = e / (xm + 1), x = e % (xm + 1), y = yb + r;
+        const float q = BX[((size_t)(b * sg.ns + s) * k + j) * H * W + (size_t)y * W + x];
+        float z = 0.f;
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+            if (c >= nc) break;                               // uniform
+            const int wy = y - c_y0[c], wx = x - c_x0[c];
+            const bool ok = wy >= 0 && wy < HO && wx >= 0 && wx < WO;
+            const float d = ok ? dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
+            const float t = c_t[c];
+            const float sgn = q > t ? 1.f : (q < t ? -1.f : 0.f);
+            const float m = c_coef[c] * d * sgn;
+            z += m;
+            dt[c] -= m;
+        }
+        zrow[r * W + x] = z;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * W; e += blockDim.x) {
+        const int r = e / W, ux = e % W;
+        const float *zr = zrow + r * W;
+        const int lo = max(0, ux - w + 1), hi = min(ux, xm);
+        float a0 = 0.f, a1 = 0.f;
+        int xp = lo;
+        for (; xp + 1 <= hi; xp += 2) {
+            a0 += zr[xp];
+            a1 += zr[xp + 1];
+        }
+        if (xp <= hi) a0 += zr[xp];
+        R2[((size_t)bj * H + yb + r) * W + ux] = a0 + a1;
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < MC; ++c) {
+        if (c >= nc) break;                                   // uniform
+        float v = dt[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c][wp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        const int c = threadIdx.x;
+        float v = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[c][q];
+        if (v != 0.f) atomicAdd(&dT[c_f[c] * k + j], v);
     }
 }
 
@@ -349,25 +385,26 @@ __global__ void tmpl_grad_kernel(const float *__restrict__ dT, int th, int tw, i
 
 // Softmax backward with the softmax recomputed: a_j = -(1/tau) p_j (g_j - sum_i p_i g_i),
 // A pixel-major; dX = 2 (sum_j a_j) x - 2 sum_j a_j c_j (skipped when dX is null).
+template <int KI>
 __global__ void __launch_bounds__(256) soft_back_kernel(const float *__restrict__ X, long long n, long long npi,
                                                         int D, const float *__restrict__ C, int k, float tau,
                                                         const float *__restrict__ Gp, float *__restrict__ A,
                                                         float *__restrict__ dX)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
     float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
-    float *as = sm + (PT + kSoftMaxK) * (DCH + 1);             // [PT][k + 1]: g, then a
-    float *asum_s = as + PT * (kSoftMaxK + 1);                  // [PT]
+    float *as = sm + (PT + 16 * KI) * (DCH + 1);             // [PT][k + 1]: g, then a
+    float *asum_s = as + PT * (16 * KI + 1);                  // [PT]
     const long long p0 = (long long)blockIdx.x * PT;
     float pr[PPT][KI];
-    tile_softmax(X, n, p0, D, C, k, tau, xs, cs, pr);
+    tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
     const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
     // g of the tile's pixels, coalesced along pixels of each plane
+    const long long it0 = p0 / npi, of0 = p0 - it0 * npi;
     for (int e = t; e < k * PT; e += blockDim.x) {
         const int j = e / PT, pp = e % PT;
-        const long long g = p0 + pp;
-        as[pp * (k + 1) + j] = g < n ? Gp[((g / npi) * k + j) * npi + g % npi] : 0.f;
+        as[pp * (k + 1) + j] = p0 + pp < n ? Gp[planar_index(it0, of0, pp, j, k, npi)] : 0.f;
     }
     __syncthreads();
     const float it = 1.0f / tau;
@@ -402,8 +439,16 @@ __global__ void __launch_bounds__(256) soft_back_kernel(const float *__restrict_
         if (g < n) A[g * k + j] = as[pp * (k + 1) + j];
     }
     if (!dX) return;                                          // uniform over the block
-    // dX tile per chunk: thread owns pixels 2 u, 2 u + 1 and dims 4 v .. 4 v + 3 of the chunk
-    const int u = t >> 3, v = t & 7;
+    // a transposed, at[j][PT + 4], for float4 reads along pixels (rows 16-byte aligned)
+    float *at = asum_s + PT;
+    for (int e = t; e < k * PT; e += blockDim.x) {
+        const int j = e / PT, pp = e % PT;
+        at[j * (PT + 4) + pp] = as[pp * (k + 1) + j];
+    }
+    // dX tile per chunk: thread owns pixels 4 pq .. 4 pq + 3 and dims 2 dg, 2 dg + 1 of the chunk;
+    // the chunk's centroid columns are restaged unpadded, cs2[j][DCH], for float2 reads
+    float *cs2 = &cs[0][0];
+    const int pq = t >> 4, dg = t & 15;
     for (int d0 = 0; d0 < D; d0 += DCH) {
         __syncthreads();
         for (int e = t; e < PT * DCH; e += blockDim.x) {
@@ -413,84 +458,90 @@ __global__ void __launch_bounds__(256) soft_back_kernel(const float *__restrict_
         }
         for (int e = t; e < k * DCH; e += blockDim.x) {
             const int j = e / DCH, dd = e % DCH;
-            cs[j][dd] = d0 + dd < D ? C[(size_t)j * D + d0 + dd] : 0.f;
+            cs2[e] = d0 + dd < D ? C[(size_t)j * D + d0 + dd] : 0.f;
         }
         __syncthreads();
-        float ac[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        float ac[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 4
         for (int j = 0; j < k; ++j) {
-            const float a0 = as[(2 * u) * (k + 1) + j], a1 = as[(2 * u + 1) * (k + 1) + j];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float cv = cs[j][4 * v + c];
-                ac[0][c] = fmaf(a0, cv, ac[0][c]);
-                ac[1][c] = fmaf(a1, cv, ac[1][c]);
-            }
+            const float4 a4 = *reinterpret_cast<const float4 *>(at + j * (PT + 4) + 4 * pq);
+            const float2 c2 = *reinterpret_cast<const float2 *>(cs2 + j * DCH + 2 * dg);
+            ac[0][0] = fmaf(a4.x, c2.x, ac[0][0]);
+            ac[0][1] = fmaf(a4.x, c2.y, ac[0][1]);
+            ac[1][0] = fmaf(a4.y, c2.x, ac[1][0]);
+            ac[1][1] = fmaf(a4.y, c2.y, ac[1][1]);
+            ac[2][0] = fmaf(a4.z, c2.x, ac[2][0]);
+            ac[2][1] = fmaf(a4.z, c2.y, ac[2][1]);
+            ac[3][0] = fmaf(a4.w, c2.x, ac[3][0]);
+            ac[3][1] = fmaf(a4.w, c2.y, ac[3][1]);
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int pp = 2 * u + r;
+        for (int r = 0; r < 4; ++r) {
+            const int pp = 4 * pq + r;
             const long long g = p0 + pp;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int d = d0 + 4 * v + c;
-                if (g < n && d < D) dX[g * D + d] = 2.0f * (asum_s[pp] * xs[pp][4 * v + c] - ac[r][c]);
+            for (int c = 0; c < 2; ++c) {
+                const int d = d0 + 2 * dg + c;
+                if (g < n && d < D) dX[g * D + d] = 2.0f * (asum_s[pp] * xs[pp][2 * dg + c] - ac[r][c]);
             }
         }
     }
 }
 
-// Partial centroid gradients over a pixel slice, one output tile of 32 centroids x 64 dims per
-// block (thread: 2 centroids x 4 dims in registers): part[slice][j D + d] = sum_u a_j(u) x_u[d];
-// the j-tile's first d-tile also writes part[slice][k D + j] = sum_u a_j(u).
+// Partial centroid gradients over a pixel slice, one output tile of 64 centroids x 64 dims per
+// block (thread: 4 centroids x 4 dims in registers, float4 shared-memory reads):
+// part[slice][j D + d] = sum_u a_j(u) x_u[d]; the j-tile's first d-tile also writes
+// part[slice][k D + j] = sum_u a_j(u).
+constexpr int DCU = 32;            // pixels staged per step of the centroid-gradient reduction
 __global__ void __launch_bounds__(256) dc_partial_kernel(const float *__restrict__ A, const float *__restrict__ X,
                                                          long long n, int D, int k, int nslice,
                                                          float *__restrict__ part)
 {
-    __shared__ float at[32][33];
-    __shared__ float xt[32][65];
-    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;        // centroids 2 ty, 2 ty + 1; dims 4 tx..
-    const int j0 = blockIdx.x * 32, d0 = blockIdx.y * 64;
+    __shared__ __align__(16) float at[DCU][64 + 4];
+    __shared__ __align__(16) float xt[DCU][64 + 4];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;        // centroids 4 ty.., dims 4 tx..
+    const int j0 = blockIdx.x * 64, d0 = blockIdx.y * 64;
     const int slice = blockIdx.z;
     const long long per = (n + nslice - 1) / nslice;
     const long long u0 = (long long)slice * per, u1 = min(n, u0 + per);
-    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-    float as0 = 0.f, as1 = 0.f;
-    for (long long t0 = u0; t0 < u1; t0 += 32) {
-        const int m = (int)min(32LL, u1 - t0);
+    float acc[4][4] = {};
+    float asum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long t0 = u0; t0 < u1; t0 += DCU) {
+        const int m = (int)min((long long)DCU, u1 - t0);
         __syncthreads();
-        for (int e = t; e < 32 * 32; e += blockDim.x) {
-            const int uu = e >> 5, jj = e & 31;
+        for (int e = t; e < DCU * 64; e += blockDim.x) {
+            const int uu = e >> 6, jj = e & 63;
             at[uu][jj] = (uu < m && j0 + jj < k) ? A[(t0 + uu) * k + j0 + jj] : 0.f;
         }
-        for (int e = t; e < 32 * 64; e += blockDim.x) {
+        for (int e = t; e < DCU * 64; e += blockDim.x) {
             const int uu = e >> 6, dd = e & 63;
             xt[uu][dd] = (uu < m && d0 + dd < D) ? X[(t0 + uu) * D + d0 + dd] : 0.f;
         }
         __syncthreads();
-#pragma unroll 8
-        for (int uu = 0; uu < 32; ++uu) {
-            const float a0 = at[uu][2 * ty], a1 = at[uu][2 * ty + 1];
-            as0 += a0;
-            as1 += a1;
+#pragma unroll 4
+        for (int uu = 0; uu < DCU; ++uu) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&at[uu][4 * ty]);
+            const float4 x4 = *reinterpret_cast<const float4 *>(&xt[uu][4 * tx]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float xv = xt[uu][4 * tx + c];
-                acc[0][c] = fmaf(a0, xv, acc[0][c]);
-                acc[1][c] = fmaf(a1, xv, acc[1][c]);
+            for (int r = 0; r < 4; ++r) {
+                asum[r] += av[r];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], xv[c], acc[r][c]);
             }
         }
     }
     float *o = part + (size_t)slice * ((size_t)k * D + k);
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int j = j0 + 2 * ty + r;
+    for (int r = 0; r < 4; ++r) {
+        const int j = j0 + 4 * ty + r;
         if (j >= k) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int d = d0 + 4 * tx + c;
             if (d < D) o[(size_t)j * D + d] = acc[r][c];
         }
-        if (blockIdx.y == 0 && tx == 0) o[(size_t)k * D + j] = r ? as1 : as0;
+        if (blockIdx.y == 0 && tx == 0) o[(size_t)k * D + j] = asum[r];
     }
 }
 
@@ -509,6 +560,44 @@ __global__ void dc_reduce_kernel(const float *__restrict__ part, int nslice, int
         a += part[(size_t)q * (kD + k) + kD + j];
     }
     dC[o] = 2.0f * (a * C[o] - s);
+}
+
+template <int KI>
+cudaError_t launch_soft_p_ki(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
+                             float *P, cudaStream_t s)
+{
+    const size_t sm = sizeof(float) * ((PT + 16 * KI) * (DCH + 1) + 16 * KI * (PT + 1));
+    cudaError_t e = cudaFuncSetAttribute(soft_p_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    soft_p_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soft_p(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
+                          float *P, cudaStream_t s)
+{
+    if (k <= 32) return launch_soft_p_ki<2>(X, n, npi, D, C, k, tau, P, s);
+    if (k <= 64) return launch_soft_p_ki<4>(X, n, npi, D, C, k, tau, P, s);
+    return launch_soft_p_ki<8>(X, n, npi, D, C, k, tau, P, s);
+}
+
+template <int KI>
+cudaError_t launch_soft_back_ki(const float *X, long long n, long long npi, int D, const float *C, int k,
+                                float tau, const float *Gp, float *A, float *dX, cudaStream_t s)
+{
+    const size_t sm = sizeof(float) * ((PT + 16 * KI) * (DCH + 1) + PT * (16 * KI + 1) + PT + 16 * KI * (PT + 4));
+    cudaError_t e = cudaFuncSetAttribute(soft_back_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    soft_back_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, Gp, A, dX);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_soft_back(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
+                             const float *Gp, float *A, float *dX, cudaStream_t s)
+{
+    if (k <= 32) return launch_soft_back_ki<2>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
+    if (k <= 64) return launch_soft_back_ki<4>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
+    return launch_soft_back_ki<8>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
 }
 
 }  // namespace
@@ -565,7 +654,6 @@ SoftWs carve_soft(WsCursor &c, int B, int H, int W, int D, int k, int th, int tw
     w.Pt = c.take<float>((size_t)k * th * tw);
     w.T = c.take<float>((size_t)sg.F * k);
     w.L1 = c.take<float>((size_t)B * sg.F * (H - th + 1) * (W - tw + 1));
-    w.Z = w.RW;                                               // backward reuses the row-sum area
     w.R2 = w.P;                                               // and the soft-assignment area
     w.G = c.take<float>((size_t)B * k * plane);
     w.A = c.take<float>((size_t)B * k * plane);
@@ -580,11 +668,10 @@ cudaError_t soft_forward(const float *Qf, int B, int H, int W, const float *Tf, 
                          SoftWs &w, cudaStream_t s)
 {
     const long long nq = (long long)B * H * W, nt = (long long)th * tw;
-    const size_t psm = sizeof(float) * ((PT + kSoftMaxK) * (DCH + 1) + kSoftMaxK * (PT + 1));
-    cudaError_t e = cudaFuncSetAttribute(soft_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm);
+    cudaError_t e = launch_soft_p(Qf, nq, (long long)H * W, D, C, k, tau, w.P, s);
     if (e != cudaSuccess) return e;
-    soft_p_kernel<<<(unsigned)((nq + PT - 1) / PT), 256, psm, s>>>(Qf, nq, (long long)H * W, D, C, k, tau, w.P);
-    soft_p_kernel<<<(unsigned)((nt + PT - 1) / PT), 256, psm, s>>>(Tf, nt, nt, D, C, k, tau, w.Pt);
+    e = launch_soft_p(Tf, nt, nt, D, C, k, tau, w.Pt, s);
+    if (e != cudaSuccess) return e;
     const long long planes = (long long)B * k;
     for (int iw = 0; iw < sg.nw; ++iw) {
         dim3 g((unsigned)(planes * H), (W + 128 * SEG - 1) / (128 * SEG));
@@ -619,23 +706,28 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
     if (e != cudaSuccess) return e;
     const long long planes = (long long)B * k;
     for (int is = 0; is < sg.ns; ++is) {
-        const int h = sg.hgt[sg.size_h[is]], wd = sg.wid[sg.size_w[is]];
-        dim3 g1((W + 127) / 128, H, (unsigned)planes);
-        soft_gather_kernel<<<g1, 128, 0, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.Z, w.dT);
-        dim3 g2((unsigned)(planes * H), (W + 128 * SEG - 1) / (128 * SEG));
-        adj_row_kernel<<<g2, 128, 0, s>>>(w.Z, H, W, h, wd, w.R2);
+        const int h = sg.hgt[sg.size_h[is]];
+        int ncell = 0;
+        for (int f = 0; f < sg.F; ++f) ncell += sg.cell[f].s == is;
+        const dim3 gg((unsigned)(planes * ((H - h + GROWS) / GROWS)));
+        const size_t zs = sizeof(float) * GROWS * W;
+        if (ncell <= 4)
+            soft_gather_kernel<4><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
+        else if (ncell <= 9)
+            soft_gather_kernel<9><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
+        else
+            soft_gather_kernel<kSoftMaxG * kSoftMaxG><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg,
+                                                                         is, w.R2, w.dT);
         dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
         adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
     }
-    const size_t bsm = sizeof(float) * ((PT + kSoftMaxK) * (DCH + 1) + PT * (kSoftMaxK + 1) + PT);
-    e = cudaFuncSetAttribute(soft_back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    e = launch_soft_back(Qf, nq, (long long)H * W, D, C, k, tau, w.G, w.A, dQf, s);
     if (e != cudaSuccess) return e;
-    soft_back_kernel<<<(unsigned)((nq + PT - 1) / PT), 256, bsm, s>>>(Qf, nq, (long long)H * W, D, C, k, tau, w.G,
-                                                                       w.A, dQf);
     // template side: pixel gradients from dT, then its softmax backward (no feature gradient)
     tmpl_grad_kernel<<<(unsigned)((k * nt + 255) / 256), 256, 0, s>>>(w.dT, th, tw, k, sg, w.G);
-    soft_back_kernel<<<(unsigned)((nt + PT - 1) / PT), 256, bsm, s>>>(Tf, nt, nt, D, C, k, tau, w.G, w.At, nullptr);
-    dim3 gp((k + 31) / 32, (D + 63) / 64, kSoftSlices);
+    e = launch_soft_back(Tf, nt, nt, D, C, k, tau, w.G, w.At, nullptr, s);
+    if (e != cudaSuccess) return e;
+    dim3 gp((k + 63) / 64, (D + 63) / 64, kSoftSlices);
     dc_partial_kernel<<<gp, 256, 0, s>>>(w.A, Qf, nq, D, k, kSoftSlices, w.part);
     dc_partial_kernel<<<gp, 256, 0, s>>>(w.At, Tf, nt, D, k, kSoftSlices, w.part + (size_t)kSoftSlices * (k * D + k));
     dc_reduce_kernel<<<(k * D + 255) / 256, 256, 0, s>>>(w.part, 2 * kSoftSlices, D, k, C, dC);

@@ -33,8 +33,7 @@ struct SoftWs {
     float *Pt;     // k x th x tw       template soft assignment
     float *T;      // F x k             template soft counts
     float *L1;     // B x F x HO x WO   per-filter L1 distances
-    float *Z;      // B x k x H x W     adjoint gather of one cell size (reuses RW)
-    float *R2;     // B x k x H x W     adjoint row pass of one cell size (reuses P)
+    float *R2;     // B x k x H x W     gradient gather + adjoint row pass of one cell size (reuses P)
     float *G;      // B x k x H x W     dL/dp of the query pixels (planar)
     float *A;      // B x H x W x k     dL/dd of the query pixels (pixel-major)
     float *At;     // th x tw x k       dL/dd of the template pixels

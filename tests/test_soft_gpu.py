@@ -20,24 +20,19 @@ def vq():
     return m
 
 
-def _case(B, H, W, D, k, th, tw, seed):
+def _case(B, H, W, D, k, th, tw, seed, scale=1.0):
     r = np.random.default_rng(seed)
-    C = r.normal(0, 1, (k, D)).astype(np.float32)
+    C = r.normal(0, scale, (k, D)).astype(np.float32)
     lab = r.integers(0, k, (B, H, W))
-    Q = (C[lab] + r.normal(0, 0.6, (B, H, W, D))).astype(np.float32)
-    T = (Q[0, 2:2 + th, 3:3 + tw] + r.normal(0, 0.2, (th, tw, D))).astype(np.float32)
+    Q = (C[lab] + r.normal(0, 0.6 * scale, (B, H, W, D))).astype(np.float32)
+    T = (Q[0, 2:2 + th, 3:3 + tw] + r.normal(0, 0.2 * scale, (th, tw, D))).astype(np.float32)
     return Q, T, C
 
 
-@pytest.mark.parametrize("B,H,W,D,k,th,tw,G,tau", [
-    (2, 40, 37, 12, 10, 16, 14, 3, 0.3),
-    (1, 64, 64, 16, 8, 21, 24, 3, 0.1),      # the FD instance of the differentiation workload
-    (1, 48, 52, 256, 64, 18, 20, 3, 0.1),    # the workload's D and k
-    (3, 20, 23, 5, 3, 9, 8, 2, 1.0),
-])
-def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
-    Q, T, C = _case(B, H, W, D, k, th, tw, seed=B * 100 + H)
-    r = np.random.default_rng(9)
+def _check(vq, Q, T, C, tau, G, seed=9):
+    B, H, W, _ = Q.shape
+    th, tw = T.shape[:2]
+    r = np.random.default_rng(seed)
     wf = r.uniform(0.5, 1.5, G * G).astype(np.float32)
     Gw = r.normal(0, 1, (B, H - th + 1, W - tw + 1)).astype(np.float32)
     Qd = torch.tensor(Q, device="cuda", requires_grad=True)
@@ -52,6 +47,26 @@ def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
     for name, g, rr in (("dQ", Qd.grad, dQ), ("dC", Cd.grad, dC), ("dw", wd.grad, dw)):
         g = g.cpu().numpy()
         assert np.abs(g - rr).max() <= 1e-3 * np.abs(rr).max(), name
+
+
+@pytest.mark.parametrize("B,H,W,D,k,th,tw,G,tau", [
+    (2, 40, 37, 12, 10, 16, 14, 3, 0.3),
+    (1, 64, 64, 16, 8, 21, 24, 3, 0.1),      # the FD instance of the differentiation workload
+    (1, 48, 52, 256, 64, 18, 20, 3, 0.1),    # the workload's D and k
+    (3, 20, 23, 5, 3, 9, 8, 2, 1.0),
+    (3, 6, 7, 5, 3, 4, 3, 2, 0.5),           # H x W = 42 < 64: one pixel tile spans all three items
+])
+def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
+    Q, T, C = _case(B, H, W, D, k, th, tw, seed=B * 100 + H)
+    _check(vq, Q, T, C, tau, G)
+
+
+@pytest.mark.parametrize("tau", [0.02, 0.05, 0.3, 1.0])
+def test_soft_tau_sweep(vq, tau):
+    # the temperature sweep of the differentiation workload (0.02 .. 1.0); features scaled so
+    # that the logit gaps (d_other - d_own) / tau run from ~150 (nearly hard) to ~3 (soft)
+    Q, T, C = _case(2, 44, 41, 16, 8, 17, 15, seed=77, scale=0.3)
+    _check(vq, Q, T, C, tau, 3)
 
 
 def test_soft_limits(vq):
