@@ -39,12 +39,12 @@ METRIC = "query Mpix/s at 2048^2, D=512, k=128: BF16 vs FP32 path, % of roofline
 OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum), from the ncu capture summarised in
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,179,409,920 + 5,074,944 bytes),
 # profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,196,549,000 + 5,988,608 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2196549000 + 5988608) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "1fc4d73920c77bde8ae08ba47f47877cfc16e80949355b4330ab3f35ae80ef32"
+TC_TRAFFIC_PER_PX = (2179409920 + 5074944) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "ab7738fdd9568ac1b645b56eaa758db9c7291b6bb7588b0792e1e42d1d0985a7"
 
 
 
@@ -334,6 +334,7 @@ def run_gpu(args, rank, world):
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev)
     paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
     soft_vq = None if args.no_soft else run_soft(vq, dev)
+    batch = None if args.no_batch else run_batch(vq, dev)
 
     if rank != 0:
         return None
@@ -361,7 +362,7 @@ def run_gpu(args, rank, world):
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "roofline_score": roof_score, "clocks": clocks, "e2e": e2e,
-        "paper_bank": paper, "soft_vq": soft_vq,
+        "paper_bank": paper, "soft_vq": soft_vq, "batch": batch,
         f"{other}_path": None if ms2 is None else {
             "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
             "ms_per_step": round(ms2, 4),
@@ -491,6 +492,65 @@ def run_soft(vq, dev, reps=3):
             "note": "backward includes the autograd engine's elementwise product and sum of the loss"}
 
 
+def run_batch(vq, dev, reps=2):
+    """Batching: 64 templates (sides ~U{16..192} per axis, k ~U{8, 16, 32, 64, 128, 256}, warped
+    crops as in the headline workload) against 16 queries (sides ~U{512..2048} per axis), D = 256,
+    FP32 features, BF16 contraction; one vqnnf_match_batch call (every template's codebook,
+    NNF and responses, every query's NNFs, every pair's heatmap and maximum) captured in a
+    CUDA graph, tile plan from vqnnf_batch_tune."""
+    import numpy as np
+    import torch
+    import synth
+    r = np.random.default_rng(6000)
+    nq, nt, D, G, iters = 16, 64, 256, 3, 10
+    qsz = r.integers(512, 2049, (nq, 2))
+    tsz = r.integers(16, 193, (nt, 2))
+    ks = [int(v) for v in r.choice([8, 16, 32, 64, 128, 256], nt)]
+    Xs = []
+    for i, (H, W) in enumerate(qsz):
+        q = synth.query_map(int(H), int(W), D, M=128, n_sp=max(64, 20000 * int(H) * int(W) // 2048 ** 2),
+                            seed=6100 + i, device=dev)
+        Xs.append(q)
+    Ts = [synth.warped_template(Xs[j % nq], int(h), int(w), seed=6300 + j)[0] for j, (h, w) in enumerate(tsz)]
+    Xs = [q.X for q in Xs]
+    plan = vq.vqnnf_batch_tune(Xs, Ts, ks, iters, 6500, G)
+    heats = [torch.empty((X.shape[0] - T.shape[0] + 1, X.shape[1] - T.shape[1] + 1), device=dev)
+             for X in Xs for T in Ts]
+    am = torch.empty((nq, nt, 2), dtype=torch.int32, device=dev)
+    ws = vq.Workspace(vq.vqnnf_batch_workspace_bytes(Xs, Ts, ks, G), dev)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    with torch.cuda.stream(s):
+        for _ in range(reps):
+            g.replay()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    px = sum(int(X.shape[0]) * int(X.shape[1]) for X in Xs)
+    cols = sum((k + 31) // 32 * 32 for k in ks)
+    out = {"workload": f"{nq} queries ~U{{512..2048}}^2, {nt} templates ~U{{16..192}}^2, "
+                       f"k ~U{{8..256}}, D={D}, grid bank G={G}, {iters} Lloyd steps; all pairs",
+           "ms_per_batch": round(ms, 2), "pairs_per_s": round(nq * nt / (ms * 1e-3), 1),
+           "query_mpix_per_s": round(px / (ms * 1e-3) / 1e6, 2),
+           "pair_mpix_per_s": round(px * nt / (ms * 1e-3) / 1e6, 1),
+           "plan": {"group_cols": plan.group_cols, "sf": plan.sf, "pf": plan.pf},
+           "codebook_columns": cols, "query_px": px,
+           "execution": "one vqnnf_match_batch call per batch, CUDA graph replay"}
+    del g, heats, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev):
     import torch
     try:
@@ -599,6 +659,7 @@ def main():
     ap.add_argument("--query-size", type=int, default=HEADLINE["H"],
                     help="query side (profiling captures on a smaller case)")
     ap.add_argument("--no-soft", action="store_true", help="skip the soft-VQ training-path timing")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched many-templates timing")
     ap.add_argument("--no-paper-bank", action="store_true",
                     help="skip scoring with the paper's own filter bank")
     ap.add_argument("--no-compare", action="store_true",

@@ -235,6 +235,65 @@ vqnnf_status vqnnf_last_device_error(void *stream);
 /* ABI version of this header (major * 100 + minor). */
 int vqnnf_version(void);
 
+/* ---------------------------------------------------------------- batched matching
+ * Many templates against many queries: the template side of the method (codebook, NNF and
+ * filter responses, Sec. 3.1-3.2) is computed once per template and reused for every query,
+ * the reuse that the similarity measure allows across images (Sec. 4).  Template j gets its
+ * own codebook of k_j centroids (seeded initialisation with seed + j, `iters` Lloyd steps,
+ * BF16 contraction), its NNF and the responses of the grid bank: the full window plus the
+ * G x G cells of the window (boundaries floor(i * side / G)), w_f = 1, A_f the pixel count.
+ * Every query i is quantised against every template's codebook (Algorithm 1).  Templates whose
+ * codebooks, each padded to a multiple of 32 centroids, fit one tensor-core contraction
+ * together (plan->group_cols columns, at most 8 codebooks) share it, so a query's features are
+ * read once per group rather than once per template; each codebook keeps its own exact
+ * labels (interval test and re-scoring as in vqnnf_assign).  Then every pair (i, j) gets the
+ * integral image of its NNF, the Eq. 2 heatmap and its maximum, as vqnnf_score computes them.
+ *   q       host array of nq >= 1 images: X device, H x W x D float32 (HWC), 16-byte aligned
+ *   t       host array of nt >= 1 templates: T device, h x w x D float32, 16-byte aligned;
+ *           1 <= k <= 256 and k <= h w;  every template fits every query (h <= H, w <= W)
+ *   D       feature length, a multiple of 16;  G: 1 <= G <= 4, G <= h and G <= w
+ *   plan    tile choices from vqnnf_batch_tune, or NULL for the defaults
+ *   heat    host array of nq * nt device pointers, pair (i, j) at [i * nt + j], each a
+ *           (H_i - h_j + 1) x (W_i - w_j + 1) float32 heatmap, written; or NULL for the
+ *           maxima only
+ *   argmax  device, nq * nt * 2 int32: (y, x) of each pair's best window, pair (i, j) at
+ *           [2 (i * nt + j)]
+ *   ws      device workspace of vqnnf_batch_workspace_bytes(q, nq, t, nt, D, G) bytes,
+ *           256-byte aligned
+ * The call only enqueues work (graph-capturable).  Limits: nq * nt <= 65536, n = H W < 2^31
+ * (else VQNNF_EUNSUPPORTED). */
+typedef struct vqnnf_image {
+    const float *X;
+    int32_t H, W;
+} vqnnf_image;
+
+typedef struct vqnnf_batch_template {
+    const float *T;
+    int32_t h, w, k;
+} vqnnf_batch_template;
+
+typedef struct vqnnf_batch_plan {
+    int32_t group_cols;   /* 128 or 256: columns of one shared contraction                 */
+    int32_t sf;           /* FP32 feature boxes in flight per SM: 0 (default) or 2, 4, 6, 8 */
+    int32_t pf;           /* L2 prefetch distance in 64-feature chunks, -1 = default       */
+    int32_t reserved;     /* 0                                                              */
+} vqnnf_batch_plan;
+
+size_t vqnnf_batch_workspace_bytes(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt,
+                                   int D, int G);
+vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                               int iters, uint64_t seed, int G, const vqnnf_batch_plan *plan,
+                               float *const *heat, int32_t *argmax_yx, void *ws, size_t ws_bytes,
+                               void *stream);
+
+/* Autotuner: fits the templates as vqnnf_match_batch does, then times the assignment of the
+ * largest query under each candidate plan (group_cols in {128, 256} x feature boxes in
+ * {4, 6, 8} x prefetch in {0, 8}) with CUDA events and writes the fastest to *plan.  It
+ * SYNCHRONISES `stream` (not graph-capturable); the workspace is the batch workspace. */
+vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                              int iters, uint64_t seed, int G, vqnnf_batch_plan *plan, void *ws,
+                              size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,3 +20,4 @@ from .api import (  # noqa: F401
 )
 from ._lib import VqnnfError  # noqa: F401
 from .soft import SoftHeatmap, soft_heatmap, soft_workspace_bytes  # noqa: F401
+from .batch import BatchPlan, vqnnf_batch_tune, vqnnf_batch_workspace_bytes, vqnnf_match_batch  # noqa: F401

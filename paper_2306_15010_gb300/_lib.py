@@ -35,6 +35,9 @@ SIGNATURES = {
     "vqnnf_soft_backward": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _vp, _i, ctypes.c_float, _i, _vp, _vp,
                                  _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "vqnnf_version": (_i, []),
+    "vqnnf_batch_workspace_bytes": (_sz, [_vp, _i, _vp, _i, _i, _i]),
+    "vqnnf_match_batch": (_i, [_vp, _i, _vp, _i, _i, _i, ctypes.c_uint64, _i, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "vqnnf_batch_tune": (_i, [_vp, _i, _vp, _i, _i, _i, ctypes.c_uint64, _i, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -46,6 +49,19 @@ class VqnnfRect(ctypes.Structure):
 class VqnnfFilter(ctypes.Structure):
     _fields_ = [("n_rects", ctypes.c_int32), ("rects", ctypes.POINTER(VqnnfRect)),
                 ("w_f", ctypes.c_float), ("area", ctypes.c_float)]
+
+
+class VqnnfImage(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32)]
+
+
+class VqnnfBatchTemplate(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_void_p), ("h", ctypes.c_int32), ("w", ctypes.c_int32), ("k", ctypes.c_int32)]
+
+
+class VqnnfBatchPlan(ctypes.Structure):
+    _fields_ = [("group_cols", ctypes.c_int32), ("sf", ctypes.c_int32), ("pf", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class VqnnfError(RuntimeError):

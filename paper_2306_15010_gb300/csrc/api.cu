@@ -6,12 +6,13 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "driver.cuh"
 #include "score_spec.cuh"
 #include "soft_spec.cuh"
 
 using namespace vqnnf;
 
-namespace {
+namespace vqnnf {
 
 constexpr int kVersion = 100;
 
@@ -20,11 +21,6 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 // ----------------------------------------------------------------------------------
 // Workspace layouts (the same code computes sizes with a null base).
 // ----------------------------------------------------------------------------------
-struct AssignWs {
-    CodebookPrep prep;
-    FlagList fl;
-};
-
 AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
 {
     AssignWs w;
@@ -43,12 +39,6 @@ AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
     return w;
 }
 
-struct FitWs {
-    AssignWs as;
-    uint8_t *lab;
-    int *cnt, *off, *members;
-};
-
 FitWs carve_fit(WsCursor &c, long long l, int D, int k)
 {
     FitWs w;
@@ -59,14 +49,6 @@ FitWs carve_fit(WsCursor &c, long long l, int D, int k)
     w.members = c.take<int>((size_t)l);
     return w;
 }
-
-struct ScoreWs {
-    void *S;          // integral image, uint16 (mod 2^16) or uint32, plus read slack
-    bool u16;
-    int *carry;
-    int *bandsum;
-    unsigned long long *amax;
-};
 
 ScoreWs carve_score(WsCursor &c, int H, int W, int k, int th, int tw)
 {
@@ -97,10 +79,10 @@ bool check_prec(int prec, int D)
 }
 
 // Profiling events set by vqnnf_set_kernel_events, per operation: {start, stop}.
-std::mutex g_ev_mu;
-cudaEvent_t g_ev[4][2] = {};
+static std::mutex g_ev_mu;
+static cudaEvent_t g_ev[4][2] = {};
 
-}  // namespace
+}  // namespace vqnnf
 
 cudaError_t vqnnf::record_kernel_event(int op, int which, cudaStream_t s)
 {
@@ -112,7 +94,7 @@ cudaError_t vqnnf::record_kernel_event(int op, int which, cudaStream_t s)
     return ev ? cudaEventRecord(ev, s) : cudaSuccess;
 }
 
-namespace {
+namespace vqnnf {
 
 // Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).
 vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
@@ -169,6 +151,24 @@ void kmeans_init_indices(long long l, int k, uint64_t seed, int32_t *out)
         set(j, vi);
         out[i] = (int32_t)vj;
     }
+}
+
+// Seeded initial centroids, then `iters` Lloyd steps (assignment + exact centroid means).
+vqnnf_status run_fit(const float *T, long long l, int D, int k, int iters, uint64_t seed, int prec,
+                     float *C, FitWs &fw, cudaStream_t s)
+{
+    InitIdx ii;
+    memset(&ii, 0, sizeof(ii));
+    kmeans_init_indices(l, k, seed, ii.idx);
+    cudaError_t e = launch_gather_init(T, D, k, ii, C, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int it = 0; it < iters; ++it) {
+        vqnnf_status st = run_assign(T, l, D, C, k, prec, fw.lab, nullptr, fw.as, s);
+        if (st != VQNNF_OK) return st;
+        e = launch_lloyd_update(T, (int)l, D, k, fw.lab, fw.cnt, fw.off, fw.members, C, s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return VQNNF_OK;
 }
 
 // ----------------------------------------------------------------------------------
@@ -360,7 +360,7 @@ int device_smem_optin()
     return v;
 }
 
-}  // namespace
+}  // namespace vqnnf
 
 extern "C" {
 
@@ -434,21 +434,9 @@ vqnnf_status vqnnf_fit_codebook(const float *T, int h, int w, int D, int k, int 
     if (l > (1ll << 30)) return VQNNF_EUNSUPPORTED;
     if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_FIT, h, w, D, k, 0, 0, 0, prec))
         return VQNNF_ENOMEM;
-    cudaStream_t s = as_stream(stream);
     WsCursor c{static_cast<char *>(ws), 0};
     FitWs fw = carve_fit(c, l, D, k);
-    InitIdx ii;
-    memset(&ii, 0, sizeof(ii));
-    kmeans_init_indices(l, k, seed, ii.idx);
-    cudaError_t e = launch_gather_init(T, D, k, ii, C, s);
-    if (e != cudaSuccess) return from_cuda(e);
-    for (int it = 0; it < iters; ++it) {
-        vqnnf_status st = run_assign(T, l, D, C, k, prec, fw.lab, nullptr, fw.as, s);
-        if (st != VQNNF_OK) return st;
-        e = launch_lloyd_update(T, (int)l, D, k, fw.lab, fw.cnt, fw.off, fw.members, C, s);
-        if (e != cudaSuccess) return from_cuda(e);
-    }
-    return VQNNF_OK;
+    return run_fit(T, l, D, k, iters, seed, prec, C, fw, as_stream(stream));
 }
 
 vqnnf_status vqnnf_filter_responses(const uint8_t *labels, int h, int w, int k,

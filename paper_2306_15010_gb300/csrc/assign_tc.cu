@@ -8,19 +8,24 @@
 // interval test as the FP32 path (assign_fp32.cu) and flags ambiguous pixels for the
 // shared re-scoring stage, so labels stay exact.
 //
-// One persistent CTA per SM, 128-pixel tiles, warp-specialised:
+// One persistent CTA per SM, 128-pixel tiles, warp-specialised (23 warps):
 //   warp 0      TMA producer of the FP32 feature boxes (128 rows x 32 floats, 128B swizzle),
 //               up to eight boxes in flight, plus L2 prefetch further ahead
-//   warp 14     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
+//   warp 22     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
 //               swizzle); separate from warp 0 so that feature loads never wait for MMAs
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warps 2-9   converters: thread (h, r) owns pixel row r and the h-th 32-column box of
-//               every 64-column chunk; FP32 -> centred BF16 hi and lo planes stored with
-//               tcgen05.st straight into tensor memory, where the MMA reads its A operand (row r
-//               in lane r, two K elements per 32-bit column), so the pixel planes never pass
-//               through shared memory; accumulates its part of ||x'||^2
-//   warps 10-13 epilogue: tcgen05.ld of the row's k accumulators, interval test, label,
-//               flag push; the TMEM accumulator is double-buffered when k <= 128
+//   warps 2-17  converters: warp w writes TMEM lane group w % 4 (pixel rows 32 (w % 4) ..)
+//               and the 16-column quarter (w - 2) / 4 of every 64-column chunk; FP32 ->
+//               centred BF16 hi and lo planes stored with tcgen05.st straight into tensor
+//               memory, where the MMA reads its A operand (row r in lane r, two K elements per
+//               32-bit column), so the pixel planes never pass through shared memory;
+//               accumulates its part of ||x'||^2
+//   warps 18-21 epilogue: tcgen05.ld of the row's accumulators, interval test, label, flag
+//               push; the TMEM accumulator is double-buffered when k <= 128
+// The columns may hold several codebooks side by side (segments, each padded to 32 columns,
+// at most 256 columns in all): the contraction is shared and the epilogue takes each
+// segment's nearest centroid, interval test, labels and flag list on its own.  One codebook
+// is the single-segment case.
 // Every mbarrier wait is bounded: on timeout the CTA records VQNNF_ETIMEOUT in the device
 // error word, all roles leave their loops, in-flight copies and MMAs are drained (bounded)
 // and the tensor memory is released before the kernel returns.
@@ -29,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <cfloat>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -51,11 +57,11 @@ constexpr int PF = 8;              // chunks prefetched into L2 ahead of the loa
 
 struct TcArgs {
     long long n;
-    int D, k, npad, nkc, sb, sf, nb, sa, pf;
+    int D, krows, npad, nkc, sb, sf, nb, sa, pf;   // krows: rows of the prepared codebook
     long long ntiles;
     CodebookPrep p;
-    uint8_t *labels;
-    FlagList fl;
+    int nseg;
+    TcSeg seg[kMaxSeg];
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int npad = g.npad, D = g.D, k = g.k, nkc = g.nkc, SB = g.sb, SF = g.sf, NB = g.nb, SA = g.sa;
+    const int npad = g.npad, D = g.D, nkc = g.nkc, SB = g.sb, SF = g.sf, NB = g.nb, SA = g.sa;
     const int B_PLANE = npad * 128;
     uint8_t *f32s = base;                                  // SF x 16 KB
     uint8_t *bs = f32s + SF * F32_BOX;                     // SB x (hi, lo)
@@ -259,7 +265,9 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     float *mean = reinterpret_cast<float *>(colc + npad);  // roundup(D, 64)
     float *norms = mean + nkc * KC;                        // [2 buf][4 quarters][128]
     uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 4 * TM);   // [128][8]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(maskbuf + TM * kMaskWords);
+    float4 *segmx = reinterpret_cast<float4 *>(maskbuf + TM * kMaskWords);   // per segment maxima
+    TcSeg *segt = reinterpret_cast<TcSeg *>(segmx + kMaxSeg);                // segment table
+    uint64_t *bar = reinterpret_cast<uint64_t *>(segt + kMaxSeg);
     uint64_t *full_f = bar, *empty_f = bar + SF, *a_full = bar + 2 * SF, *a_empty = bar + 2 * SF + SA;
     uint64_t *full_b = bar + 2 * SF + 2 * SA, *empty_b = full_b + kMaxSB;
     uint64_t *acc_full = empty_b + kMaxSB, *acc_empty = acc_full + 2, *nrm_full = acc_empty + 2,
@@ -275,12 +283,19 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     const uint32_t tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 
     for (int j = tid; j < npad; j += NT) {
-        const bool ok = j < k;
-        const int jc = ok ? j : k - 1;
+        bool ok = false;                                  // a real centroid of some segment
+#pragma unroll
+        for (int q = 0; q < kMaxSeg; ++q)
+            ok |= q < g.nseg && j >= g.seg[q].col0 && j < g.seg[q].col0 + g.seg[q].k;
+        const int jc = j < g.krows ? j : g.krows - 1;
         const float nrm = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
         cn[j] = nrm;
         colc[j] = make_float4(nrm, ok ? g.p.a[jc] : 0.f, ok ? g.p.v[jc] : 0.f, ok ? g.p.b[jc] : 0.f);
     }
+    // segment table (static indices into the kernel parameters)
+#pragma unroll
+    for (int q = 0; q < kMaxSeg; ++q)
+        if (tid == q && q < g.nseg) segt[q] = g.seg[q];
     for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
     if (tid == 0) {
         for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], 2 * TM); }
@@ -481,17 +496,22 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const float u = (float)kU;
         const float u4 = 4.0f * u;
         const float infl = 1.0f + 0.00390625f;
-        // largest a_j, v_j, b_j and ||c_j*||^2 of the codebook: Bmax below bounds every B_j of a pixel
-        float amax_s = 0.f, vmax_s = 0.f, bmax_s = 0.f, nrm_max = 0.f;
-        for (int j = 0; j < k; ++j) {
-            const float4 c = colc[j];
-            nrm_max = fmaxf(nrm_max, c.x);
-            amax_s = fmaxf(amax_s, c.y);
-            vmax_s = fmaxf(vmax_s, c.z);
-            bmax_s = fmaxf(bmax_s, c.w);
+        const int nseg = g.nseg;
+        // per segment the largest ||c_j*||^2, a_j, v_j and b_j over its centroids (lane q of the
+        // first epilogue warp scans segment q): Bmax below bounds every B_j of a pixel within
+        // the segment
+        if (warp == 18 && lane < nseg) {
+            float nm = 0.f, am = 0.f, vm = 0.f, bm = 0.f;
+            for (int j = segt[lane].col0; j < segt[lane].col0 + segt[lane].k; ++j) {
+                const float4 c = colc[j];
+                nm = fmaxf(nm, c.x);
+                am = fmaxf(am, c.y);
+                vm = fmaxf(vm, c.z);
+                bm = fmaxf(bm, c.w);
+            }
+            segmx[lane] = make_float4(nm, am, vm, bm);
         }
-        const float cnorm_max = sqrtf(nrm_max) * 1.0001f;    // max ||c_j*|| (cn = ||c*||^2 in FP32)
-        nrm_max *= 1.0001f;
+        asm volatile("bar.sync 1, 128;" ::: "memory");       // the four epilogue warps
         uint32_t tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
@@ -510,82 +530,91 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             mbar_arrive(&nrm_empty[nb]);
             const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
             const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
-            // pass 1: smallest score, lowest column on ties, as four interleaved running minima.
-            // Columns past k hold +inf in cn (never chosen).
-            float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
-            int am[4] = {0, 0, 0, 0};
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                float v[32];
-                tc_ld32(taddr + c0, v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
-                    if (s < sm[j & 3]) { sm[j & 3] = s; am[j & 3] = c0 + j; }
-                }
-            }
-            float smin = sm[0];
-            int amin = am[0];
-#pragma unroll
-            for (int q = 1; q < 4; ++q)
-                if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
-            // U, the upper end of column amin's interval, bounds the smallest distance from
-            // above, so the nearest column j has s_j - B_j <= U.
-            const float4 ca = colc[amin];
-            const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
-            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the contraction's
-            // own error, so Bmax >= every B_j of this pixel (the float evaluation is monotone).  The
-            // nearest column has s_j <= U + B_j <= U + Bmax; the limit U + 2 Bmax also covers the
-            // rounding of that sum (u |U| < Bmax / 2 because Bmax >= 4u |smin|).  A 32-column block
-            // where no lane has a column under the limit besides amin needs no per-column interval
-            // test: its only candidate is amin.
-            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
-            const float Bmax = fmaf(X, amax_s, fmaf(Y, vmax_s, fmaf(u4, smax_abs, bmax_s))) * infl;
-            const float lim = U + 2.0f * Bmax;
-            int cnt = 0, last = amin;
-            for (int c0 = 0; c0 < npad; c0 += 32) {
-                float v[32];
-                tc_ld32(taddr + c0, v);
-                uint32_t maybe = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
-                const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
-                uint32_t word = own;
-                if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
-                    word = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float4 c = colc[c0 + j];
-                        const float s = fmaf(-2.0f, v[j], c.x);
-                        const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(s), c.w))) * infl;
-                        word |= (uint32_t)(s - B <= U) << j;
-                    }
-                }
-                cnt += __popc(word);
-                if (word) last = c0 + 31 - __clz(word);
-                maskbuf[r * kMaskWords + (c0 >> 5)] = word;
-            }
-
-            for (int w = (npad + 31) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
-            tc_fence_before();
-            mbar_arrive(&acc_empty[buf]);
             const long long pix = tile * TM + r;
             const bool valid = pix < g.n;
-            const int lab = cnt == 1 ? last : amin;
-            if (valid) g.labels[pix] = (uint8_t)lab;
-            const bool flagged = valid && cnt > 1;
-            const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
-            if (ballot) {
-                const int leader = __ffs(ballot) - 1;
-                unsigned basei = 0;
-                if (lane == leader) basei = atomicAdd(g.fl.count, (unsigned)__popc(ballot));
-                basei = __shfl_sync(0xffffffffu, basei, leader);
-                if (flagged) {
-                    const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
-                    if (slot < (unsigned long long)g.n) {
-                        g.fl.pix[slot] = (unsigned)pix;
+            for (int sgi = 0; sgi < nseg; ++sgi) {
+                const int cb = segt[sgi].col0, ce = cb + segt[sgi].ncol;
+                const float4 mx = segmx[sgi];
+                const float cnorm_max = sqrtf(mx.x) * 1.0001f;    // max ||c_j*|| (cn = ||c*||^2 in FP32)
+                const float nrm_max = mx.x * 1.0001f;
+                // pass 1: smallest score of the segment, lowest column on ties, as four
+                // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
+                float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+                int am[4] = {cb, cb, cb, cb};
+                for (int c0 = cb; c0 < ce; c0 += 32) {
+                    float v[32];
+                    tc_ld32(taddr + c0, v);
 #pragma unroll
-                        for (int w = 0; w < kMaskWords; ++w)
-                            g.fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                    for (int j = 0; j < 32; ++j) {
+                        const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
+                        if (s < sm[j & 3]) { sm[j & 3] = s; am[j & 3] = c0 + j; }
+                    }
+                }
+                float smin = sm[0];
+                int amin = am[0];
+#pragma unroll
+                for (int q = 1; q < 4; ++q)
+                    if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
+                // U, the upper end of column amin's interval, bounds the smallest distance from
+                // above, so the nearest column j has s_j - B_j <= U.
+                const float4 ca = colc[amin];
+                const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+                // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
+                // contraction's own error, so Bmax >= every B_j of this pixel in the segment (the
+                // float evaluation is monotone).  The nearest column has s_j <= U + B_j <= U + Bmax;
+                // the limit U + 2 Bmax also covers the rounding of that sum (u |U| < Bmax / 2
+                // because Bmax >= 4u |smin|).  A 32-column block where no lane has a column under
+                // the limit besides amin needs no per-column interval test: its only candidate is
+                // amin.
+                const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
+                const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
+                const float lim = U + 2.0f * Bmax;
+                int cnt = 0, last = amin;
+                for (int c0 = cb; c0 < ce; c0 += 32) {
+                    float v[32];
+                    tc_ld32(taddr + c0, v);
+                    uint32_t maybe = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
+                    const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                    uint32_t word = own;
+                    if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
+                        word = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float4 c = colc[c0 + j];
+                            const float s = fmaf(-2.0f, v[j], c.x);
+                            const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(s), c.w))) * infl;
+                            word |= (uint32_t)(s - B <= U) << j;
+                        }
+                    }
+                    cnt += __popc(word);
+                    if (word) last = c0 + 31 - __clz(word);
+                    maskbuf[r * kMaskWords + ((c0 - cb) >> 5)] = word;
+                }
+                for (int w = (ce - cb) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
+                if (sgi == nseg - 1) {                      // every accumulator of the tile read
+                    tc_fence_before();
+                    mbar_arrive(&acc_empty[buf]);
+                }
+                const TcSeg &sq = segt[sgi];
+                const int lab = (cnt == 1 ? last : amin) - cb;
+                if (valid) sq.labels[pix] = (uint8_t)lab;
+                const bool flagged = valid && cnt > 1;
+                const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+                if (ballot) {
+                    const int leader = __ffs(ballot) - 1;
+                    unsigned basei = 0;
+                    if (lane == leader) basei = atomicAdd(sq.fl.count, (unsigned)__popc(ballot));
+                    basei = __shfl_sync(0xffffffffu, basei, leader);
+                    if (flagged) {
+                        const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
+                        if (slot < (unsigned long long)g.n) {
+                            sq.fl.pix[slot] = (unsigned)pix;
+#pragma unroll
+                            for (int w = 0; w < kMaskWords; ++w)
+                                sq.fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                        }
                     }
                 }
             }
@@ -639,30 +668,45 @@ size_t tc_smem_bytes(int npad, int D, int sb, int sf)
     b += (size_t)sf * F32_BOX + (size_t)sb * 2 * npad * 128;
     b += sizeof(float) * (5 * (size_t)npad + (size_t)nkc * KC + 8 * TM);
     b += sizeof(uint32_t) * TM * kMaskWords;
+    b += (sizeof(float4) + sizeof(TcSeg)) * kMaxSeg;
     b += sizeof(uint64_t) * (2 * sf + 2 * kMaxSA + 2 * kMaxSB + 8 + 1) + 16;   // barriers, TMEM slot, abort flag
     return b;
 }
 
 }  // namespace
 
-cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const CodebookPrep &p,
-                               uint8_t *labels, FlagList fl, cudaStream_t s)
+cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const CodebookPrep &p, int krows,
+                                   const TcSeg *seg, int nseg, int sf_req, int pf, cudaStream_t s)
 {
-    if (D % 16 != 0 || k < 1 || k > kMaxK) return cudaErrorNotSupported;
+    if (D % 16 != 0 || nseg < 1 || nseg > kMaxSeg || krows < 1 || n < 1) return cudaErrorNotSupported;
+    int npad = 0;
+    for (int q = 0; q < nseg; ++q) {
+        if (seg[q].col0 != npad || seg[q].ncol % 32 != 0 || seg[q].k < 1 || seg[q].k > seg[q].ncol ||
+            seg[q].col0 + seg[q].k > krows)
+            return cudaErrorNotSupported;
+        npad += seg[q].ncol;
+    }
+    if (npad > kMaxK) return cudaErrorNotSupported;
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int npad = (k + 31) / 32 * 32;      // UMMA N (multiple of 16) and whole 32-column TMEM loads
     // centroid stages (the codebook is streamed from L2 by every CTA) and feature boxes (HBM
-    // latency): the first split that fits
+    // latency): the first split that fits, or the requested feature-box count with as many
+    // centroid stages as fit
     static const int kSplit[][2] = {{3, 6}, {2, 8}, {2, 6}, {2, 4}, {1, 4}};
     int sb = 0, sf = 0;
     size_t smem = 0;
-    for (const auto &c : kSplit)
-        if ((smem = tc_smem_bytes(npad, D, c[0], c[1])) <= (size_t)optin) { sb = c[0]; sf = c[1]; break; }
+    if (sf_req > 0) {
+        if (sf_req < 2 || sf_req > kMaxSF || sf_req % 2) return cudaErrorNotSupported;
+        for (int b = 3; b >= 1 && !sf; --b)
+            if ((smem = tc_smem_bytes(npad, D, b, sf_req)) <= (size_t)optin) { sb = b; sf = sf_req; }
+    } else {
+        for (const auto &c : kSplit)
+            if ((smem = tc_smem_bytes(npad, D, c[0], c[1])) <= (size_t)optin) { sb = c[0]; sf = c[1]; break; }
+    }
     if (!sf) return cudaErrorNotSupported;
     // accumulators double-buffered when they fit beside two A stages in the 512 TMEM columns;
     // the remaining columns hold as many A stages as fit (at most four)
@@ -672,32 +716,46 @@ cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const 
     if ((e = make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)D, (uint64_t)n, (uint64_t)D * 4, 32,
                       TM)) != cudaSuccess)
         return e;
-    if ((e = make_map(&tmBhi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.chi, (uint64_t)D, (uint64_t)k,
+    if ((e = make_map(&tmBhi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.chi, (uint64_t)D, (uint64_t)krows,
                       (uint64_t)D * 2, KC, (uint32_t)npad)) != cudaSuccess)
         return e;
-    if ((e = make_map(&tmBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.clo, (uint64_t)D, (uint64_t)k,
+    if ((e = make_map(&tmBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.clo, (uint64_t)D, (uint64_t)krows,
                       (uint64_t)D * 2, KC, (uint32_t)npad)) != cudaSuccess)
         return e;
     TcArgs a;
+    memset(&a, 0, sizeof(a));
     a.n = n;
     a.D = D;
-    a.k = k;
+    a.krows = krows;
     a.npad = npad;
     a.nkc = (D + KC - 1) / KC;
     a.sb = sb;
     a.sf = sf;
     a.nb = nb;
     a.sa = sa;
-    a.pf = PF;
+    a.pf = pf < 0 ? PF : pf;
     a.ntiles = (n + TM - 1) / TM;
     a.p = p;
-    a.labels = labels;
-    a.fl = fl;
+    a.nseg = nseg;
+    for (int q = 0; q < nseg; ++q) a.seg[q] = seg[q];
     e = cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long grid = a.ntiles < sms ? a.ntiles : sms;
     assign_tc_kernel<<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const CodebookPrep &p,
+                               uint8_t *labels, FlagList fl, cudaStream_t s)
+{
+    if (k < 1 || k > kMaxK) return cudaErrorNotSupported;
+    TcSeg one;
+    one.col0 = 0;
+    one.ncol = (k + 31) / 32 * 32;            // UMMA N (multiple of 16) and whole 32-column TMEM loads
+    one.k = k;
+    one.labels = labels;
+    one.fl = fl;
+    return launch_assign_bf16_seg(X, n, D, p, k, &one, 1, 0, -1, s);
 }
 
 cudaError_t read_and_clear_tc_error(int *out)

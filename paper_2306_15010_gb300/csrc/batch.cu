@@ -1,0 +1,418 @@
+// Batched matching (vqnnf_match_batch, vqnnf_batch_tune): many templates against many queries.
+//
+// The template side of the method (codebook by k-means, template NNF, filter responses;
+// Sec. 3.1-3.2) runs once per template; every query is then quantised against every
+// template's codebook (Algorithm 1) and every pair gets its integral image, Eq. 2 heatmap and
+// maximum (Sec. 3.3).  Codebooks are packed into groups that share one tensor-core
+// contraction: each codebook padded to a multiple of 32 columns, at most plan.group_cols
+// columns (and eight codebooks) per group, first fit in template order.  The contraction
+// kernel keeps every codebook's argmin, interval test, labels and flag list apart (segments),
+// so a query's features are read from HBM once per group instead of once per template.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "driver.cuh"
+#include "score_spec.cuh"
+
+using namespace vqnnf;
+
+namespace {
+
+constexpr int kGroupRows = kMaxK;            // rows of one group codebook, at most
+
+struct GroupSrc {
+    int nseg;
+    int col0[kMaxSeg], ncol[kMaxSeg], k[kMaxSeg];
+    const float *C[kMaxSeg];
+};
+
+// Group codebook: row r of segment q is centroid r - col0[q] of codebook q; its padding rows
+// repeat centroid 0 (the contraction kernel never picks a padding column).
+__global__ void group_codebook_kernel(GroupSrc g, int D, float *__restrict__ Cg)
+{
+    const int r = blockIdx.x;
+    const float *src = nullptr;
+#pragma unroll
+    for (int q = 0; q < kMaxSeg; ++q)
+        if (q < g.nseg && r >= g.col0[q] && r < g.col0[q] + g.ncol[q]) {
+            const int li = r - g.col0[q];
+            src = g.C[q] + (size_t)(li < g.k[q] ? li : 0) * D;
+        }
+    if (!src) return;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) Cg[(size_t)r * D + d] = src[d];
+}
+
+struct Group {
+    int nseg = 0, npad = 0;
+    int tj[kMaxSeg];                          // template of each segment
+};
+
+struct BatchWs {
+    std::vector<float *> C;                   // per template: codebook k x D
+    std::vector<uint8_t *> tlab;              // per template: NNF h x w
+    std::vector<int32_t *> tcnt;              // per template: responses F x k
+    std::vector<float *> gC;                  // per group slot: group codebook
+    std::vector<CodebookPrep> gprep;          // per group slot: its prepared planes
+    std::vector<uint8_t *> qlab;              // per template: the current query's NNF
+    unsigned *flcount;                        // kMaxSeg x 64 (counters and stats, one memset)
+    FlagList fl[kMaxSeg];
+    FitWs fit;
+    char *score_base;                         // integral-image workspace of one pair
+    float *heat_scratch;                      // heatmap of one pair when the caller wants maxima only
+};
+
+int bank_size(int G) { return 1 + G * G; }
+
+BatchWs carve_batch(WsCursor &c, const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                    int G)
+{
+    BatchWs w;
+    long long n_max = 0, l_max = 0, hw_max = 0;
+    int k_max = 1, H_max = 1, W_max = 1;
+    for (int i = 0; i < nq; ++i) {
+        n_max = std::max(n_max, (long long)q[i].H * q[i].W);
+        H_max = std::max(H_max, (int)q[i].H);
+        W_max = std::max(W_max, (int)q[i].W);
+    }
+    for (int j = 0; j < nt; ++j) {
+        l_max = std::max(l_max, (long long)t[j].h * t[j].w);
+        k_max = std::max(k_max, (int)t[j].k);
+    }
+    for (int i = 0; i < nq; ++i)
+        for (int j = 0; j < nt; ++j)
+            hw_max = std::max(hw_max, (long long)(q[i].H - t[j].h + 1) * (q[i].W - t[j].w + 1));
+    const int F = bank_size(G);
+    for (int j = 0; j < nt; ++j) {
+        w.C.push_back(c.take<float>((size_t)t[j].k * D));
+        w.tlab.push_back(c.take<uint8_t>((size_t)t[j].h * t[j].w));
+        w.tcnt.push_back(c.take<int32_t>((size_t)F * t[j].k));
+    }
+    for (int g = 0; g < nt; ++g) {            // at most one group per template
+        w.gC.push_back(c.take<float>((size_t)kGroupRows * D));
+        CodebookPrep p;
+        p.mean = c.take<float>((size_t)D);
+        p.cc = c.take<float>((size_t)kGroupRows * D);
+        p.chi = c.take<uint16_t>((size_t)kGroupRows * D);
+        p.clo = c.take<uint16_t>((size_t)kGroupRows * D);
+        p.nrm = c.take<float>(kGroupRows);
+        p.a = c.take<float>(kGroupRows);
+        p.v = c.take<float>(kGroupRows);
+        p.b = c.take<float>(kGroupRows);
+        w.gprep.push_back(p);
+    }
+    for (int j = 0; j < nt; ++j) w.qlab.push_back(c.take<uint8_t>((size_t)n_max));
+    w.flcount = c.take<unsigned>((size_t)kMaxSeg * 64);
+    for (int s = 0; s < kMaxSeg; ++s) {
+        FlagList &f = w.fl[s];
+        f.count = w.flcount ? w.flcount + 64 * s : nullptr;
+        f.stats = w.flcount ? reinterpret_cast<unsigned long long *>(f.count + 16) : nullptr;
+        f.pix = c.take<unsigned>((size_t)n_max);
+        f.mask = c.take<unsigned>((size_t)n_max * kMaskWords);
+    }
+    w.fit = carve_fit(c, l_max, D, k_max);
+    // the largest integral-image layout over the templates (its size depends on the template)
+    size_t sbytes = 0;
+    for (int j = 0; j < nt; ++j) {
+        WsCursor z{nullptr, 0};
+        carve_score(z, H_max, W_max, k_max, t[j].h, t[j].w);
+        sbytes = std::max(sbytes, z.off);
+    }
+    w.score_base = c.take<char>(sbytes);
+    w.heat_scratch = c.take<float>((size_t)hw_max);
+    return w;
+}
+
+// Grid bank of a th x tw template: the full window, then the cells r * G + c.
+void grid_bank(int th, int tw, int G, std::vector<vqnnf_rect> &rects, std::vector<vqnnf_filter> &bank)
+{
+    rects.clear();
+    bank.clear();
+    rects.push_back(vqnnf_rect{0, 0, tw, th, 1});
+    for (int r = 0; r < G; ++r)
+        for (int c = 0; c < G; ++c) {
+            vqnnf_rect rc;
+            rc.x0 = c * tw / G;
+            rc.x1 = (c + 1) * tw / G;
+            rc.y0 = r * th / G;
+            rc.y1 = (r + 1) * th / G;
+            rc.weight = 1;
+            rects.push_back(rc);
+        }
+    for (size_t f = 0; f < rects.size(); ++f) {
+        vqnnf_filter fl;
+        fl.n_rects = 1;
+        fl.rects = nullptr;                     // set below, once rects no longer moves
+        fl.w_f = 1.0f;
+        fl.area = (float)((rects[f].x1 - rects[f].x0) * (rects[f].y1 - rects[f].y0));
+        bank.push_back(fl);
+    }
+    for (size_t f = 0; f < rects.size(); ++f) bank[f].rects = &rects[f];
+}
+
+// First-fit packing of the codebooks (padded to 32 columns) into groups of at most
+// group_cols columns and kMaxSeg codebooks; a codebook wider than group_cols is a group of
+// its own.
+std::vector<Group> make_groups(const vqnnf_batch_template *t, int nt, int group_cols)
+{
+    std::vector<Group> gs;
+    for (int j = 0; j < nt; ++j) {
+        const int nc = (t[j].k + 31) / 32 * 32;
+        size_t g = 0;
+        while (g < gs.size() && (gs[g].nseg == kMaxSeg || gs[g].npad + nc > std::max(group_cols, nc))) ++g;
+        if (g == gs.size()) gs.push_back(Group{});
+        Group &G = gs[g];
+        G.tj[G.nseg++] = j;
+        G.npad += nc;
+    }
+    return gs;
+}
+
+vqnnf_status check_batch(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D, int G)
+{
+    if (!q || !t || nq < 1 || nt < 1 || D < 1) return VQNNF_EINVAL;
+    if (G < 1 || G > 4 || D % 16 != 0) return VQNNF_EUNSUPPORTED;
+    if ((long long)nq * nt > 65536) return VQNNF_EUNSUPPORTED;
+    for (int i = 0; i < nq; ++i) {
+        if (!q[i].X || q[i].H < 1 || q[i].W < 1 || !aligned(q[i].X, 16)) return VQNNF_EINVAL;
+        if ((long long)q[i].H * q[i].W >= (1ll << 31) || (long long)(q[i].H + 1) * (q[i].W + 1) >= (1ll << 31))
+            return VQNNF_EUNSUPPORTED;
+    }
+    for (int j = 0; j < nt; ++j) {
+        if (!t[j].T || t[j].h < 1 || t[j].w < 1 || t[j].k < 1 || !aligned(t[j].T, 16)) return VQNNF_EINVAL;
+        if ((long long)t[j].k > (long long)t[j].h * t[j].w || t[j].h < G || t[j].w < G) return VQNNF_EINVAL;
+        if (t[j].k > kMaxK) return VQNNF_EUNSUPPORTED;
+        for (int i = 0; i < nq; ++i)
+            if (t[j].h > q[i].H || t[j].w > q[i].W) return VQNNF_EINVAL;
+    }
+    return VQNNF_OK;
+}
+
+vqnnf_status check_plan(const vqnnf_batch_plan &p)
+{
+    if (p.group_cols != 128 && p.group_cols != 256) return VQNNF_EINVAL;
+    if (p.sf != 0 && (p.sf < 2 || p.sf > 8 || p.sf % 2)) return VQNNF_EINVAL;
+    if (p.pf < -1 || p.pf > 64) return VQNNF_EINVAL;
+    return VQNNF_OK;
+}
+
+const vqnnf_batch_plan kDefaultPlan = {256, 0, -1, 0};
+
+struct Banks {
+    std::vector<BankSpec> bs;
+    std::vector<GridSpec> gs;
+};
+
+vqnnf_status compile_banks(const vqnnf_batch_template *t, int nt, int G, Banks &b)
+{
+    b.bs.resize(nt);
+    b.gs.resize(nt);
+    std::vector<vqnnf_rect> rects;
+    std::vector<vqnnf_filter> bank;
+    const int optin = device_smem_optin();
+    for (int j = 0; j < nt; ++j) {
+        grid_bank(t[j].h, t[j].w, G, rects, bank);
+        vqnnf_status st = compile_bank(bank.data(), (int)bank.size(), t[j].h, t[j].w, b.bs[j], b.gs[j]);
+        if (st != VQNNF_OK) return st;
+        const bool u16 = sat_is_u16(t[j].h, t[j].w);
+        if (score_smem_bytes_for(u16 ? 2 : 4, b.bs[j], b.gs[j], t[j].k) > (size_t)optin) return VQNNF_EUNSUPPORTED;
+    }
+    return VQNNF_OK;
+}
+
+// Template side: codebook, NNF and filter responses of every template.
+vqnnf_status fit_templates(const vqnnf_batch_template *t, int nt, int D, int iters, uint64_t seed, const Banks &b,
+                           BatchWs &w, cudaStream_t s)
+{
+    for (int j = 0; j < nt; ++j) {
+        const long long l = (long long)t[j].h * t[j].w;
+        vqnnf_status st = run_fit(t[j].T, l, D, t[j].k, iters, seed + (uint64_t)j, VQNNF_PREC_BF16, w.C[j], w.fit, s);
+        if (st != VQNNF_OK) return st;
+        st = run_assign(t[j].T, l, D, w.C[j], t[j].k, VQNNF_PREC_BF16, w.tlab[j], nullptr, w.fit.as, s);
+        if (st != VQNNF_OK) return st;
+        cudaError_t e = launch_filter_responses(w.tlab[j], t[j].h, t[j].w, t[j].k, b.bs[j], w.tcnt[j], s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return VQNNF_OK;
+}
+
+// Group codebooks and their prepared BF16 planes.
+vqnnf_status build_groups(const std::vector<Group> &groups, const vqnnf_batch_template *t, int D, BatchWs &w,
+                          cudaStream_t s)
+{
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const Group &G = groups[g];
+        GroupSrc src;
+        memset(&src, 0, sizeof(src));
+        src.nseg = G.nseg;
+        int col = 0;
+        for (int q = 0; q < G.nseg; ++q) {
+            const int j = G.tj[q];
+            src.col0[q] = col;
+            src.ncol[q] = (t[j].k + 31) / 32 * 32;
+            src.k[q] = t[j].k;
+            src.C[q] = w.C[j];
+            col += src.ncol[q];
+        }
+        group_codebook_kernel<<<G.npad, 128, 0, s>>>(src, D, w.gC[g]);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_prep_codebook(w.gC[g], G.npad, D, VQNNF_PREC_BF16, w.gprep[g], s);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return VQNNF_OK;
+}
+
+// NNF of query i under every template's codebook: one contraction per group, then the
+// re-scoring of each codebook's flagged pixels.
+vqnnf_status assign_query(const vqnnf_image &qi, const std::vector<Group> &groups, const vqnnf_batch_template *t,
+                          int D, const vqnnf_batch_plan &plan, BatchWs &w, cudaStream_t s)
+{
+    const long long n = (long long)qi.H * qi.W;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const Group &G = groups[g];
+        cudaError_t e = cudaMemsetAsync(w.flcount, 0, sizeof(unsigned) * 64 * kMaxSeg, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        TcSeg seg[kMaxSeg];
+        int col = 0;
+        for (int q = 0; q < G.nseg; ++q) {
+            const int j = G.tj[q];
+            seg[q].col0 = col;
+            seg[q].ncol = (t[j].k + 31) / 32 * 32;
+            seg[q].k = t[j].k;
+            seg[q].labels = w.qlab[j];
+            seg[q].fl = w.fl[q];
+            col += seg[q].ncol;
+        }
+        e = launch_assign_bf16_seg(qi.X, n, D, w.gprep[g], G.npad, seg, G.nseg, plan.sf, plan.pf, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        for (int q = 0; q < G.nseg; ++q) {
+            const int j = G.tj[q];
+            e = launch_rescore(qi.X, n, D, w.C[j], t[j].k, w.qlab[j], w.fl[q], s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    return VQNNF_OK;
+}
+
+size_t batch_bytes(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D, int G)
+{
+    WsCursor c{nullptr, 0};
+    carve_batch(c, q, nq, t, nt, D, G);
+    return (c.off + 255) & ~size_t(255);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t vqnnf_batch_workspace_bytes(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                                   int G)
+{
+    if (check_batch(q, nq, t, nt, D, G) != VQNNF_OK) return 0;
+    return batch_bytes(q, nq, t, nt, D, G);
+}
+
+vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                               int iters, uint64_t seed, int G, const vqnnf_batch_plan *plan,
+                               float *const *heat, int32_t *argmax_yx, void *ws, size_t ws_bytes, void *stream)
+{
+    vqnnf_status st = check_batch(q, nq, t, nt, D, G);
+    if (st != VQNNF_OK) return st;
+    if (!argmax_yx || !ws || iters < 0 || !aligned(ws, 256)) return VQNNF_EINVAL;
+    const vqnnf_batch_plan p = plan ? *plan : kDefaultPlan;
+    if ((st = check_plan(p)) != VQNNF_OK) return st;
+    if (heat)
+        for (int e = 0; e < nq * nt; ++e)
+            if (!heat[e]) return VQNNF_EINVAL;
+    if (ws_bytes < batch_bytes(q, nq, t, nt, D, G)) return VQNNF_ENOMEM;
+    Banks banks;
+    if ((st = compile_banks(t, nt, G, banks)) != VQNNF_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    WsCursor c{static_cast<char *>(ws), 0};
+    BatchWs w = carve_batch(c, q, nq, t, nt, D, G);
+    if ((st = fit_templates(t, nt, D, iters, seed, banks, w, s)) != VQNNF_OK) return st;
+    const std::vector<Group> groups = make_groups(t, nt, p.group_cols);
+    if ((st = build_groups(groups, t, D, w, s)) != VQNNF_OK) return st;
+    WGridSpec no_wgrid;
+    memset(&no_wgrid, 0, sizeof(no_wgrid));
+    for (int i = 0; i < nq; ++i) {
+        if ((st = assign_query(q[i], groups, t, D, p, w, s)) != VQNNF_OK) return st;
+        for (int j = 0; j < nt; ++j) {
+            WsCursor sc{w.score_base, 0};
+            ScoreWs sw = carve_score(sc, q[i].H, q[i].W, t[j].k, t[j].h, t[j].w);
+            cudaError_t e = launch_sat(w.qlab[j], q[i].H, q[i].W, t[j].k, sw.u16, sw.carry, sw.bandsum, sw.S, s);
+            if (e != cudaSuccess) return from_cuda(e);
+            const int HO = q[i].H - t[j].h + 1, WO = q[i].W - t[j].w + 1;
+            float *hp = heat ? heat[(size_t)i * nt + j] : w.heat_scratch;
+            e = launch_score(sw.S, sw.u16, q[i].W, t[j].k, HO, WO, banks.bs[j], banks.gs[j], no_wgrid, w.tcnt[j], hp,
+                             sw.amax, argmax_yx + 2 * ((size_t)i * nt + j), s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    return VQNNF_OK;
+}
+
+vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
+                              int iters, uint64_t seed, int G, vqnnf_batch_plan *plan, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    vqnnf_status st = check_batch(q, nq, t, nt, D, G);
+    if (st != VQNNF_OK) return st;
+    if (!plan || !ws || iters < 0 || !aligned(ws, 256)) return VQNNF_EINVAL;
+    if (ws_bytes < batch_bytes(q, nq, t, nt, D, G)) return VQNNF_ENOMEM;
+    Banks banks;
+    if ((st = compile_banks(t, nt, G, banks)) != VQNNF_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    WsCursor c{static_cast<char *>(ws), 0};
+    BatchWs w = carve_batch(c, q, nq, t, nt, D, G);
+    if ((st = fit_templates(t, nt, D, iters, seed, banks, w, s)) != VQNNF_OK) return st;
+    int ib = 0;
+    for (int i = 1; i < nq; ++i)
+        if ((long long)q[i].H * q[i].W > (long long)q[ib].H * q[ib].W) ib = i;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return VQNNF_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return VQNNF_ECUDA;
+    }
+    float best = 0.f;
+    vqnnf_batch_plan best_plan = kDefaultPlan;
+    // time one candidate: assignment of the largest query, second of two runs
+    auto time_plan = [&](const vqnnf_batch_plan &cand, float &ms) -> vqnnf_status {
+        const std::vector<Group> groups = make_groups(t, nt, cand.group_cols);
+        vqnnf_status r = build_groups(groups, t, D, w, s);
+        for (int rep = 0; rep < 2 && r == VQNNF_OK; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return VQNNF_ECUDA;
+            if ((r = assign_query(q[ib], groups, t, D, cand, w, s)) != VQNNF_OK) return r;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return VQNNF_ECUDA;
+        }
+        return r;
+    };
+    for (int gc : {128, 256}) {
+        for (int sf : {4, 6, 8}) {
+            for (int pf : {0, 8}) {
+                const vqnnf_batch_plan cand = {gc, sf, pf, 0};
+                float ms = 0.f;
+                st = time_plan(cand, ms);
+                if (st == VQNNF_EUNSUPPORTED) {               // this split does not fit shared memory
+                    st = VQNNF_OK;
+                    continue;
+                }
+                if (st != VQNNF_OK) break;
+                if (best == 0.f || ms < best) { best = ms; best_plan = cand; }
+            }
+            if (st != VQNNF_OK) break;
+        }
+        if (st != VQNNF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != VQNNF_OK) return st;
+    *plan = best_plan;
+    return VQNNF_OK;
+}
+
+}  // extern "C"

@@ -32,6 +32,16 @@ struct FlagList {
     unsigned long long *stats;  // [n_flagged, n_candidates, n_deep, reserved]
 };
 
+// One codebook among several side by side in the columns of one tensor-core contraction:
+// columns [col0, col0 + ncol) of the prepared codebook, ncol a multiple of 32, the first k of
+// them real centroids; its labels and its flag list (candidate masks relative to col0).
+constexpr int kMaxSeg = 8;
+struct TcSeg {
+    int col0, ncol, k;
+    uint8_t *labels;
+    FlagList fl;
+};
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
                                  cudaStream_t s);
@@ -41,6 +51,10 @@ cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k,
 cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k,
                                const CodebookPrep &p, uint8_t *labels, FlagList fl,
                                cudaStream_t s);
+// Several codebooks in one contraction: p holds krows prepared rows (the segments' columns,
+// padding rows included); the sum of the segments' ncol is at most 256.
+cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const CodebookPrep &p, int krows,
+                                   const TcSeg *seg, int nseg, int sf, int pf, cudaStream_t s);
 cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
                            uint8_t *labels, FlagList fl, cudaStream_t s);
 cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s);

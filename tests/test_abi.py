@@ -132,3 +132,40 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def _batch_arrays(qshapes, tshapes):
+    from paper_2306_15010_gb300 import _lib
+    qa = (_lib.VqnnfImage * len(qshapes))(*[_lib.VqnnfImage(FAKE, H, W) for H, W in qshapes])
+    ta = (_lib.VqnnfBatchTemplate * len(tshapes))(*[_lib.VqnnfBatchTemplate(FAKE, h, w, k) for h, w, k in tshapes])
+    return qa, ta
+
+
+def test_batch_workspace_and_refusals(lib):
+    """Batched matching: workspace sizes and the host-side checks (no kernel is launched)."""
+    from paper_2306_15010_gb300 import _lib
+    qa, ta = _batch_arrays([(512, 700), (300, 256)], [(16, 20, 8), (64, 64, 256), (40, 33, 100)])
+    nb = lib.vqnnf_batch_workspace_bytes(qa, 2, ta, 3, 256, 3)
+    # at least: the NNF of the largest query under every codebook, flag lists of eight codebooks,
+    # one 16-bit integral image of the largest pair
+    assert nb % 256 == 0 and nb > 3 * 512 * 700 + 8 * 512 * 700 * 36 + 513 * 256 * 700 * 2
+    for q, t, D, G in [([(512, 700)], [(16, 20, 8), (600, 20, 8)], 256, 3),    # template taller than a query
+                       ([(512, 700)], [(16, 20, 321)], 256, 3),                 # k > h w
+                       ([(512, 700)], [(16, 20, 8)], 250, 3),                   # D % 16
+                       ([(512, 700)], [(16, 20, 8)], 256, 5),                   # G > 4
+                       ([(512, 700)], [(3, 20, 8)], 256, 4),                    # cells thinner than G
+                       ([(512, 700)], [(64, 64, 257)], 256, 3)]:               # k > 256
+        qa, ta = _batch_arrays(q, t)
+        assert lib.vqnnf_batch_workspace_bytes(qa, len(q), ta, len(t), D, G) == 0
+    qa, ta = _batch_arrays([(512, 700)], [(16, 20, 8)])
+    plan = _lib.VqnnfBatchPlan(256, 0, -1, 0)
+    call = lambda **kw: lib.vqnnf_match_batch(
+        qa, 1, ta, 1, 256, 3, ctypes.c_uint64(1), kw.get("G", 3), ctypes.byref(kw.get("plan", plan)), None,
+        kw.get("am", FAKE), kw.get("ws", FAKE), kw.get("wsb", 1 << 40), None)
+    assert call(am=None) == _lib.EINVAL
+    assert call(ws=None) == _lib.EINVAL
+    assert call(wsb=1024) == _lib.ENOMEM
+    assert call(G=0) == _lib.EUNSUPPORTED
+    assert call(plan=_lib.VqnnfBatchPlan(64, 0, -1, 0)) == _lib.EINVAL
+    assert call(plan=_lib.VqnnfBatchPlan(256, 3, -1, 0)) == _lib.EINVAL
+    assert lib.vqnnf_batch_tune(qa, 1, ta, 1, 256, 3, ctypes.c_uint64(1), 3, None, FAKE, 1 << 40, None) == _lib.EINVAL
