@@ -108,14 +108,15 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
 // every partial sum of the in-order FP64 evaluation fits in 53 significant bits, none of its
 // additions rounds and its result IS the exact sum.  Sufficient: the top bit of sum |x| (a
 // bound of every partial sum) and the lowest set bit over all members' values are at most 52
-// positions apart.  A (cluster, dimension) pair that fails this (or holds a value outside the
-// range) is summed in FP64 in pixel order by its lane, as before.  Both branches therefore
-// equal the in-order FP64 sum bit for bit.
+// positions apart.  A (cluster, dimension) pair that fails this, holds a value outside the
+// range, or whose sums could exceed 128 bits is summed in FP64 in pixel order by its lane.
+// Both branches therefore equal the in-order FP64 sum bit for bit.
 constexpr int UW = 16;       // warps per (cluster, 32 dimensions)
 
 struct Fixed {
     unsigned __int128 pos, neg, mag;   // sums of the positive and negative parts, of |x|
     int low;                           // lowest set bit position over the values (units 2^-80)
+    int hish;                          // largest shift: every value is below 2^(hish + 24) units
     bool bad;                          // a value outside the exact range
 };
 
@@ -133,6 +134,7 @@ __device__ __forceinline__ void fixed_add(Fixed &f, float x)
     else f.pos += X;
     f.mag += X;
     f.low = min(f.low, sh + __ffs((int)M) - 1);
+    f.hish = max(f.hish, sh);
 }
 
 __device__ __forceinline__ int top_bit(unsigned __int128 v)
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
                                                          const int *__restrict__ members, float *__restrict__ C)
 {
     __shared__ unsigned __int128 spos[UW][32], sneg[UW][32], smag[UW][32];
-    __shared__ int slow[UW][32];
+    __shared__ int slow[UW][32], shish[UW][32];
     __shared__ unsigned char sbad[UW][32];
     const int j = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
     Fixed f;
     f.pos = f.neg = f.mag = 0;
     f.low = 1 << 30;
+    f.hish = 0;
     f.bad = false;
     int q = w;
     for (; q + 7 * UW < c; q += 8 * UW) {                // eight member rows in flight per warp
@@ -172,11 +175,12 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
     sneg[w][lane] = f.neg;
     smag[w][lane] = f.mag;
     slow[w][lane] = f.low;
+    shish[w][lane] = f.hish;
     sbad[w][lane] = f.bad ? 1 : 0;
     __syncthreads();
     if (w != 0) return;
     unsigned __int128 pos = 0, neg = 0, mag = 0;
-    int low = 1 << 30;
+    int low = 1 << 30, hish = 0;
     bool bad = false;
 #pragma unroll 2
     for (int u = 0; u < UW; ++u) {
@@ -184,12 +188,19 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
         neg += sneg[u][lane];
         mag += smag[u][lane];
         low = min(low, slow[u][lane]);
+        hish = max(hish, shish[u][lane]);
         bad |= sbad[u][lane] != 0;
     }
     double s;
-    if (mag == 0) {
+    // the 128-bit sums cannot have wrapped while c values below 2^(hish + 24) units stay below
+    // 2^128: hish + 24 + ceil(log2 c) <= 127
+    const bool nowrap = hish + 24 + (32 - __clz(c)) <= 127;
+    if (bad || !nowrap) {
+        s = 0.0;                                         // outside the exact route: in-order FP64
+        for (int q2 = 0; q2 < c; ++q2) s += (double)__ldg(T + (size_t)m[q2] * D + ic);
+    } else if (mag == 0) {
         s = 0.0;                                         // only zeros: the FP64 sum is +0
-    } else if (!bad && top_bit(mag) - low <= 52) {
+    } else if (top_bit(mag) - low <= 52) {
         // exact: |sum| >> low has at most 53 significant bits
         const bool negative = neg > pos;
         const unsigned __int128 d = negative ? neg - pos : pos - neg;

@@ -121,7 +121,8 @@ def test_fit_codebook_bit_exact(vq, prec, h, w, D, k, iters):
 @pytest.mark.parametrize("prec", PRECS)
 def test_fit_codebook_exact_sum_edge_values(vq, prec):
     """Centroid sums with values the exact fixed-point route cannot take (below 2^-57,
-    spans over 52 bits, subnormals), negatives and signed zeros: still bit-identical."""
+    spans over 52 bits, subnormals, a column with no value in range, sums too large for the
+    128-bit accumulator), negatives and signed zeros: still bit-identical."""
     r = np.random.default_rng(5)
     l, D, k = 700, 64, 6
     T = r.normal(0.5, 0.3, (l, D)).astype(np.float32)
@@ -131,6 +132,9 @@ def test_fit_codebook_exact_sum_edge_values(vq, prec):
     T[r.random((l, D)) < 0.005] = np.float32(1e-30)             # below the exact range
     T[r.random((l, D)) < 0.002] = np.float32(3e-42)             # subnormal
     T[:, :8] = np.abs(T[:, :8])                                 # some all-positive columns
+    T[:, 8] = np.float32(1e-30)                                 # a column entirely below the range
+    T[:, 9] = (r.uniform(1, 2, l) * 2.0 ** 44).astype(np.float32)   # sums past 2^127 units
+    T[:, 10] = (r.uniform(-2, 2, l) * 2.0 ** 45).astype(np.float32)  # large, both signs
     T = T.reshape(35, 20, D)
     C = vq.vqnnf_fit_codebook(_dev(T), k, 4, 9, prec)
     C_ref = oracle.fit_codebook(T, k, 4, 9)
