@@ -21,10 +21,10 @@
 //       Adjacent warps take adjacent strips, so the rows they write are contiguous runs.
 //
 // Score: one block per (window row, 512 windows).  The corner rows of its windows are
-// staged in shared memory 8 clusters at a time by bulk copies (one per row segment,
-// completing on an mbarrier, double-buffered); each thread owns four windows and
+// staged in shared memory one cluster at a time by bulk copies (one per row segment,
+// completing on an mbarrier, four buffers in flight); each thread owns four windows and
 // accumulates exact integer L1 distances per filter over all clusters, then combines them
-// in float32 in bank order.
+// in float32 in a fixed filter order.
 #include <cfloat>
 
 #include "common.cuh"
