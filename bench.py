@@ -39,12 +39,12 @@ METRIC = "query Mpix/s at 2048^2, D=512, k=128: BF16 vs FP32 path, % of roofline
 OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,179,409,920 + 5,074,944 bytes),
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,196,549,000 + 5,988,608 bytes),
+# dram__bytes_write.sum), from the ncu capture summarised in
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,187,915,008 + 5,257,216 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2179409920 + 5074944) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "ab7738fdd9568ac1b645b56eaa758db9c7291b6bb7588b0792e1e42d1d0985a7"
+TC_TRAFFIC_PER_PX = (2187915008 + 5257216) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "57ad17d226cde24c61df45e28e6ccc89d65364d1586ec5f2fd572098ae947ae3"
 
 
 

@@ -249,6 +249,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b, float &ra, float
 }
 
 // ------------------------------------------------------------------ the kernel
+// MULTI: several codebook segments (batching); the single-codebook instantiation keeps the
+// segment's bounds and bound maxima out of the tile loop.
+template <bool MULTI>
 __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmBhi,
                                                           const __grid_constant__ CUtensorMap tmBlo,
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const float u = (float)kU;
         const float u4 = 4.0f * u;
         const float infl = 1.0f + 0.00390625f;
-        const int nseg = g.nseg;
+        const int nseg = MULTI ? g.nseg : 1;
         // per segment the largest ||c_j*||^2, a_j, v_j and b_j over its centroids (lane q of the
         // first epilogue warp scans segment q): Bmax below bounds every B_j of a pixel within
         // the segment
@@ -512,6 +515,11 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             segmx[lane] = make_float4(nm, am, vm, bm);
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");       // the four epilogue warps
+        // one codebook: its bound maxima and output pointers are loop invariants
+        const float4 mx0 = segmx[0];
+        const float cnorm0 = sqrtf(mx0.x) * 1.0001f, nrm0 = mx0.x * 1.0001f;
+        uint8_t *const labels0 = g.seg[0].labels;
+        const FlagList fl0 = g.seg[0].fl;
         uint32_t tl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
@@ -533,10 +541,11 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             const long long pix = tile * TM + r;
             const bool valid = pix < g.n;
             for (int sgi = 0; sgi < nseg; ++sgi) {
-                const int cb = segt[sgi].col0, ce = cb + segt[sgi].ncol;
-                const float4 mx = segmx[sgi];
-                const float cnorm_max = sqrtf(mx.x) * 1.0001f;    // max ||c_j*|| (cn = ||c*||^2 in FP32)
-                const float nrm_max = mx.x * 1.0001f;
+                const int cb = MULTI ? segt[sgi].col0 : 0, ce = MULTI ? cb + segt[sgi].ncol : npad;
+                const float4 mx = MULTI ? segmx[sgi] : mx0;
+                // max ||c_j*|| (cn = ||c*||^2 in FP32) and max ||c_j*||^2, with margins
+                const float cnorm_max = MULTI ? sqrtf(mx.x) * 1.0001f : cnorm0;
+                const float nrm_max = MULTI ? mx.x * 1.0001f : nrm0;
                 // pass 1: smallest score of the segment, lowest column on ties, as four
                 // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
                 float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
@@ -597,23 +606,24 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                     tc_fence_before();
                     mbar_arrive(&acc_empty[buf]);
                 }
-                const TcSeg &sq = segt[sgi];
+                uint8_t *const labels = MULTI ? segt[sgi].labels : labels0;
+                const FlagList fl = MULTI ? segt[sgi].fl : fl0;
                 const int lab = (cnt == 1 ? last : amin) - cb;
-                if (valid) sq.labels[pix] = (uint8_t)lab;
+                if (valid) labels[pix] = (uint8_t)lab;
                 const bool flagged = valid && cnt > 1;
                 const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
                 if (ballot) {
                     const int leader = __ffs(ballot) - 1;
                     unsigned basei = 0;
-                    if (lane == leader) basei = atomicAdd(sq.fl.count, (unsigned)__popc(ballot));
+                    if (lane == leader) basei = atomicAdd(fl.count, (unsigned)__popc(ballot));
                     basei = __shfl_sync(0xffffffffu, basei, leader);
                     if (flagged) {
                         const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
                         if (slot < (unsigned long long)g.n) {
-                            sq.fl.pix[slot] = (unsigned)pix;
+                            fl.pix[slot] = (unsigned)pix;
 #pragma unroll
                             for (int w = 0; w < kMaskWords; ++w)
-                                sq.fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                                fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
                         }
                     }
                 }
@@ -738,10 +748,16 @@ cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const Cod
     a.p = p;
     a.nseg = nseg;
     for (int q = 0; q < nseg; ++q) a.seg[q] = seg[q];
-    e = cudaFuncSetAttribute(assign_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const long long grid = a.ntiles < sms ? a.ntiles : sms;
-    assign_tc_kernel<<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+    if (nseg == 1) {
+        e = cudaFuncSetAttribute(assign_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        assign_tc_kernel<false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+    } else {
+        e = cudaFuncSetAttribute(assign_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        assign_tc_kernel<true><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+    }
     return cudaGetLastError();
 }
 
