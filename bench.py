@@ -334,7 +334,7 @@ def run_gpu(args, rank, world):
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=am)
     paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
     soft_vq = None if args.no_soft else run_soft(vq, dev)
-    batch = None if args.no_batch else run_batch(vq, dev)
+    batch = None if args.no_batch else run_batch(vq, dev, eager=args.batch_eager)
 
     if rank != 0:
         return None
@@ -492,7 +492,7 @@ def run_soft(vq, dev, reps=3):
             "note": "backward includes the autograd engine's elementwise product and sum of the loss"}
 
 
-def run_batch(vq, dev, reps=2):
+def run_batch(vq, dev, reps=2, eager=False):
     """Batching: 64 templates (sides ~U{16..192} per axis, k ~U{8, 16, 32, 64, 128, 256}, warped
     crops as in the headline workload) against 16 queries (sides ~U{512..2048} per axis), D = 256,
     FP32 features, BF16 contraction; one vqnnf_match_batch call (every template's codebook,
@@ -522,17 +522,22 @@ def run_batch(vq, dev, reps=2):
     with torch.cuda.stream(s):
         vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
     torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        with torch.cuda.graph(g, stream=s):
-            vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
-        g.replay()
-    torch.cuda.synchronize()
+    g = None
+    if not eager:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
+            g.replay()
+        torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     with torch.cuda.stream(s):
         for _ in range(reps):
-            g.replay()
+            if g is not None:
+                g.replay()
+            else:
+                vq.vqnnf_match_batch(Xs, Ts, ks, iters, 6500, G, plan, heat=heats, argmax_yx=am, ws=ws, stream=s)
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -545,7 +550,8 @@ def run_batch(vq, dev, reps=2):
            "pair_mpix_per_s": round(px * nt / (ms * 1e-3) / 1e6, 1),
            "plan": {"group_cols": plan.group_cols, "sf": plan.sf, "pf": plan.pf},
            "codebook_columns": cols, "query_px": px,
-           "execution": "one vqnnf_match_batch call per batch, CUDA graph replay"}
+           "execution": "one vqnnf_match_batch call per batch, " +
+                        ("enqueued directly" if eager else "CUDA graph replay")}
     del g, heats, ws
     torch.cuda.empty_cache()
     return out
@@ -719,6 +725,9 @@ def main():
                     help="query side (profiling captures on a smaller case)")
     ap.add_argument("--no-soft", action="store_true", help="skip the soft-VQ training-path timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-templates timing")
+    ap.add_argument("--batch-eager", action="store_true",
+                    help="time the batch call enqueued directly instead of replayed from a CUDA graph "
+                         "(for profilers that do not follow the replay of a large graph)")
     ap.add_argument("--no-paper-bank", action="store_true",
                     help="skip scoring with the paper's own filter bank")
     ap.add_argument("--no-compare", action="store_true",
