@@ -557,13 +557,11 @@ def run_batch(vq, dev, reps=2, eager=False):
     return out
 
 
-def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None, bands=8):
-    """End to end through the public API with host buffers: pinned features in, heatmap and
-    maximum out, every step.  The host link (~210 GB/s here) bounds it, so the compute is
-    overlapped with the copy: the template goes first and its side (codebook, NNF, responses)
-    runs on a second stream while the query's features arrive in row bands; each band is
-    assigned (vqnnf_assign on the band) as soon as it has landed; the integral image and the
-    score follow the last band."""
+def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
+    """End to end through the C ABI with host buffers: vqnnf_match_host takes the pinned host
+    feature maps and writes the host heatmap and maximum, every step.  The host link (~210 GB/s
+    here) bounds it; inside the call the template goes first and its side runs on a second
+    stream while the query arrives in row bands, each assigned as soon as it has landed."""
     import torch
     try:
         hX = torch.empty(X.shape, dtype=X.dtype, pin_memory=True)
@@ -574,47 +572,17 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None, bands=8):
         ham = torch.empty(2, dtype=torch.int32, pin_memory=True)
     except Exception as exc:  # pragma: no cover
         return {"value": None, "unit": "Mpix/s", "error": str(exc)}
-    H = cfg["H"]
     c = cfg
-    rows = [(H * b // bands, H * (b + 1) // bands) for b in range(bands)]
-    s_tpl = torch.cuda.Stream(device=dev)     # template side
-    s_q = torch.cuda.Stream(device=dev)       # query side
-    ev_T = torch.cuda.Event()
-    ev_start = torch.cuda.Event(enable_timing=True)
-    ev_C = torch.cuda.Event(enable_timing=True)
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in rows]
-    ev_done = torch.cuda.Event(enable_timing=True)
-    ev_done.record(s)
+    H, W, D = X.shape
+    ws = vq.Workspace(vq.vqnnf_match_host_workspace_bytes(H, W, D, c["k"], c["th"], c["tw"], pipe.bank.F,
+                                                          pipe.prec), dev)
+    s2 = torch.cuda.Stream(device=dev)
 
     def one_step():
-        s.wait_event(ev_done)                 # the previous step has released every buffer
-        s_tpl.wait_event(ev_done)
-        with torch.cuda.stream(s):
-            ev_start.record(s)
-            pipe.T.copy_(hT, non_blocking=True)
-            ev_T.record(s)
-            for b, (y0, y1) in enumerate(rows):
-                pipe.X[y0:y1].copy_(hX[y0:y1], non_blocking=True)
-                ev_b[b].record(s)
-        s_tpl.wait_event(ev_T)
-        vq.vqnnf_fit_codebook(pipe.T, c["k"], c["iters"], c["fit_seed"], pipe.prec, C=pipe.C,
-                              ws=pipe.ws_fit, stream=s_tpl)
-        vq.vqnnf_assign(pipe.T, pipe.C, pipe.prec, labels=pipe.tl, ws=pipe.ws_a, stream=s_tpl)
-        vq.vqnnf_filter_responses(pipe.tl, c["k"], pipe.bank, counts=pipe.tc, stream=s_tpl)
-        ev_C.record(s_tpl)
-        s_q.wait_event(ev_C)
-        for b, (y0, y1) in enumerate(rows):
-            s_q.wait_event(ev_b[b])
-            vq.vqnnf_assign(pipe.X[y0:y1], pipe.C, pipe.prec, labels=pipe.ql[y0:y1], ws=pipe.ws_a,
-                            stream=s_q)
-        vq.vqnnf_score(pipe.ql, c["k"], c["th"], c["tw"], pipe.bank, pipe.tc, heatmap=pipe.heat,
-                       argmax_yx=pipe.am, ws=pipe.ws_s, stream=s_q)
-        with torch.cuda.stream(s_q):
-            hheat.copy_(pipe.heat, non_blocking=True)
-            ham.copy_(pipe.am, non_blocking=True)
-        ev_done.record(s_q)
+        vq.vqnnf_match_host(hX, hT, c["k"], c["iters"], c["fit_seed"], pipe.bank, pipe.prec, heatmap=hheat,
+                            argmax_yx=ham, ws=ws, stream=s, stream2=s2)
 
-    one_step()                                # warm-up (stream and event set-up)
+    one_step()                                # warm-up
     torch.cuda.synchronize()
     # the floor: the step's host-to-device bytes alone, one copy
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -629,20 +597,17 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None, bands=8):
     t0 = time.perf_counter()
     for _ in range(n):
         one_step()
-    torch.cuda.synchronize()
+    s.synchronize()
     dt = (time.perf_counter() - t0) / n
-    L = cfg["H"] * cfg["W"]
-    # device timeline of the last step, from its start
-    timeline = {"template_side_done": round(ev_start.elapsed_time(ev_C), 2),
-                "last_band_copied": round(ev_start.elapsed_time(ev_b[-1]), 2),
-                "step_done": round(ev_start.elapsed_time(ev_done), 2)}
-    return {"value": round(L / dt / 1e6, 3), "unit": "Mpix/s",
-            "h2d_bytes_per_step": hX.numel() * 4 + hT.numel() * 4,
-            "d2h_bytes_per_step": hheat.numel() * 4 + 8, "steps": n, "ms_per_step": round(dt * 1e3, 2),
-            "h2d_copy_ms": round(copy_ms, 2),
-            "overlap": f"template side on a second stream, query copied and assigned in {bands} row bands",
-            "timeline_ms": timeline,
-            "argmax_matches_device_run": None if am_ref is None else ham.tolist() == list(am_ref)}
+    L = H * W
+    out = {"value": round(L / dt / 1e6, 3), "unit": "Mpix/s",
+           "h2d_bytes_per_step": hX.numel() * 4 + hT.numel() * 4,
+           "d2h_bytes_per_step": hheat.numel() * 4 + 8, "steps": n, "ms_per_step": round(dt * 1e3, 2),
+           "h2d_copy_ms": round(copy_ms, 2),
+           "call": "vqnnf_match_host (C ABI, pinned host buffers in and out, two streams)",
+           "argmax_matches_device_run": None if am_ref is None else ham.tolist() == list(am_ref)}
+    del ws
+    return out
 
 
 def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1):

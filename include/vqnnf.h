@@ -235,6 +235,30 @@ vqnnf_status vqnnf_last_device_error(void *stream);
 /* ABI version of this header (major * 100 + minor). */
 int vqnnf_version(void);
 
+/* ---------------------------------------------------------------- whole path, host buffers
+ * One template-query pair end to end with the features in host memory: the template's
+ * codebook (vqnnf_fit_codebook with `iters`, `seed`), both NNFs, the template's responses,
+ * the query's integral image, Eq. 2 heatmap and maximum; results copied back to the host.
+ * The copies overlap the compute: the template goes first and its side runs while the query
+ * arrives in row bands, each assigned as soon as it has landed.
+ *   X_host      host, H x W x D float32 (HWC); pinned memory lets the copies run asynchronously
+ *   T_host      host, th x tw x D float32
+ *   bank, F     host filter bank, as for vqnnf_score
+ *   heat_host   host, (H - th + 1) x (W - tw + 1) float32, written; NULL = maximum only
+ *   argmax_host host, 2 int32 (y, x), written
+ *   ws          device workspace of vqnnf_match_host_workspace_bytes(...) bytes, 256-byte
+ *               aligned: it holds the device copies of X and T and every intermediate
+ *   stream      the copies run on it, and it is the stream to synchronise on: when it reaches
+ *               the end of this call's work, the host results are written
+ *   stream2     a second stream for the compute, or NULL (everything on `stream`, no overlap)
+ * Enqueues only; the events it uses are created and released inside the call, so the call is
+ * not graph-capturable.  Errors as for the calls it is made of. */
+size_t vqnnf_match_host_workspace_bytes(int H, int W, int D, int k, int th, int tw, int F, vqnnf_prec prec);
+vqnnf_status vqnnf_match_host(const float *X_host, int H, int W, int D, const float *T_host, int th, int tw,
+                              int k, int iters, uint64_t seed, vqnnf_prec prec, const vqnnf_filter *bank, int F,
+                              float *heat_host, int32_t *argmax_host, void *ws, size_t ws_bytes, void *stream,
+                              void *stream2);
+
 /* ---------------------------------------------------------------- batched matching
  * Many templates against many queries: the template side of the method (codebook, NNF and
  * filter responses, Sec. 3.1-3.2) is computed once per template and reused for every query,

@@ -11,6 +11,8 @@ from .api import (  # noqa: F401
     vqnnf_fit_codebook,
     vqnnf_filter_responses,
     vqnnf_last_device_error,
+    vqnnf_match_host,
+    vqnnf_match_host_workspace_bytes,
     vqnnf_score,
     vqnnf_set_kernel_events,
     vqnnf_version,

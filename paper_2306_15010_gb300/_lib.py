@@ -35,6 +35,9 @@ SIGNATURES = {
     "vqnnf_soft_backward": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _vp, _i, ctypes.c_float, _i, _vp, _vp,
                                  _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "vqnnf_version": (_i, []),
+    "vqnnf_match_host_workspace_bytes": (_sz, [_i, _i, _i, _i, _i, _i, _i, _i]),
+    "vqnnf_match_host": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _i, ctypes.c_uint64, _i, _vp, _i, _vp, _vp, _vp,
+                              _sz, _vp, _vp]),
     "vqnnf_batch_workspace_bytes": (_sz, [_vp, _i, _vp, _i, _i, _i]),
     "vqnnf_match_batch": (_i, [_vp, _i, _vp, _i, _i, _i, ctypes.c_uint64, _i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "vqnnf_batch_tune": (_i, [_vp, _i, _vp, _i, _i, _i, ctypes.c_uint64, _i, _vp, _vp, _sz, _vp]),

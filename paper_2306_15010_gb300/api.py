@@ -241,6 +241,52 @@ def vqnnf_score(q_labels: torch.Tensor, k: int, th: int, tw: int, bank, t_counts
     return heatmap, argmax_yx
 
 
+def _need_host(t: torch.Tensor, name: str, dtype: torch.dtype) -> None:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def vqnnf_match_host_workspace_bytes(H: int, W: int, D: int, k: int, th: int, tw: int, F: int, prec="bf16") -> int:
+    return int(_lib.load().vqnnf_match_host_workspace_bytes(H, W, D, k, th, tw, F, _prec(prec)))
+
+
+def vqnnf_match_host(X: torch.Tensor, T: torch.Tensor, k: int, iters: int, seed: int, bank, prec="bf16", *,
+                     heatmap: torch.Tensor | bool = True, argmax_yx: torch.Tensor | None = None,
+                     ws: Workspace | None = None, stream=None, stream2=None):
+    """The whole path for one pair with host feature maps (H x W x D and th x tw x D float32 CPU
+    tensors, pinned for asynchronous copies): the host heatmap (or None with heatmap=False) and
+    the host int32 (y, x) of its maximum, valid once ``stream`` reaches the end of the call's
+    work.  ``stream2``: the compute stream (copies and compute overlap), or None."""
+    _need_host(X, "X", torch.float32)
+    _need_host(T, "T", torch.float32)
+    H, W, D = X.shape
+    th, tw = T.shape[:2]
+    b = Bank.of(bank)
+    p = _prec(prec)
+    if heatmap is True:
+        heatmap = torch.empty((H - th + 1, W - tw + 1), dtype=torch.float32, pin_memory=True)
+    if heatmap is not False:
+        _need_host(heatmap, "heatmap", torch.float32)
+    if argmax_yx is None:
+        argmax_yx = torch.empty(2, dtype=torch.int32, pin_memory=True)
+    _need_host(argmax_yx, "argmax_yx", torch.int32)
+    nb = int(_lib.load().vqnnf_match_host_workspace_bytes(H, W, D, k, th, tw, b.F, p))
+    if nb == 0:
+        raise _lib.VqnnfError("vqnnf_match_host", _lib.EUNSUPPORTED, "unsupported shape")
+    ws = Workspace.ensure(ws, nb, None)
+    st = _lib.load().vqnnf_match_host(X.data_ptr(), H, W, D, T.data_ptr(), th, tw, k, iters,
+                                      ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), p, b.ptr, b.F,
+                                      heatmap.data_ptr() if heatmap is not False else None,
+                                      argmax_yx.data_ptr(), ws.ptr, ws.nbytes, _stream(stream),
+                                      None if stream2 is None else int(stream2.cuda_stream))
+    _lib.check("vqnnf_match_host", st)
+    return (heatmap if heatmap is not False else None), argmax_yx
+
+
 def vqnnf_set_kernel_events(op: int, start=None, stop=None) -> None:
     """Profiling aid: record the torch.cuda.Event pair (start, stop) immediately around the main
     kernel of every later call of ``op`` (OP_ASSIGN: the distance contraction; OP_SCORE: the

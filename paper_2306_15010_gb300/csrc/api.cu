@@ -62,6 +62,34 @@ ScoreWs carve_score(WsCursor &c, int H, int W, int k, int th, int tw)
     return w;
 }
 
+// Whole path with host buffers: device copies of both feature maps and every intermediate.
+struct HostWs {
+    float *X, *T, *C, *heat;
+    uint8_t *tl, *ql;
+    int32_t *tc, *am;
+    FitWs fit;
+    AssignWs as;
+    ScoreWs sc;
+};
+
+HostWs carve_host(WsCursor &c, int H, int W, int D, int k, int th, int tw, int F)
+{
+    HostWs w;
+    const long long n = (long long)H * W, l = (long long)th * tw;
+    w.X = c.take<float>((size_t)n * D);
+    w.T = c.take<float>((size_t)l * D);
+    w.C = c.take<float>((size_t)k * D);
+    w.heat = c.take<float>((size_t)(H - th + 1) * (W - tw + 1));
+    w.tl = c.take<uint8_t>((size_t)l);
+    w.ql = c.take<uint8_t>((size_t)n);
+    w.tc = c.take<int32_t>((size_t)F * k);
+    w.am = c.take<int32_t>(2);
+    w.fit = carve_fit(c, l, D, k);
+    w.as = carve_assign(c, n, D, k);
+    w.sc = carve_score(c, H, W, k, th, tw);
+    return w;
+}
+
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 vqnnf_status from_cuda(cudaError_t e)
@@ -484,6 +512,102 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
     const int HO = H - th + 1, WO = W - tw + 1;
     return from_cuda(launch_score(sw.S, sw.u16, W, k, HO, WO, bs, gs, wg, t_counts, heatmap, sw.amax,
                                   argmax_yx, s));
+}
+
+// ------------------------------------------------------------------ whole path, host buffers
+static vqnnf_status match_host_check(int H, int W, int D, int k, int th, int tw, int F, int prec)
+{
+    if (H < 1 || W < 1 || D < 1 || k < 1 || th < 1 || tw < 1 || th > H || tw > W || F < 1) return VQNNF_EINVAL;
+    if ((long long)k > (long long)th * tw) return VQNNF_EINVAL;
+    if (k > kMaxK) return VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if ((long long)H * W >= (1ll << 32) || (long long)th * tw > (1ll << 30) ||
+        (long long)(H + 1) * (W + 1) >= (1ll << 31))
+        return VQNNF_EUNSUPPORTED;
+    return VQNNF_OK;
+}
+
+size_t vqnnf_match_host_workspace_bytes(int H, int W, int D, int k, int th, int tw, int F, vqnnf_prec prec)
+{
+    if (match_host_check(H, W, D, k, th, tw, F, prec) != VQNNF_OK) return 0;
+    WsCursor c{nullptr, 0};
+    carve_host(c, H, W, D, k, th, tw, F);
+    return (c.off + 255) & ~size_t(255);
+}
+
+vqnnf_status vqnnf_match_host(const float *X_host, int H, int W, int D, const float *T_host, int th, int tw,
+                              int k, int iters, uint64_t seed, vqnnf_prec prec, const vqnnf_filter *bank, int F,
+                              float *heat_host, int32_t *argmax_host, void *ws, size_t ws_bytes, void *stream,
+                              void *stream2)
+{
+    if (!X_host || !T_host || !argmax_host || !ws || iters < 0 || !aligned(ws, 256)) return VQNNF_EINVAL;
+    vqnnf_status st = match_host_check(H, W, D, k, th, tw, F, prec);
+    if (st != VQNNF_OK) return st;
+    if (ws_bytes < vqnnf_match_host_workspace_bytes(H, W, D, k, th, tw, F, prec)) return VQNNF_ENOMEM;
+    BankSpec bs;
+    GridSpec gs;
+    WGridSpec wg;
+    if ((st = compile_bank(bank, F, th, tw, bs, gs)) != VQNNF_OK) return st;
+    memset(&wg, 0, sizeof(wg));
+    if (gs.G == 0) detect_wgrid(bank, F, bs, wg);
+    const bool u16 = sat_is_u16(th, tw);
+    const size_t smem = wg.NG > 0 ? score_wgrid_smem_bytes(u16 ? 2 : 4, wg, k)
+                                  : score_smem_bytes_for(u16 ? 2 : 4, bs, gs, k);
+    if (smem > (size_t)device_smem_optin()) return VQNNF_EUNSUPPORTED;
+    WsCursor cur{static_cast<char *>(ws), 0};
+    HostWs w = carve_host(cur, H, W, D, k, th, tw, F);
+    const cudaStream_t s = as_stream(stream), cs = stream2 ? as_stream(stream2) : s;
+    const long long l = (long long)th * tw;
+    constexpr int kBands = 8;
+    const int nb = H < kBands ? H : kBands;
+    cudaEvent_t evT = nullptr, evDone = nullptr, evB[kBands] = {};
+    cudaError_t e = cudaEventCreateWithFlags(&evT, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evDone, cudaEventDisableTiming);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaEventCreateWithFlags(&evB[b], cudaEventDisableTiming);
+    // copies, in order: the template, then the query's row bands
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.T, T_host, sizeof(float) * (size_t)l * D, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(evT, s);
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const long long y0 = (long long)H * b / nb, y1 = (long long)H * (b + 1) / nb;
+        const size_t off = (size_t)y0 * W * D;
+        e = cudaMemcpyAsync(w.X + off, X_host + off, sizeof(float) * (size_t)(y1 - y0) * W * D,
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(evB[b], s);
+    }
+    // compute: template side, then each band's assignment once it has landed, then the score
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, evT, 0);
+    if (e == cudaSuccess) {
+        st = run_fit(w.T, l, D, k, iters, seed, prec, w.C, w.fit, cs);
+        if (st == VQNNF_OK) st = run_assign(w.T, l, D, w.C, k, prec, w.tl, nullptr, w.fit.as, cs);
+        if (st == VQNNF_OK) st = from_cuda(launch_filter_responses(w.tl, th, tw, k, bs, w.tc, cs));
+        for (int b = 0; b < nb && st == VQNNF_OK; ++b) {
+            const long long y0 = (long long)H * b / nb, y1 = (long long)H * (b + 1) / nb;
+            st = from_cuda(cudaStreamWaitEvent(cs, evB[b], 0));
+            if (st == VQNNF_OK)
+                st = run_assign(w.X + (size_t)y0 * W * D, (y1 - y0) * W, D, w.C, k, prec, w.ql + (size_t)y0 * W,
+                                nullptr, w.as, cs);
+        }
+        const int HO = H - th + 1, WO = W - tw + 1;
+        if (st == VQNNF_OK) st = from_cuda(launch_sat(w.ql, H, W, k, w.sc.u16, w.sc.carry, w.sc.bandsum, w.sc.S, cs));
+        if (st == VQNNF_OK)
+            st = from_cuda(launch_score(w.sc.S, w.sc.u16, W, k, HO, WO, bs, gs, wg, w.tc, w.heat, w.sc.amax, w.am, cs));
+        if (st == VQNNF_OK && heat_host)
+            st = from_cuda(cudaMemcpyAsync(heat_host, w.heat, sizeof(float) * (size_t)HO * WO,
+                                           cudaMemcpyDeviceToHost, cs));
+        if (st == VQNNF_OK)
+            st = from_cuda(cudaMemcpyAsync(argmax_host, w.am, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+        // the caller's stream reaches the end of this call's work only after the compute stream
+        if (st == VQNNF_OK) st = from_cuda(cudaEventRecord(evDone, cs));
+        if (st == VQNNF_OK) st = from_cuda(cudaStreamWaitEvent(s, evDone, 0));
+    } else {
+        st = from_cuda(e);
+    }
+    // events are released once their pending work completes
+    if (evT) cudaEventDestroy(evT);
+    if (evDone) cudaEventDestroy(evDone);
+    for (int b = 0; b < nb; ++b)
+        if (evB[b]) cudaEventDestroy(evB[b]);
+    return st;
 }
 
 // ------------------------------------------------------------------ soft-VQ heatmap
