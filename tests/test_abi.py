@@ -169,3 +169,28 @@ def test_batch_workspace_and_refusals(lib):
     assert call(plan=_lib.VqnnfBatchPlan(64, 0, -1, 0)) == _lib.EINVAL
     assert call(plan=_lib.VqnnfBatchPlan(256, 3, -1, 0)) == _lib.EINVAL
     assert lib.vqnnf_batch_tune(qa, 1, ta, 1, 256, 3, ctypes.c_uint64(1), 3, None, FAKE, 1 << 40, None) == _lib.EINVAL
+
+
+def test_match_host_workspace_and_refusals(lib):
+    """Whole path with host buffers: workspace size and host-side argument checks only."""
+    from paper_2306_15010_gb300 import _lib
+    nb = lib.vqnnf_match_host_workspace_bytes(2048, 2048, 512, 128, 128, 128, 10, 1)
+    # at least the device copy of the query's features and the 16-bit integral image
+    assert nb % 256 == 0 and nb > 2048 * 2048 * 512 * 4 + 2049 * 128 * 2056 * 2
+    for args in [(64, 64, 16, 8, 65, 8, 5, 1),       # template taller than the query
+                 (64, 64, 16, 257, 32, 32, 5, 1),    # k > 256
+                 (64, 64, 16, 100, 8, 8, 5, 1),      # k > template pixels
+                 (64, 64, 10, 8, 8, 8, 5, 1),        # D % 16 on the tensor path
+                 (64, 64, 16, 8, 8, 8, 0, 1)]:       # empty bank
+        assert lib.vqnnf_match_host_workspace_bytes(*args) == 0
+    rect = _lib.VqnnfRect(0, 0, 8, 8, 1)
+    filt = (_lib.VqnnfFilter * 1)(_lib.VqnnfFilter(1, ctypes.pointer(rect), 1.0, 64.0))
+    am = (ctypes.c_int32 * 2)()
+    call = lambda **kw: lib.vqnnf_match_host(
+        kw.get("X", FAKE), 64, 64, 16, kw.get("T", FAKE), 8, 8, 8, 3, ctypes.c_uint64(1), 1, filt, 1, None,
+        kw.get("am", ctypes.addressof(am)), kw.get("ws", FAKE), kw.get("wsb", 1 << 40), None, None)
+    assert call(X=None) == _lib.EINVAL
+    assert call(T=None) == _lib.EINVAL
+    assert call(am=None) == _lib.EINVAL
+    assert call(ws=None) == _lib.EINVAL
+    assert call(wsb=256) == _lib.ENOMEM
