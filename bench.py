@@ -40,11 +40,11 @@ OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,187,915,008 + 5,257,216 bytes),
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,862,016 + 4,998,400 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2187915008 + 5257216) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "57ad17d226cde24c61df45e28e6ccc89d65364d1586ec5f2fd572098ae947ae3"
+TC_TRAFFIC_PER_PX = (2147862016 + 4998400) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "b489483627cd9c6e1a203d81920e5cb4db3d8c7a708669f5be9115375c0fdd70"
 
 
 

@@ -10,7 +10,8 @@
 //
 // One persistent CTA per SM, 128-pixel tiles, warp-specialised (23 warps):
 //   warp 0      TMA producer of the FP32 feature boxes (128 rows x 32 floats, 128B swizzle),
-//               up to eight boxes in flight, plus L2 prefetch further ahead
+//               up to eight boxes in flight (an optional L2 prefetch further ahead is off by
+//               default: it measured slower)
 //   warp 22     TMA producer of the two BF16 centroid planes (k rows x 64 elements, 128B
 //               swizzle); separate from warp 0 so that feature loads never wait for MMAs
 //   warp 1      TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
@@ -53,7 +54,7 @@ constexpr int NT = 736;            // 23 warps
 constexpr int F32_BOX = TM * 32 * 4;       // 16 KB: 128 rows x 32 floats
 constexpr double kU = 5.9604644775390625e-08;
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
-constexpr int PF = 8;              // chunks prefetched into L2 ahead of the loads
+constexpr int PF = 0;              // chunks prefetched into L2 ahead of the loads (none: measured best)
 
 struct TcArgs {
     long long n;
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             bool ok = true;
             long long last[kMaxSF];
             for (int q = 0; q < kMaxSF; ++q) last[q] = -1;
-            // L2 prefetch runs PF chunks ahead of the shared-memory loads
+            // optional L2 prefetch, g.pf chunks ahead of the shared-memory loads
             long long pf_tile = blockIdx.x;
             int pf_kc = 0;
             auto prefetch_next = [&]() {
