@@ -409,6 +409,8 @@ __device__ __forceinline__ void df_warp_sum(float &hi, float &lo)
     lo = e;
 }
 
+constexpr int RS_MAXC = 16;        // 32-feature chunks of a pixel held in registers by the re-scoring
+
 __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ X, int D,
                                                       const float *__restrict__ C, int k,
                                                       uint8_t *__restrict__ labels, FlagList fl,
@@ -428,6 +430,15 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
         const float *x = X + (size_t)pix * D;
         float r1 = FLT_MAX, r2 = FLT_MAX;
         int a = 0, nc = 0;
+        // D <= 32 RS_MAXC: the pixel's features stay in registers and every candidate's loads
+        // are issued together (the same per-lane order of additions as the general loop)
+        const bool inreg = D <= 32 * RS_MAXC;
+        float xv[RS_MAXC];
+#pragma unroll
+        for (int t = 0; t < RS_MAXC; ++t) {
+            const int i = 32 * t + lane;
+            xv[t] = inreg && i < D ? x[i] : 0.f;
+        }
         for (int w = 0; w < kMaskWords; ++w) {
             unsigned bits = __shfl_sync(0xffffffffu, mw, w);
             while (bits) {
@@ -435,11 +446,25 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
                 bits &= bits - 1;
                 const float *c = C + (size_t)j * D;
                 float acc = 0.f;
-                for (int i0 = 0; i0 < D; i0 += 32) {
-                    const bool ok = i0 + lane < D;
-                    const int i = ok ? i0 + lane : D - 1;
-                    const float d = x[i] - c[i];
-                    acc = ok ? fmaf(d, d, acc) : acc;
+                if (inreg) {
+                    float cv[RS_MAXC];
+#pragma unroll
+                    for (int t = 0; t < RS_MAXC; ++t) {
+                        const int i = 32 * t + lane;
+                        cv[t] = i < D ? c[i] : 0.f;
+                    }
+#pragma unroll
+                    for (int t = 0; t < RS_MAXC; ++t) {
+                        const float d = xv[t] - cv[t];
+                        if (32 * t + lane < D) acc = fmaf(d, d, acc);
+                    }
+                } else {
+                    for (int i0 = 0; i0 < D; i0 += 32) {
+                        const bool ok = i0 + lane < D;
+                        const int i = ok ? i0 + lane : D - 1;
+                        const float d = x[i] - c[i];
+                        acc = ok ? fmaf(d, d, acc) : acc;
+                    }
                 }
                 const float r = warp_sum(acc);
                 ++nc;
