@@ -172,3 +172,25 @@ def test_batch_argument_errors(vq, case):
     with pytest.raises(vq.VqnnfError) as e:                  # plan outside the candidates
         vq.vqnnf_match_batch(Xs, [Ts[0]], [8], ITERS, SEED, G, vq.BatchPlan(64, 0, -1))
     assert e.value.status == 1
+
+
+def test_batch_wide_template_and_tiny_query(vq):
+    """A template wider than the grid score kernel stages (the generic score kernel) and a
+    query that is exactly one template: still bit-identical to the single-pair path."""
+    q1 = synth.query_map(60, 420, 32, M=8, n_sp=60, seed=901)
+    q2 = synth.query_map(40, 300, 32, M=8, n_sp=40, seed=902)
+    T1, _ = synth.crop_template(q1, 20, 300, seed=903)                 # 300 columns wide
+    T2 = q2.X[:40, :300].clone()                                       # the whole second query
+    Xs, Ts, ks = [q1.X.cuda(), q2.X.cuda()], [T1.cuda(), T2.cuda()], [12, 40]
+    heats, ams = vq.vqnnf_match_batch(Xs, Ts, ks, 3, 77, 2)
+    for j, (T, k) in enumerate(zip(Ts, ks)):
+        h, w = T.shape[:2]
+        bank = synth.grid_bank(h, w, 2)
+        C = vq.vqnnf_fit_codebook(T, k, 3, 77 + j, "bf16")
+        tc = vq.vqnnf_filter_responses(vq.vqnnf_assign(T, C, "bf16"), k, bank)
+        for i, X in enumerate(Xs):
+            if h > X.shape[0] or w > X.shape[1]:
+                continue
+            heat, am = vq.vqnnf_score(vq.vqnnf_assign(X, C, "bf16"), k, h, w, bank, tc)
+            assert torch.equal(heats[i][j], heat), (i, j)
+            assert ams[i, j].tolist() == am.tolist()

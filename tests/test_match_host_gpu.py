@@ -59,3 +59,17 @@ def test_match_host_maximum_only_and_refusals(vq, case):
         vq.vqnnf_match_host(X.cuda(), T, k, iters, seed, bank)
     with pytest.raises(vq.VqnnfError):                      # k larger than the template
         vq.vqnnf_match_host(X, T, 40 * 36 + 1, iters, seed, bank)
+
+
+def test_match_host_fewer_rows_than_bands(vq):
+    """A query of 5 rows (fewer than the copy bands) and a template of its full height."""
+    q = synth.query_map(5, 90, 16, M=4, n_sp=6, seed=81)
+    T = q.X[:, 10:30].clone()
+    bank = synth.grid_bank(5, 20, 1)
+    C = vq.vqnnf_fit_codebook(T.cuda(), 6, 2, 82, "bf16")
+    tc = vq.vqnnf_filter_responses(vq.vqnnf_assign(T.cuda(), C, "bf16"), 6, bank)
+    heat_ref, am_ref = vq.vqnnf_score(vq.vqnnf_assign(q.X.cuda(), C, "bf16"), 6, 5, 20, bank, tc)
+    heat, am = vq.vqnnf_match_host(q.X, T, 6, 2, 82, bank, "bf16", stream2=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    assert torch.equal(heat, heat_ref.cpu()) and am.tolist() == am_ref.cpu().tolist()
+    assert float(heat[0, 10]) == 0.0                                   # the template's own place
