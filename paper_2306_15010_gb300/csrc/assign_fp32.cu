@@ -241,7 +241,7 @@ __device__ __forceinline__ int decide_pixel(const float *srow, int stride, int k
     return cnt == 1 ? last : amin;
 }
 
-__global__ void __launch_bounds__(NT) assign_fp32_kernel(const float *__restrict__ X, long long n,
+__global__ void __launch_bounds__(NT, 2) assign_fp32_kernel(const float *__restrict__ X, long long n,
                                                          int D, int k, CodebookPrep p,
                                                          uint8_t *__restrict__ labels, FlagList fl)
 {
