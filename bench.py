@@ -333,7 +333,7 @@ def run_gpu(args, rank, world):
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=am)
     paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
-    soft_vq = None if args.no_soft else run_soft(vq, dev)
+    soft_vq = None if args.no_soft else run_soft(vq, dev, B=args.soft_batch)
     batch = None if args.no_batch else run_batch(vq, dev, eager=args.batch_eager)
 
     if rank != 0:
@@ -456,13 +456,13 @@ def run_paper_bank(vq, pipe, cfg, s, dev, reps=5):
             "argmax_yx": am.cpu().tolist(), "kernel": "score_wgrid_kernel (weighted 3 x 3 grids, one per sub-scale)"}
 
 
-def run_soft(vq, dev, reps=3):
+def run_soft(vq, dev, reps=3, B=8):
     """The training path: soft-VQ heatmap of 8 queries 512 x 512, D = 256, k = 64, 3 x 3 cell
     filters (learnable weights, 1 at start), tau = 0.1; forward and backward (gradients for the
     query features, the centroids and the weights of L = sum heat * N(0,1) weights)."""
     import torch
     import synth
-    B, H, W, D, k, th, tw, G, tau = 8, 512, 512, 256, 64, 64, 64, 3, 0.1
+    H, W, D, k, th, tw, G, tau = 512, 512, 256, 64, 64, 64, 3, 0.1
     Q = torch.stack([synth.query_map(H, W, D, M=64, n_sp=1250, seed=4000 + i, device=dev).X for i in range(B)])
     T, _ = synth.crop_template(synth.query_map(H, W, D, M=64, n_sp=1250, seed=4000, device=dev), th, tw, seed=4100)
     T = T.to(dev).contiguous()
@@ -486,7 +486,7 @@ def run_soft(vq, dev, reps=3):
             bw.append(e[1].elapsed_time(e[2]))
         Q.grad = C.grad = wf.grad = None
     f_ms, b_ms = sorted(fw)[reps // 2], sorted(bw)[reps // 2]
-    return {"workload": "8 queries 512x512, D=256, k=64, 64x64 template, 3x3 cells (F=9), tau=0.1",
+    return {"workload": f"{B} queries 512x512, D=256, k=64, 64x64 template, 3x3 cells (F=9), tau=0.1",
             "forward_ms": round(f_ms, 3), "backward_ms": round(b_ms, 3),
             "train_step_mpix_s": round(B * H * W / ((f_ms + b_ms) * 1e-3) / 1e6, 2),
             "note": "backward includes the autograd engine's elementwise product and sum of the loss"}
@@ -689,6 +689,8 @@ def main():
     ap.add_argument("--query-size", type=int, default=HEADLINE["H"],
                     help="query side (profiling captures on a smaller case)")
     ap.add_argument("--no-soft", action="store_true", help="skip the soft-VQ training-path timing")
+    ap.add_argument("--soft-batch", type=int, default=8,
+                    help="queries in the soft-VQ training step (8 is the workload; fewer for profiling captures)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-templates timing")
     ap.add_argument("--batch-eager", action="store_true",
                     help="time the batch call enqueued directly instead of replayed from a CUDA graph "
