@@ -143,13 +143,20 @@ __device__ __forceinline__ int top_bit(unsigned __int128 v)
     return hi ? 127 - __clzll((long long)hi) : (lo ? 63 - __clzll((long long)lo) : -1);
 }
 
-__global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict__ T, int D, int k,
+constexpr int FCH = 88;      // member rows per staged chunk of the in-order FP64 route
+constexpr int COOP_MIN = 1024;   // clusters at least this large stage that route block-wide
+
+__global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restrict__ T, int D, int k,
                                                          const int *__restrict__ cnt, const int *__restrict__ off,
                                                          const int *__restrict__ members, float *__restrict__ C)
 {
-    __shared__ unsigned __int128 spos[UW][32], sneg[UW][32], smag[UW][32];
+    // the 128-bit partial sums, later reused for the staged member values of the FP64 route
+    __shared__ __align__(16) unsigned __int128 sacc[3][UW][32];
     __shared__ int slow[UW][32], shish[UW][32];
     __shared__ unsigned char sbad[UW][32];
+    __shared__ unsigned s_need;
+    static_assert(2 * FCH * 33 * sizeof(float) <= sizeof(sacc), "staging buffers exceed the reused space");
+    auto spos = sacc[0], sneg = sacc[1], smag = sacc[2];
     const int j = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
@@ -178,39 +185,78 @@ __global__ void __launch_bounds__(32 * UW) update_kernel(const float *__restrict
     shish[w][lane] = f.hish;
     sbad[w][lane] = f.bad ? 1 : 0;
     __syncthreads();
-    if (w != 0) return;
-    unsigned __int128 pos = 0, neg = 0, mag = 0;
-    int low = 1 << 30, hish = 0;
-    bool bad = false;
+    // small clusters: warp 0 alone finishes (the other warps leave now, so the next block can
+    // start); large clusters keep every warp for a staged in-order FP64 route
+    const bool coop = c >= COOP_MIN;                    // uniform over the block
+    if (!coop && w != 0) return;
+    double s = 0.0;
+    bool need = false;                                  // this lane's column takes the FP64 route
+    if (w == 0) {
+        unsigned __int128 pos = 0, neg = 0, mag = 0;
+        int low = 1 << 30, hish = 0;
+        bool bad = false;
 #pragma unroll 2
-    for (int u = 0; u < UW; ++u) {
-        pos += spos[u][lane];
-        neg += sneg[u][lane];
-        mag += smag[u][lane];
-        low = min(low, slow[u][lane]);
-        hish = max(hish, shish[u][lane]);
-        bad |= sbad[u][lane] != 0;
+        for (int u = 0; u < UW; ++u) {
+            pos += spos[u][lane];
+            neg += sneg[u][lane];
+            mag += smag[u][lane];
+            low = min(low, slow[u][lane]);
+            hish = max(hish, shish[u][lane]);
+            bad |= sbad[u][lane] != 0;
+        }
+        // the 128-bit sums cannot have wrapped while c values below 2^(hish + 24) units stay
+        // below 2^128: hish + 24 + ceil(log2 c) <= 127
+        const bool nowrap = hish + 24 + (32 - __clz(c)) <= 127;
+        if (bad || !nowrap) {
+            need = true;                                 // outside the exact route
+        } else if (mag == 0) {
+            s = 0.0;                                     // only zeros: the FP64 sum is +0
+        } else if (top_bit(mag) - low <= 52) {
+            // exact: |sum| >> low has at most 53 significant bits
+            const bool negative = neg > pos;
+            const unsigned __int128 d = negative ? neg - pos : pos - neg;
+            const double v = (double)(uint64_t)(d >> low);
+            s = ldexp(negative ? -v : v, low - 80);
+        } else {
+            need = true;                                 // a rounding could occur in order
+        }
+        const unsigned nm = __ballot_sync(0xffffffffu, need && i < D);
+        if (lane == 0) s_need = nm;
+        if (!coop && need) {                             // the in-order FP64 sum, lane by lane
+            s = 0.0;
+            for (int q2 = 0; q2 < c; ++q2) s += (double)__ldg(T + (size_t)m[q2] * D + ic);
+        }
     }
-    double s;
-    // the 128-bit sums cannot have wrapped while c values below 2^(hish + 24) units stay below
-    // 2^128: hish + 24 + ceil(log2 c) <= 127
-    const bool nowrap = hish + 24 + (32 - __clz(c)) <= 127;
-    if (bad || !nowrap) {
-        s = 0.0;                                         // outside the exact route: in-order FP64
-        for (int q2 = 0; q2 < c; ++q2) s += (double)__ldg(T + (size_t)m[q2] * D + ic);
-    } else if (mag == 0) {
-        s = 0.0;                                         // only zeros: the FP64 sum is +0
-    } else if (top_bit(mag) - low <= 52) {
-        // exact: |sum| >> low has at most 53 significant bits
-        const bool negative = neg > pos;
-        const unsigned __int128 d = negative ? neg - pos : pos - neg;
-        const double v = (double)(uint64_t)(d >> low);
-        s = ldexp(negative ? -v : v, low - 80);
-    } else {
-        s = 0.0;                                         // rare: the in-order FP64 evaluation
-        for (int q2 = 0; q2 < c; ++q2) s += (double)__ldg(T + (size_t)m[q2] * D + ic);
+    if (!coop) {
+        if (i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
+        return;
     }
-    if (i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
+    __syncthreads();                                     // partial sums read; s_need visible
+    const unsigned nm = s_need;
+    if (nm) {
+        // the in-order FP64 sum of the flagged columns: the block's 32 columns of the members'
+        // rows are staged in shared memory, FCH rows at a time and double-buffered; warps 1..15
+        // load the next chunk while warp 0 adds the current one, row by row, in member order
+        float (*vals)[FCH][33] = reinterpret_cast<float (*)[FCH][33]>(&sacc[0][0][0]);
+        auto stage = [&](int q0, int buf, int w0, int nwarp) {
+            const int nr = min(FCH, c - q0);
+            for (int r = w - w0; r < nr; r += nwarp) vals[buf][r][lane] = __ldg(T + (size_t)m[q0 + r] * D + ic);
+        };
+        stage(0, 0, 0, UW);
+        __syncthreads();
+        const bool mine = w == 0 && ((nm >> lane) & 1u);
+        double acc = 0.0;
+        for (int q0 = 0, t = 0; q0 < c; q0 += FCH, ++t) {
+            if (w != 0 && q0 + FCH < c) stage(q0 + FCH, (t + 1) & 1, 1, UW - 1);
+            if (mine) {
+                const int nr = min(FCH, c - q0);
+                for (int r = 0; r < nr; ++r) acc += (double)vals[t & 1][r][lane];
+            }
+            __syncthreads();
+        }
+        if (mine) s = acc;
+    }
+    if (w == 0 && i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
 }
 
 }  // namespace

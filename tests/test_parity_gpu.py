@@ -141,6 +141,22 @@ def test_fit_codebook_exact_sum_edge_values(vq, prec):
     assert np.array_equal(C.cpu().numpy().view(np.uint32), C_ref.view(np.uint32))
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_fit_codebook_large_clusters_exact(vq, prec):
+    """Clusters of more than a thousand members (the block-wide staged route of the in-order
+    FP64 sums) with values that force that route: bit-identical to the oracle."""
+    r = np.random.default_rng(11)
+    l, D, k = 3600, 32, 2
+    T = np.abs(r.normal(0.5, 0.3, (l, D))).astype(np.float32)
+    T[r.random((l, D)) < 0.01] *= np.float32(2.0 ** -50)        # spans over 52 bits
+    T[:, 3] = np.float32(1e-30)                                 # a column with no value in range
+    T[:, 5] = (r.uniform(1, 2, l) * 2.0 ** 44).astype(np.float32)   # sums past 2^127 units
+    T = T.reshape(60, 60, D)
+    C = vq.vqnnf_fit_codebook(_dev(T), k, 3, 21, prec)
+    C_ref = oracle.fit_codebook(T, k, 3, 21)
+    assert np.array_equal(C.cpu().numpy().view(np.uint32), C_ref.view(np.uint32))
+
+
 def test_fit_zero_iters_gathers_seeded_init(vq):
     r = np.random.default_rng(6)
     T = r.random((30, 31, 8)).astype(np.float32)
