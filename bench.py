@@ -371,7 +371,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": kernels_per_step(cfg, args.prec) * K,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe)
     return line
 
 
@@ -610,8 +610,10 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
     return out
 
 
-def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1):
-    """The FP64 oracle timed on bounded samples of the same workload, scaled to one step."""
+def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None):
+    """The FP64 oracle timed on bounded samples of the same workload, scaled to one step.
+    With ``pipe`` (the timed BF16 pipeline), this run's own results are also checked against
+    the oracle on the same samples."""
     import numpy as np
     import oracle
     oracle.build()
@@ -641,11 +643,28 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1):
     t_sc = time.perf_counter() - t0
     t_step = (t_fit1 * cfg["iters"] + t_asg * (L + th * tw) / px_asg
               + t_sc * HO * WO / nwin)
-    return {"value": round(L / t_step / 1e6, 6), "unit": "Mpix/s",
-            "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"1 Lloyd step (x{cfg['iters']}), {px_asg} query pixels assigned, "
-                       f"{nwin} windows scored; scaled to one full step"),
-            "step_s_estimate": round(t_step, 2)}
+    out = {"value": round(L / t_step / 1e6, 6), "unit": "Mpix/s",
+           "cores": os.cpu_count(), "kind": "oracle",
+           "sample": (f"1 Lloyd step (x{cfg['iters']}), {px_asg} query pixels assigned, "
+                      f"{nwin} windows scored; scaled to one full step"),
+           "step_s_estimate": round(t_step, 2)}
+    if pipe is not None:
+        # this run's results on the same samples: the labels of the first 8 query rows under the
+        # run's codebook (equal outside the oracle's near-tie band, relative gap < 1e-6), and the
+        # heatmap at the sampled windows recomputed in FP64 from the run's labels and counts
+        Cg = pipe.C.cpu().numpy()
+        ref, d1, d2 = oracle.assign(Xh, Cg, return_dist=True)
+        band = (oracle.relative_gap(d1, d2) < 1e-6).reshape(-1)
+        gl = pipe.ql[: 8].cpu().numpy().astype(np.int32).reshape(-1)
+        mism = int(((gl != ref.reshape(-1)) & ~band).sum())
+        href = oracle.score_at(pipe.ql.cpu().numpy().astype(np.int32), k, bank, pipe.tc.cpu().numpy(), win)
+        hg = pipe.heat.cpu().numpy()[win[:, 0], win[:, 1]].astype(np.float64)
+        rel = float(np.abs(hg - href).max() / max(float(np.abs(href).max()), 1e-30))
+        out["oracle_check"] = {"labels_checked": int(gl.size), "label_mismatches_outside_band": mism,
+                               "near_tie_band_pixels": int(band.sum()),
+                               "heat_windows_checked": int(nwin), "heat_max_rel_err": rel,
+                               "heat_bound": 1e-4}
+    return out
 
 
 def run_reference(args, rank, world):
