@@ -548,7 +548,7 @@ def run_batch(vq, dev, reps=2, eager=False):
            "ms_per_batch": round(ms, 2), "pairs_per_s": round(nq * nt / (ms * 1e-3), 1),
            "query_mpix_per_s": round(px / (ms * 1e-3) / 1e6, 2),
            "pair_mpix_per_s": round(px * nt / (ms * 1e-3) / 1e6, 1),
-           "plan": {"group_cols": plan.group_cols, "sf": plan.sf, "pf": plan.pf},
+           "plan": {"stationary": plan.stationary, "group_cols": plan.group_cols, "sf": plan.sf, "pf": plan.pf},
            "codebook_columns": cols, "query_px": px,
            "execution": "one vqnnf_match_batch call per batch, " +
                         ("enqueued directly" if eager else "CUDA graph replay")}

@@ -300,7 +300,9 @@ typedef struct vqnnf_batch_plan {
     int32_t group_cols;   /* 128 or 256: columns of one shared contraction                 */
     int32_t sf;           /* FP32 feature boxes in flight per SM: 0 (default) or 2, 4, 6, 8 */
     int32_t pf;           /* L2 prefetch distance in 64-feature chunks, -1 = default       */
-    int32_t reserved;     /* 0                                                              */
+    int32_t stationary;   /* 1: where D <= 256, a query's features are read once per tile for
+                             all its groups (the tile's operand stays in tensor memory while
+                             every group's centroids stream past); 0: one launch per group  */
 } vqnnf_batch_plan;
 
 size_t vqnnf_batch_workspace_bytes(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt,
@@ -311,8 +313,9 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
                                void *stream);
 
 /* Autotuner: fits the templates as vqnnf_match_batch does, then times the assignment of the
- * largest query under each candidate plan (group_cols in {128, 256} x feature boxes in
- * {4, 6, 8} x prefetch in {0, 8}) with CUDA events and writes the fastest to *plan.  It
+ * largest query under each candidate plan (stationary where D <= 256, and one launch per group
+ * with group_cols in {128, 256} x feature boxes in {4, 6, 8} x prefetch in {0, 8}) with CUDA
+ * events and writes the fastest to *plan.  It
  * SYNCHRONISES `stream` (not graph-capturable); the workspace is the batch workspace. */
 vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
                               int iters, uint64_t seed, int G, vqnnf_batch_plan *plan, void *ws,

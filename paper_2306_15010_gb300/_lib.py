@@ -64,7 +64,7 @@ class VqnnfBatchTemplate(ctypes.Structure):
 
 class VqnnfBatchPlan(ctypes.Structure):
     _fields_ = [("group_cols", ctypes.c_int32), ("sf", ctypes.c_int32), ("pf", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("stationary", ctypes.c_int32)]
 
 
 class VqnnfError(RuntimeError):

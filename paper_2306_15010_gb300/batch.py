@@ -25,9 +25,10 @@ class BatchPlan:
     group_cols: int = 256
     sf: int = 0
     pf: int = -1
+    stationary: int = 1
 
     def c(self) -> "_lib.VqnnfBatchPlan":
-        return _lib.VqnnfBatchPlan(int(self.group_cols), int(self.sf), int(self.pf), 0)
+        return _lib.VqnnfBatchPlan(int(self.group_cols), int(self.sf), int(self.pf), int(self.stationary))
 
 
 def _arrays(queries: Sequence[torch.Tensor], templates: Sequence[torch.Tensor], ks: Sequence[int]):
@@ -114,4 +115,4 @@ def vqnnf_batch_tune(queries: Sequence[torch.Tensor], templates: Sequence[torch.
                                       ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(G), ctypes.byref(p),
                                       ws.ptr, ws.nbytes, _stream(stream))
     _lib.check("vqnnf_batch_tune", st)
-    return BatchPlan(p.group_cols, p.sf, p.pf)
+    return BatchPlan(p.group_cols, p.sf, p.pf, p.stationary)

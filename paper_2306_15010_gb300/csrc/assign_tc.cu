@@ -62,7 +62,9 @@ struct TcArgs {
     long long ntiles;
     CodebookPrep p;
     int nseg;
-    TcSeg seg[kMaxSeg];
+    TcSeg seg[kMaxSegStat];          // the single and multi modes use the first kMaxSeg
+    int ngroup;                      // stationary mode: groups of npad columns
+    int gs0[kMaxGroupsStat + 1];     // stationary mode: group g's segments are seg[gs0[g] .. gs0[g + 1])
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -251,27 +253,32 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b, float &ra, float
 
 // ------------------------------------------------------------------ the kernel
 // MULTI: several codebook segments (batching); the single-codebook instantiation keeps the
-// segment's bounds and bound maxima out of the tile loop.
-template <bool MULTI>
+// segment's bounds and bound maxima out of the tile loop.  STAT (with MULTI): several groups
+// of npad columns per tile; the tile's A stages (all nkc chunks) stay in tensor memory until
+// the last group's MMAs, and every group's centroid chunks stream through the B stages.
+template <bool MULTI, bool STAT>
 __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant__ CUtensorMap tmA,
                                                           const __grid_constant__ CUtensorMap tmBhi,
                                                           const __grid_constant__ CUtensorMap tmBlo,
-                                                          TcArgs g)
+                                                          const __grid_constant__ TcArgs g)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int npad = g.npad, D = g.D, nkc = g.nkc, SB = g.sb, SF = g.sf, NB = g.nb, SA = g.sa;
     const int B_PLANE = npad * 128;
+    const int ngroup = STAT ? g.ngroup : 1;
+    const int ncols = ngroup * npad;                       // prepared columns of this launch
+    const int nsegcap = STAT ? kMaxSegStat : kMaxSeg;
     uint8_t *f32s = base;                                  // SF x 16 KB
     uint8_t *bs = f32s + SF * F32_BOX;                     // SB x (hi, lo)
     float *cn = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
-    float4 *colc = reinterpret_cast<float4 *>(cn + npad);  // per column {||c*||^2, a, v, b}
-    float *mean = reinterpret_cast<float *>(colc + npad);  // roundup(D, 64)
+    float4 *colc = reinterpret_cast<float4 *>(cn + ncols); // per column {||c*||^2, a, v, b}
+    float *mean = reinterpret_cast<float *>(colc + ncols); // roundup(D, 64)
     float *norms = mean + nkc * KC;                        // [2 buf][4 quarters][128]
     uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 4 * TM);   // [128][8]
     float4 *segmx = reinterpret_cast<float4 *>(maskbuf + TM * kMaskWords);   // per segment maxima
-    TcSeg *segt = reinterpret_cast<TcSeg *>(segmx + kMaxSeg);                // segment table
-    uint64_t *bar = reinterpret_cast<uint64_t *>(segt + kMaxSeg);
+    TcSeg *segt = reinterpret_cast<TcSeg *>(segmx + nsegcap);                // segment table
+    uint64_t *bar = reinterpret_cast<uint64_t *>(segt + nsegcap);
     uint64_t *full_f = bar, *empty_f = bar + SF, *a_full = bar + 2 * SF, *a_empty = bar + 2 * SF + SA;
     uint64_t *full_b = bar + 2 * SF + 2 * SA, *empty_b = full_b + kMaxSB;
     uint64_t *acc_full = empty_b + kMaxSB, *acc_empty = acc_full + 2, *nrm_full = acc_empty + 2,
@@ -286,20 +293,30 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     const int need = a_col0 + SA * 64;
     const uint32_t tmem_cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 
-    for (int j = tid; j < npad; j += NT) {
+    for (int j = tid; j < ncols; j += NT) {
         bool ok = false;                                  // a real centroid of some segment
+        if constexpr (STAT) {
+            const int gi = j / npad;
+            for (int q = g.gs0[gi]; q < g.gs0[gi + 1]; ++q)
+                ok |= j >= g.seg[q].col0 && j < g.seg[q].col0 + g.seg[q].k;
+        } else {
 #pragma unroll
-        for (int q = 0; q < kMaxSeg; ++q)
-            ok |= q < g.nseg && j >= g.seg[q].col0 && j < g.seg[q].col0 + g.seg[q].k;
+            for (int q = 0; q < kMaxSeg; ++q)
+                ok |= q < g.nseg && j >= g.seg[q].col0 && j < g.seg[q].col0 + g.seg[q].k;
+        }
         const int jc = j < g.krows ? j : g.krows - 1;
         const float nrm = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
         cn[j] = nrm;
         colc[j] = make_float4(nrm, ok ? g.p.a[jc] : 0.f, ok ? g.p.v[jc] : 0.f, ok ? g.p.b[jc] : 0.f);
     }
-    // segment table (static indices into the kernel parameters)
+    // segment table
+    if constexpr (STAT) {
+        for (int q = tid; q < g.nseg; q += NT) segt[q] = g.seg[q];
+    } else {
 #pragma unroll
-    for (int q = 0; q < kMaxSeg; ++q)
-        if (tid == q && q < g.nseg) segt[q] = g.seg[q];
+        for (int q = 0; q < kMaxSeg; ++q)
+            if (tid == q && q < g.nseg) segt[q] = g.seg[q];
+    }
     for (int i = tid; i < nkc * KC; i += NT) mean[i] = g.p.mean[i < D ? i : D - 1];
     if (tid == 0) {
         for (int s = 0; s < SF; ++s) { mbar_init(&full_f[s], 1); mbar_init(&empty_f[s], 2 * TM); }
@@ -368,14 +385,16 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             bool ok = true;
             long long last_b[kMaxSB] = {-1, -1, -1, -1};
             for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
-                for (int kc = 0; kc < nkc; ++kc, ++itb) {
-                    if (!(ok = mbar_wait(&empty_b[sb], pb ^ 1, abort))) break;
-                    mbar_expect_tx(&full_b[sb], 2 * B_PLANE);
-                    uint8_t *bd = bs + sb * 2 * B_PLANE;
-                    tma_load_2d(bd, &tmBhi, kc * KC, 0, &full_b[sb]);
-                    tma_load_2d(bd + B_PLANE, &tmBlo, kc * KC, 0, &full_b[sb]);
-                    last_b[sb] = itb;
-                    if (++sb == (uint32_t)SB) { sb = 0; pb ^= 1; }
+                for (int gi = 0; ok && gi < ngroup; ++gi) {      // one group unless stationary
+                    for (int kc = 0; kc < nkc; ++kc, ++itb) {
+                        if (!(ok = mbar_wait(&empty_b[sb], pb ^ 1, abort))) break;
+                        mbar_expect_tx(&full_b[sb], 2 * B_PLANE);
+                        uint8_t *bd = bs + sb * 2 * B_PLANE;
+                        tma_load_2d(bd, &tmBhi, kc * KC, gi * npad, &full_b[sb]);
+                        tma_load_2d(bd + B_PLANE, &tmBlo, kc * KC, gi * npad, &full_b[sb]);
+                        last_b[sb] = itb;
+                        if (++sb == (uint32_t)SB) { sb = 0; pb ^= 1; }
+                    }
                 }
             }
             if (!ok) {
@@ -394,7 +413,34 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             uint32_t sa = 0, pa = 0, sb = 0, pb = 0, tl = 0;   // stage indices and phase parities
             uint32_t ready = 0;                                // this chunk's barriers seen complete
             bool ok = true;
-            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+            if constexpr (STAT) {
+                // SA == nkc: chunk kc of every tile sits in A stage kc; each tile's stages are
+                // released after the last group's MMAs.  gl counts (tile, group) pairs for the
+                // accumulator buffers.
+                uint32_t gl = 0;
+                for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x) {
+                    for (int gi = 0; ok && gi < ngroup; ++gi, ++gl) {
+                        const uint32_t buf = gl % NB;
+                        if (!(ok = mbar_wait(&acc_empty[buf], ((gl / NB) & 1) ^ 1, abort))) break;
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem_base + buf * npad;
+                        for (int kc = 0; kc < nkc; ++kc) {
+                            if (gi == 0 && !(ok = mbar_wait(&a_full[kc], pa, abort))) break;
+                            if (!(ok = mbar_wait(&full_b[sb], pb, abort))) break;
+                            tc_fence_after();
+                            const uint32_t nsb = sb + 1 == (uint32_t)SB ? 0 : sb + 1, npb = nsb ? pb : pb ^ 1;
+                            tc_mma_chunk(d_tmem, a_base + kc * 64, bdesc0 + (uint64_t)sb * bstep, blo_off, idesc,
+                                         kc != 0, smem_u32(&full_b[nsb]), npb, smem_u32(&full_b[nsb]), npb);
+                            tc_commit(&empty_b[sb]);
+                            if (gi == ngroup - 1) tc_commit(&a_empty[kc]);
+                            sb = nsb; pb = npb;
+                        }
+                        if (ok) tc_commit(&acc_full[buf]);
+                    }
+                    pa ^= 1;
+                }
+            }
+            for (long long tile = blockIdx.x; !STAT && ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
                 const uint32_t buf = tl % NB;
                 if (!(ok = mbar_wait(&acc_empty[buf], ((tl / NB) & 1) ^ 1, abort))) break;
                 tc_fence_after();
@@ -501,19 +547,21 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const float u4 = 4.0f * u;
         const float infl = 1.0f + 0.00390625f;
         const int nseg = MULTI ? g.nseg : 1;
-        // per segment the largest ||c_j*||^2, a_j, v_j and b_j over its centroids (lane q of the
-        // first epilogue warp scans segment q): Bmax below bounds every B_j of a pixel within
+        // per segment the largest ||c_j*||^2, a_j, v_j and b_j over its centroids (lanes of the
+        // first epilogue warp scan the segments): Bmax below bounds every B_j of a pixel within
         // the segment
-        if (warp == 18 && lane < nseg) {
-            float nm = 0.f, am = 0.f, vm = 0.f, bm = 0.f;
-            for (int j = segt[lane].col0; j < segt[lane].col0 + segt[lane].k; ++j) {
-                const float4 c = colc[j];
-                nm = fmaxf(nm, c.x);
-                am = fmaxf(am, c.y);
-                vm = fmaxf(vm, c.z);
-                bm = fmaxf(bm, c.w);
+        if (warp == 18) {
+            for (int q = lane; q < nseg; q += 32) {
+                float nm = 0.f, am = 0.f, vm = 0.f, bm = 0.f;
+                for (int j = segt[q].col0; j < segt[q].col0 + segt[q].k; ++j) {
+                    const float4 c = colc[j];
+                    nm = fmaxf(nm, c.x);
+                    am = fmaxf(am, c.y);
+                    vm = fmaxf(vm, c.z);
+                    bm = fmaxf(bm, c.w);
+                }
+                segmx[q] = make_float4(nm, am, vm, bm);
             }
-            segmx[lane] = make_float4(nm, am, vm, bm);
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");       // the four epilogue warps
         // one codebook: its bound maxima and output pointers are loop invariants
@@ -521,12 +569,108 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         const float cnorm0 = sqrtf(mx0.x) * 1.0001f, nrm0 = mx0.x * 1.0001f;
         uint8_t *const labels0 = g.seg[0].labels;
         const FlagList fl0 = g.seg[0].fl;
-        uint32_t tl = 0;
+        // One segment of this tile: prepared columns [cb, ce), whose accumulators sit at TMEM
+        // column c - cshift of taddr; `release` frees the accumulator buffer after its last read.
+        auto segment = [&](int sgi, uint32_t taddr, int cshift, float X, float Y, float nx, long long pix,
+                           bool valid, bool release, uint32_t buf) {
+            const int cb = MULTI ? segt[sgi].col0 : 0, ce = MULTI ? cb + segt[sgi].ncol : npad;
+            const float4 mx = MULTI ? segmx[sgi] : mx0;
+            // max ||c_j*|| (cn = ||c*||^2 in FP32) and max ||c_j*||^2, with margins
+            const float cnorm_max = MULTI ? sqrtf(mx.x) * 1.0001f : cnorm0;
+            const float nrm_max = MULTI ? mx.x * 1.0001f : nrm0;
+            // pass 1: smallest score of the segment, lowest column on ties, as four
+            // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
+            float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+            int am[4] = {cb, cb, cb, cb};
+            for (int c0 = cb; c0 < ce; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float sc = fmaf(-2.0f, v[j], cn[c0 + j]);
+                    if (sc < sm[j & 3]) { sm[j & 3] = sc; am[j & 3] = c0 + j; }
+                }
+            }
+            float smin = sm[0];
+            int amin = am[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
+            // U, the upper end of column amin's interval, bounds the smallest distance from
+            // above, so the nearest column j has s_j - B_j <= U.
+            const float4 ca = colc[amin];
+            const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
+            // contraction's own error, so Bmax >= every B_j of this pixel in the segment (the
+            // float evaluation is monotone).  The nearest column has s_j <= U + B_j <= U + Bmax;
+            // the limit U + 2 Bmax also covers the rounding of that sum (u |U| < Bmax / 2
+            // because Bmax >= 4u |smin|).  A 32-column block where no lane has a column under
+            // the limit besides amin needs no per-column interval test: its only candidate is
+            // amin.
+            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
+            const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
+            const float lim = U + 2.0f * Bmax;
+            int cnt = 0, last = amin;
+            for (int c0 = cb; c0 < ce; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+                uint32_t maybe = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
+                const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                uint32_t word = own;
+                if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
+                    word = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float4 c = colc[c0 + j];
+                        const float sc = fmaf(-2.0f, v[j], c.x);
+                        const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(sc), c.w))) * infl;
+                        word |= (uint32_t)(sc - B <= U) << j;
+                    }
+                }
+                cnt += __popc(word);
+                if (word) last = c0 + 31 - __clz(word);
+                maskbuf[r * kMaskWords + ((c0 - cb) >> 5)] = word;
+            }
+            for (int w = (ce - cb) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
+            if (release) {                               // every accumulator of the buffer read
+                tc_fence_before();
+                mbar_arrive(&acc_empty[buf]);
+            }
+            uint8_t *const labels = MULTI ? segt[sgi].labels : labels0;
+            const FlagList fl = MULTI ? segt[sgi].fl : fl0;
+            const int lab = (cnt == 1 ? last : amin) - cb;
+            if (valid) labels[pix] = (uint8_t)lab;
+            const bool flagged = valid && cnt > 1;
+            const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+            if (ballot) {
+                const int leader = __ffs(ballot) - 1;
+                unsigned basei = 0;
+                if (lane == leader) basei = atomicAdd(fl.count, (unsigned)__popc(ballot));
+                basei = __shfl_sync(0xffffffffu, basei, leader);
+                if (flagged) {
+                    const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
+                    if (slot < (unsigned long long)g.n) {
+                        fl.pix[slot] = (unsigned)pix;
+#pragma unroll
+                        for (int w = 0; w < kMaskWords; ++w)
+                            fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                    }
+                }
+            }
+        };
+        uint32_t tl = 0, gl = 0;
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
-            const uint32_t buf = tl % NB, ph = (tl / NB) & 1, nb = tl & 1, nph = (tl >> 1) & 1;
-            ok = mbar_wait(&acc_full[buf], ph, abort);
-            ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[nb], nph, abort));
+            const uint32_t nb = tl & 1, nph = (tl >> 1) & 1;
+            if constexpr (!STAT) {
+                const uint32_t buf = tl % NB, ph = (tl / NB) & 1;
+                ok = mbar_wait(&acc_full[buf], ph, abort);
+                ok = __all_sync(0xffffffffu, ok && mbar_wait(&nrm_full[nb], nph, abort));
+            } else {
+                ok = __all_sync(0xffffffffu, mbar_wait(&nrm_full[nb], nph, abort));
+            }
             if (!ok) break;
             tc_fence_after();
             // ||x_hi|| <= (1 + 2^-8) ||x'||  and  ||x' - x_hi - x_lo|| <= 2^-16 ||x'||  (two
@@ -538,95 +682,22 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             const float Dl = nx * 1.5318e-05f + 1e-30f;      // 2^-16 * 1.004
             mbar_arrive(&nrm_empty[nb]);
             const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
-            const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
             const long long pix = tile * TM + r;
             const bool valid = pix < g.n;
-            for (int sgi = 0; sgi < nseg; ++sgi) {
-                const int cb = MULTI ? segt[sgi].col0 : 0, ce = MULTI ? cb + segt[sgi].ncol : npad;
-                const float4 mx = MULTI ? segmx[sgi] : mx0;
-                // max ||c_j*|| (cn = ||c*||^2 in FP32) and max ||c_j*||^2, with margins
-                const float cnorm_max = MULTI ? sqrtf(mx.x) * 1.0001f : cnorm0;
-                const float nrm_max = MULTI ? mx.x * 1.0001f : nrm0;
-                // pass 1: smallest score of the segment, lowest column on ties, as four
-                // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
-                float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
-                int am[4] = {cb, cb, cb, cb};
-                for (int c0 = cb; c0 < ce; c0 += 32) {
-                    float v[32];
-                    tc_ld32(taddr + c0, v);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float s = fmaf(-2.0f, v[j], cn[c0 + j]);
-                        if (s < sm[j & 3]) { sm[j & 3] = s; am[j & 3] = c0 + j; }
-                    }
-                }
-                float smin = sm[0];
-                int amin = am[0];
-#pragma unroll
-                for (int q = 1; q < 4; ++q)
-                    if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
-                // U, the upper end of column amin's interval, bounds the smallest distance from
-                // above, so the nearest column j has s_j - B_j <= U.
-                const float4 ca = colc[amin];
-                const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
-                // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
-                // contraction's own error, so Bmax >= every B_j of this pixel in the segment (the
-                // float evaluation is monotone).  The nearest column has s_j <= U + B_j <= U + Bmax;
-                // the limit U + 2 Bmax also covers the rounding of that sum (u |U| < Bmax / 2
-                // because Bmax >= 4u |smin|).  A 32-column block where no lane has a column under
-                // the limit besides amin needs no per-column interval test: its only candidate is
-                // amin.
-                const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
-                const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
-                const float lim = U + 2.0f * Bmax;
-                int cnt = 0, last = amin;
-                for (int c0 = cb; c0 < ce; c0 += 32) {
-                    float v[32];
-                    tc_ld32(taddr + c0, v);
-                    uint32_t maybe = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
-                    const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
-                    uint32_t word = own;
-                    if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
-                        word = 0;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float4 c = colc[c0 + j];
-                            const float s = fmaf(-2.0f, v[j], c.x);
-                            const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(s), c.w))) * infl;
-                            word |= (uint32_t)(s - B <= U) << j;
-                        }
-                    }
-                    cnt += __popc(word);
-                    if (word) last = c0 + 31 - __clz(word);
-                    maskbuf[r * kMaskWords + ((c0 - cb) >> 5)] = word;
-                }
-                for (int w = (ce - cb) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
-                if (sgi == nseg - 1) {                      // every accumulator of the tile read
-                    tc_fence_before();
-                    mbar_arrive(&acc_empty[buf]);
-                }
-                uint8_t *const labels = MULTI ? segt[sgi].labels : labels0;
-                const FlagList fl = MULTI ? segt[sgi].fl : fl0;
-                const int lab = (cnt == 1 ? last : amin) - cb;
-                if (valid) labels[pix] = (uint8_t)lab;
-                const bool flagged = valid && cnt > 1;
-                const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
-                if (ballot) {
-                    const int leader = __ffs(ballot) - 1;
-                    unsigned basei = 0;
-                    if (lane == leader) basei = atomicAdd(fl.count, (unsigned)__popc(ballot));
-                    basei = __shfl_sync(0xffffffffu, basei, leader);
-                    if (flagged) {
-                        const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
-                        if (slot < (unsigned long long)g.n) {
-                            fl.pix[slot] = (unsigned)pix;
-#pragma unroll
-                            for (int w = 0; w < kMaskWords; ++w)
-                                fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
-                        }
-                    }
+            const uint32_t lanes = tmem_base + ((uint32_t)(grp * 32) << 16);
+            if constexpr (!STAT) {
+                const uint32_t buf = tl % NB;
+                for (int sgi = 0; sgi < nseg; ++sgi)
+                    segment(sgi, lanes + buf * npad, 0, X, Y, nx, pix, valid, sgi == nseg - 1, buf);
+            } else {
+                for (int gi = 0; ok && gi < ngroup; ++gi, ++gl) {
+                    const uint32_t buf = gl % NB, ph = (gl / NB) & 1;
+                    ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], ph, abort));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const int s0 = g.gs0[gi], s1 = g.gs0[gi + 1];
+                    for (int sgi = s0; sgi < s1; ++sgi)
+                        segment(sgi, lanes + buf * npad, gi * npad, X, Y, nx, pix, valid, sgi == s1 - 1, buf);
                 }
             }
         }
@@ -672,14 +743,17 @@ cudaError_t make_map(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, ui
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t tc_smem_bytes(int npad, int D, int sb, int sf)
+// ncols: prepared columns held per column (npad, or ngroup * npad when stationary); nsegcap:
+// capacity of the segment table
+size_t tc_smem_bytes(int npad, int D, int sb, int sf, int ncols = 0, int nsegcap = kMaxSeg)
 {
     const int nkc = (D + KC - 1) / KC;
+    if (ncols == 0) ncols = npad;
     size_t b = 1024;                                       // alignment slack
     b += (size_t)sf * F32_BOX + (size_t)sb * 2 * npad * 128;
-    b += sizeof(float) * (5 * (size_t)npad + (size_t)nkc * KC + 8 * TM);
+    b += sizeof(float) * (5 * (size_t)ncols + (size_t)nkc * KC + 8 * TM);
     b += sizeof(uint32_t) * TM * kMaskWords;
-    b += (sizeof(float4) + sizeof(TcSeg)) * kMaxSeg;
+    b += (sizeof(float4) + sizeof(TcSeg)) * nsegcap;
     b += sizeof(uint64_t) * (2 * sf + 2 * kMaxSA + 2 * kMaxSB + 8 + 1) + 16;   // barriers, TMEM slot, abort flag
     return b;
 }
@@ -751,14 +825,95 @@ cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const Cod
     for (int q = 0; q < nseg; ++q) a.seg[q] = seg[q];
     const long long grid = a.ntiles < sms ? a.ntiles : sms;
     if (nseg == 1) {
-        e = cudaFuncSetAttribute(assign_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(assign_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
-        assign_tc_kernel<false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+        assign_tc_kernel<false, false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
     } else {
-        e = cudaFuncSetAttribute(assign_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(assign_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
-        assign_tc_kernel<true><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+        assign_tc_kernel<true, false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
     }
+    return cudaGetLastError();
+}
+
+// Stationary mode: two FP32 feature boxes in flight (the features are read once per tile, then
+// every group's MMAs run on them) and two centroid stages.
+constexpr int STAT_SF = 2, STAT_SB = 2;
+
+int stat_max_groups(int D, int gcols)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int gmax = 0;
+    for (int ng = 1; ng <= kMaxGroupsStat; ++ng)
+        if (tc_smem_bytes(gcols, D, STAT_SB, STAT_SF, ng * gcols, kMaxSegStat) <= (size_t)optin) gmax = ng;
+    return gmax;
+}
+
+cudaError_t launch_assign_bf16_stat(const float *X, long long n, int D, const CodebookPrep &p, int ngroup,
+                                    int gcols, const TcSeg *seg, const int *gs0, cudaStream_t s)
+{
+    const int nkc = (D + KC - 1) / KC;
+    // all A stages resident: nkc * 64 columns beside one or two accumulators of gcols columns
+    const int nb = 2 * gcols + nkc * 64 <= 512 ? 2 : 1;
+    if (D % 16 != 0 || nkc > kMaxSA || gcols % 32 != 0 || gcols < 32 || gcols > kMaxK ||
+        nb * gcols + nkc * 64 > 512 ||
+        ngroup < 1 || ngroup > kMaxGroupsStat || n < 1 || gs0[0] != 0 || gs0[ngroup] > kMaxSegStat)
+        return cudaErrorNotSupported;
+    for (int gi = 0; gi < ngroup; ++gi) {
+        if (gs0[gi + 1] <= gs0[gi]) return cudaErrorNotSupported;
+        int col = gi * gcols;
+        for (int q = gs0[gi]; q < gs0[gi + 1]; ++q) {
+            if (seg[q].col0 != col || seg[q].ncol % 32 != 0 || seg[q].k < 1 || seg[q].k > seg[q].ncol)
+                return cudaErrorNotSupported;
+            col += seg[q].ncol;
+        }
+        if (col > (gi + 1) * gcols) return cudaErrorNotSupported;
+    }
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem = tc_smem_bytes(gcols, D, STAT_SB, STAT_SF, ngroup * gcols, kMaxSegStat);
+    if (smem > (size_t)optin) return cudaErrorNotSupported;
+    const int krows = ngroup * gcols;
+    CUtensorMap tmA, tmBhi, tmBlo;
+    if ((e = make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)D, (uint64_t)n, (uint64_t)D * 4, 32,
+                      TM)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&tmBhi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.chi, (uint64_t)D, (uint64_t)krows,
+                      (uint64_t)D * 2, KC, (uint32_t)gcols)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&tmBlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.clo, (uint64_t)D, (uint64_t)krows,
+                      (uint64_t)D * 2, KC, (uint32_t)gcols)) != cudaSuccess)
+        return e;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.D = D;
+    a.krows = krows;
+    a.npad = gcols;
+    a.nkc = nkc;
+    a.sb = STAT_SB;
+    a.sf = STAT_SF;
+    a.nb = nb;
+    a.sa = nkc;                                            // chunk kc in A stage kc
+    a.pf = 0;
+    a.ntiles = (n + TM - 1) / TM;
+    a.p = p;
+    a.nseg = gs0[ngroup];
+    for (int q = 0; q < a.nseg; ++q) a.seg[q] = seg[q];
+    a.ngroup = ngroup;
+    for (int gi = 0; gi <= ngroup; ++gi) a.gs0[gi] = gs0[gi];
+    const long long grid = a.ntiles < sms ? a.ntiles : sms;
+    e = cudaFuncSetAttribute(assign_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    assign_tc_kernel<true, true><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
     return cudaGetLastError();
 }
 

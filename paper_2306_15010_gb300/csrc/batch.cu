@@ -29,7 +29,8 @@ struct GroupSrc {
 };
 
 // Group codebook: row r of segment q is centroid r - col0[q] of codebook q; its padding rows
-// repeat centroid 0 (the contraction kernel never picks a padding column).
+// repeat centroid 0, and rows past the last segment are zero (the contraction kernel never
+// picks a padding column).
 __global__ void group_codebook_kernel(GroupSrc g, int D, float *__restrict__ Cg)
 {
     const int r = blockIdx.x;
@@ -40,8 +41,7 @@ __global__ void group_codebook_kernel(GroupSrc g, int D, float *__restrict__ Cg)
             const int li = r - g.col0[q];
             src = g.C[q] + (size_t)(li < g.k[q] ? li : 0) * D;
         }
-    if (!src) return;
-    for (int d = threadIdx.x; d < D; d += blockDim.x) Cg[(size_t)r * D + d] = src[d];
+    for (int d = threadIdx.x; d < D; d += blockDim.x) Cg[(size_t)r * D + d] = src ? src[d] : 0.f;
 }
 
 struct Group {
@@ -56,8 +56,10 @@ struct BatchWs {
     std::vector<float *> gC;                  // per group slot: group codebook
     std::vector<CodebookPrep> gprep;          // per group slot: its prepared planes
     std::vector<uint8_t *> qlab;              // per template: the current query's NNF
-    unsigned *flcount;                        // kMaxSeg x 64 (counters and stats, one memset)
-    FlagList fl[kMaxSeg];
+    unsigned *flcount;                        // kMaxSegStat x 64 (counters and stats, one memset)
+    FlagList fl[kMaxSegStat];
+    float *sC;                                // stationary codebooks, every launch's groups in a row
+    CodebookPrep sprep;                       // their prepared planes (one common centring mean)
     FitWs fit;
     char *score_base;                         // integral-image workspace of one pair
     float *heat_scratch;                      // heatmap of one pair when the caller wants maxima only
@@ -103,14 +105,25 @@ BatchWs carve_batch(WsCursor &c, const vqnnf_image *q, int nq, const vqnnf_batch
         w.gprep.push_back(p);
     }
     for (int j = 0; j < nt; ++j) w.qlab.push_back(c.take<uint8_t>((size_t)n_max));
-    w.flcount = c.take<unsigned>((size_t)kMaxSeg * 64);
-    for (int s = 0; s < kMaxSeg; ++s) {
+    w.flcount = c.take<unsigned>((size_t)kMaxSegStat * 64);
+    for (int s = 0; s < kMaxSegStat; ++s) {
         FlagList &f = w.fl[s];
         f.count = w.flcount ? w.flcount + 64 * s : nullptr;
         f.stats = w.flcount ? reinterpret_cast<unsigned long long *>(f.count + 16) : nullptr;
         f.pix = c.take<unsigned>((size_t)n_max);
         f.mask = c.take<unsigned>((size_t)n_max * kMaskWords);
     }
+    // stationary codebooks: at most one 256-column group per template
+    const size_t srows = (size_t)nt * kGroupRows;
+    w.sC = c.take<float>(srows * D);
+    w.sprep.mean = c.take<float>((size_t)D);
+    w.sprep.cc = c.take<float>(srows * D);
+    w.sprep.chi = c.take<uint16_t>(srows * D);
+    w.sprep.clo = c.take<uint16_t>(srows * D);
+    w.sprep.nrm = c.take<float>(srows);
+    w.sprep.a = c.take<float>(srows);
+    w.sprep.v = c.take<float>(srows);
+    w.sprep.b = c.take<float>(srows);
     w.fit = carve_fit(c, l_max, D, k_max);
     // the largest integral-image layout over the templates (its size depends on the template)
     size_t sbytes = 0;
@@ -194,10 +207,144 @@ vqnnf_status check_plan(const vqnnf_batch_plan &p)
     if (p.group_cols != 128 && p.group_cols != 256) return VQNNF_EINVAL;
     if (p.sf != 0 && (p.sf < 2 || p.sf > 8 || p.sf % 2)) return VQNNF_EINVAL;
     if (p.pf < -1 || p.pf > 64) return VQNNF_EINVAL;
+    if (p.stationary != 0 && p.stationary != 1) return VQNNF_EINVAL;
     return VQNNF_OK;
 }
 
-const vqnnf_batch_plan kDefaultPlan = {256, 0, -1, 0};
+const vqnnf_batch_plan kDefaultPlan = {256, 0, -1, 1};
+
+// ---------------------------------------------------------------- stationary launches
+// Codebooks of at most 128 columns go to groups of 128 columns (first fit), wider ones to
+// groups of 256; each launch holds as many groups as its shared memory allows (and at most
+// kMaxSegStat codebooks); every launch's groups sit one after another in the concatenated
+// stationary codebook.
+struct StatLaunch {
+    int gcols, ngroup, row0;                  // group width, groups, first row in the codebook
+    std::vector<int> tj;                      // template of each segment, in group order
+    std::vector<int> gs0;                     // group g's segments: [gs0[g], gs0[g + 1])
+};
+
+bool stat_possible(int D)
+{
+    return D % 16 == 0 && (D + 63) / 64 <= 4 && stat_max_groups(D, 128) >= 1 && stat_max_groups(D, 256) >= 1;
+}
+
+std::vector<StatLaunch> make_stat_plan(const vqnnf_batch_template *t, int nt, int D)
+{
+    std::vector<StatLaunch> out;
+    int row = 0;
+    for (int gcols : {128, 256}) {
+        std::vector<int> js;
+        for (int j = 0; j < nt; ++j) {
+            const int nc = (t[j].k + 31) / 32 * 32;
+            if ((gcols == 128) == (nc <= 128)) js.push_back(j);
+        }
+        if (js.empty()) continue;
+        std::vector<Group> gs;                            // first fit into groups of gcols columns
+        for (int j : js) {
+            const int nc = (t[j].k + 31) / 32 * 32;
+            size_t g = 0;
+            while (g < gs.size() && (gs[g].nseg == kMaxSeg || gs[g].npad + nc > gcols)) ++g;
+            if (g == gs.size()) gs.push_back(Group{});
+            gs[g].tj[gs[g].nseg++] = j;
+            gs[g].npad += nc;
+        }
+        const int gmax = std::min(stat_max_groups(D, gcols), kMaxGroupsStat);
+        size_t gi = 0;
+        while (gi < gs.size()) {
+            StatLaunch L;
+            L.gcols = gcols;
+            L.row0 = row;
+            L.gs0.push_back(0);
+            while (gi < gs.size() && (int)L.gs0.size() - 1 < gmax &&
+                   (int)L.tj.size() + gs[gi].nseg <= kMaxSegStat) {
+                for (int q = 0; q < gs[gi].nseg; ++q) L.tj.push_back(gs[gi].tj[q]);
+                L.gs0.push_back((int)L.tj.size());
+                ++gi;
+            }
+            L.ngroup = (int)L.gs0.size() - 1;
+            row += L.ngroup * gcols;
+            out.push_back(L);
+        }
+    }
+    return out;
+}
+
+// The concatenated stationary codebook (group g of launch L at rows L.row0 + g * L.gcols) and
+// its prepared planes, centred on the mean of all its rows.
+vqnnf_status build_stat(const std::vector<StatLaunch> &plan, const vqnnf_batch_template *t, int D, BatchWs &w,
+                        cudaStream_t s)
+{
+    int rows = 0;
+    for (const StatLaunch &L : plan) {
+        for (int gi = 0; gi < L.ngroup; ++gi) {
+            GroupSrc src;
+            memset(&src, 0, sizeof(src));
+            int col = 0;
+            for (int q = L.gs0[gi]; q < L.gs0[gi + 1]; ++q) {
+                const int j = L.tj[q], e = q - L.gs0[gi];
+                src.col0[e] = col;
+                src.ncol[e] = (t[j].k + 31) / 32 * 32;
+                src.k[e] = t[j].k;
+                src.C[e] = w.C[j];
+                col += src.ncol[e];
+            }
+            src.nseg = L.gs0[gi + 1] - L.gs0[gi];
+            group_codebook_kernel<<<L.gcols, 128, 0, s>>>(src, D, w.sC + (size_t)(L.row0 + gi * L.gcols) * D);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        rows = L.row0 + L.ngroup * L.gcols;
+    }
+    if (rows == 0) return VQNNF_OK;
+    return from_cuda(launch_prep_codebook(w.sC, rows, D, VQNNF_PREC_BF16, w.sprep, s));
+}
+
+CodebookPrep prep_rows(const CodebookPrep &p, int row0, int D)
+{
+    CodebookPrep v = p;                                   // same centring mean
+    v.cc = p.cc + (size_t)row0 * D;
+    v.chi = p.chi + (size_t)row0 * D;
+    v.clo = p.clo + (size_t)row0 * D;
+    v.nrm = p.nrm + row0;
+    v.a = p.a + row0;
+    v.v = p.v + row0;
+    v.b = p.b + row0;
+    return v;
+}
+
+// NNF of query i under every codebook, each stationary launch reading the features once.
+vqnnf_status assign_query_stat(const vqnnf_image &qi, const std::vector<StatLaunch> &plan,
+                               const vqnnf_batch_template *t, int D, BatchWs &w, cudaStream_t s)
+{
+    const long long n = (long long)qi.H * qi.W;
+    for (const StatLaunch &L : plan) {
+        cudaError_t e = cudaMemsetAsync(w.flcount, 0, sizeof(unsigned) * 64 * kMaxSegStat, s);
+        if (e != cudaSuccess) return from_cuda(e);
+        std::vector<TcSeg> seg(L.tj.size());
+        for (int gi = 0; gi < L.ngroup; ++gi) {
+            int col = gi * L.gcols;
+            for (int q = L.gs0[gi]; q < L.gs0[gi + 1]; ++q) {
+                const int j = L.tj[q];
+                seg[q].col0 = col;
+                seg[q].ncol = (t[j].k + 31) / 32 * 32;
+                seg[q].k = t[j].k;
+                seg[q].labels = w.qlab[j];
+                seg[q].fl = w.fl[q];
+                col += seg[q].ncol;
+            }
+        }
+        e = launch_assign_bf16_stat(qi.X, n, D, prep_rows(w.sprep, L.row0, D), L.ngroup, L.gcols, seg.data(),
+                                    L.gs0.data(), s);
+        if (e != cudaSuccess) return from_cuda(e);
+        for (size_t q = 0; q < L.tj.size(); ++q) {
+            const int j = L.tj[q];
+            e = launch_rescore(qi.X, n, D, w.C[j], t[j].k, w.qlab[j], w.fl[q], s);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    return VQNNF_OK;
+}
 
 struct Banks {
     std::vector<BankSpec> bs;
@@ -332,12 +479,21 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
     WsCursor c{static_cast<char *>(ws), 0};
     BatchWs w = carve_batch(c, q, nq, t, nt, D, G);
     if ((st = fit_templates(t, nt, D, iters, seed, banks, w, s)) != VQNNF_OK) return st;
-    const std::vector<Group> groups = make_groups(t, nt, p.group_cols);
-    if ((st = build_groups(groups, t, D, w, s)) != VQNNF_OK) return st;
+    const bool stat = p.stationary && stat_possible(D);
+    std::vector<Group> groups;
+    std::vector<StatLaunch> splan;
+    if (stat) {
+        splan = make_stat_plan(t, nt, D);
+        if ((st = build_stat(splan, t, D, w, s)) != VQNNF_OK) return st;
+    } else {
+        groups = make_groups(t, nt, p.group_cols);
+        if ((st = build_groups(groups, t, D, w, s)) != VQNNF_OK) return st;
+    }
     WGridSpec no_wgrid;
     memset(&no_wgrid, 0, sizeof(no_wgrid));
     for (int i = 0; i < nq; ++i) {
-        if ((st = assign_query(q[i], groups, t, D, p, w, s)) != VQNNF_OK) return st;
+        st = stat ? assign_query_stat(q[i], splan, t, D, w, s) : assign_query(q[i], groups, t, D, p, w, s);
+        if (st != VQNNF_OK) return st;
         for (int j = 0; j < nt; ++j) {
             WsCursor sc{w.score_base, 0};
             ScoreWs sw = carve_score(sc, q[i].H, q[i].W, t[j].k, t[j].h, t[j].w);
@@ -380,18 +536,36 @@ vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_te
     vqnnf_batch_plan best_plan = kDefaultPlan;
     // time one candidate: assignment of the largest query, second of two runs
     auto time_plan = [&](const vqnnf_batch_plan &cand, float &ms) -> vqnnf_status {
-        const std::vector<Group> groups = make_groups(t, nt, cand.group_cols);
-        vqnnf_status r = build_groups(groups, t, D, w, s);
+        const bool stat = cand.stationary && stat_possible(D);
+        std::vector<Group> groups;
+        std::vector<StatLaunch> splan;
+        vqnnf_status r;
+        if (stat) {
+            splan = make_stat_plan(t, nt, D);
+            r = build_stat(splan, t, D, w, s);
+        } else {
+            groups = make_groups(t, nt, cand.group_cols);
+            r = build_groups(groups, t, D, w, s);
+        }
         for (int rep = 0; rep < 2 && r == VQNNF_OK; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) return VQNNF_ECUDA;
-            if ((r = assign_query(q[ib], groups, t, D, cand, w, s)) != VQNNF_OK) return r;
+            r = stat ? assign_query_stat(q[ib], splan, t, D, w, s) : assign_query(q[ib], groups, t, D, cand, w, s);
+            if (r != VQNNF_OK) return r;
             if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                 cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
                 return VQNNF_ECUDA;
         }
         return r;
     };
+    if (stat_possible(D)) {
+        const vqnnf_batch_plan cand = {256, 0, -1, 1};
+        float ms = 0.f;
+        st = time_plan(cand, ms);
+        if (st == VQNNF_EUNSUPPORTED) st = VQNNF_OK;
+        else if (st == VQNNF_OK) { best = ms; best_plan = cand; }
+    }
     for (int gc : {128, 256}) {
+        if (st != VQNNF_OK) break;
         for (int sf : {4, 6, 8}) {
             for (int pf : {0, 8}) {
                 const vqnnf_batch_plan cand = {gc, sf, pf, 0};

@@ -36,6 +36,8 @@ struct FlagList {
 // columns [col0, col0 + ncol) of the prepared codebook, ncol a multiple of 32, the first k of
 // them real centroids; its labels and its flag list (candidate masks relative to col0).
 constexpr int kMaxSeg = 8;
+constexpr int kMaxSegStat = 64;     // segments of one stationary launch (all its groups)
+constexpr int kMaxGroupsStat = 63;  // groups of one stationary launch
 struct TcSeg {
     int col0, ncol, k;
     uint8_t *labels;
@@ -55,6 +57,15 @@ cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k,
 // padding rows included); the sum of the segments' ncol is at most 256.
 cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const CodebookPrep &p, int krows,
                                    const TcSeg *seg, int nseg, int sf, int pf, cudaStream_t s);
+// Several groups of codebooks against one tile of features read once (the tile's BF16 operand
+// stays in tensor memory while every group's centroids stream past): p holds ngroup * gcols
+// prepared rows, group g at rows g * gcols; seg[] lists every group's segments with absolute
+// columns (group g's segments are seg[gs0[g] .. gs0[g + 1]), inside [g * gcols, (g + 1) * gcols)).
+// D <= 256; gcols <= 128 (double-buffered accumulators) or 256 (single).
+cudaError_t launch_assign_bf16_stat(const float *X, long long n, int D, const CodebookPrep &p, int ngroup,
+                                    int gcols, const TcSeg *seg, const int *gs0, cudaStream_t s);
+// Largest number of groups of gcols columns one stationary launch holds (shared memory).
+int stat_max_groups(int D, int gcols);
 cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
                            uint8_t *labels, FlagList fl, cudaStream_t s);
 cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s);

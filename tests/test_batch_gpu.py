@@ -5,8 +5,10 @@
   several codebooks changes no label, count or heatmap value.
 * Every pair against the FP64 oracle: labels outside the near-tie band, heatmap within
   1e-4 of max|H| (the whole-path tolerance of the single-pair tests), argmax a maximum.
-* Plans (128 or 256 shared columns, feature boxes in flight, L2 prefetch) give identical
-  results; the tuner returns one of its candidates; the call captures into a CUDA graph.
+* Plans (one launch per group with 128 or 256 shared columns, feature boxes in flight, L2
+  prefetch; or the stationary launches, features read once per tile for every group) give
+  identical results; the tuner returns one of its candidates; the call captures into a CUDA
+  graph.
 """
 import numpy as np
 import pytest
@@ -105,20 +107,23 @@ def test_batch_against_oracle(vq, case, single):
             assert ref[y, x] >= ref.max() - 2e-4 * scale, (i, j)
 
 
-@pytest.mark.parametrize("gc,sf,pf", [(128, 0, -1), (256, 4, 0), (256, 8, 8), (128, 6, 0)])
-def test_batch_plans_agree(vq, case, single, gc, sf, pf):
-    heats, ams = _run(vq, case, vq.BatchPlan(gc, sf, pf))
+@pytest.mark.parametrize("gc,sf,pf,stat", [(128, 0, -1, 0), (256, 4, 0, 0), (256, 8, 8, 0), (128, 6, 0, 0),
+                                           (256, 0, -1, 1)])
+def test_batch_plans_agree(vq, case, single, gc, sf, pf, stat):
+    """One launch per group (any group width, feature stages, prefetch) and the stationary
+    launches (every group against features read once per tile) give identical results."""
+    heats, ams = _run(vq, case, vq.BatchPlan(gc, sf, pf, stat))
     s_heat, s_am, _, _ = single
     for i in range(len(QUERIES)):
         for j in range(len(TEMPLATES)):
-            assert torch.equal(heats[i][j].cpu(), s_heat[i, j]), (gc, sf, pf, i, j)
+            assert torch.equal(heats[i][j].cpu(), s_heat[i, j]), (gc, sf, pf, stat, i, j)
             assert ams[i, j].cpu().tolist() == s_am[i, j].tolist()
 
 
 def test_batch_tune_and_maxima_only(vq, case, single):
     qs, ts, ks = case
     plan = vq.vqnnf_batch_tune([q.X.cuda() for q in qs], [T.cuda() for T in ts], ks, ITERS, SEED, G)
-    assert plan.group_cols in (128, 256) and plan.sf in (4, 6, 8) and plan.pf in (0, 8)
+    assert plan.stationary == 1 or (plan.group_cols in (128, 256) and plan.sf in (4, 6, 8) and plan.pf in (0, 8))
     heats, ams = _run(vq, case, plan, heat=False)
     assert heats is None
     _, s_am, _, _ = single
