@@ -271,8 +271,12 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     const int nsegcap = STAT ? kMaxSegStat : kMaxSeg;
     uint8_t *f32s = base;                                  // SF x 16 KB
     uint8_t *bs = f32s + SF * F32_BOX;                     // SB x (hi, lo)
-    float *cn = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
-    float4 *colc = reinterpret_cast<float4 *>(cn + ncols); // per column {||c*||^2, a, v, b}
+    // per column {||c*||^2, a, v, b}; cn[c * CS] = ||c*||^2 (the stationary mode keeps no
+    // separate copy of it, to leave shared memory for centroid stages)
+    constexpr int CS = STAT ? 4 : 1;
+    float *cn0 = reinterpret_cast<float *>(bs + SB * 2 * B_PLANE);
+    float4 *colc = reinterpret_cast<float4 *>(cn0 + (STAT ? 0 : ncols));
+    const float *cn = STAT ? reinterpret_cast<const float *>(colc) : cn0;
     float *mean = reinterpret_cast<float *>(colc + ncols); // roundup(D, 64)
     float *norms = mean + nkc * KC;                        // [2 buf][4 quarters][128]
     uint32_t *maskbuf = reinterpret_cast<uint32_t *>(norms + 2 * 4 * TM);   // [128][8]
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         }
         const int jc = j < g.krows ? j : g.krows - 1;
         const float nrm = ok ? g.p.nrm[jc] : FLT_MAX;     // padding columns never win nor qualify
-        cn[j] = nrm;
+        if constexpr (!STAT) cn0[j] = nrm;
         colc[j] = make_float4(nrm, ok ? g.p.a[jc] : 0.f, ok ? g.p.v[jc] : 0.f, ok ? g.p.b[jc] : 0.f);
     }
     // segment table
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float sc = fmaf(-2.0f, v[j], cn[c0 + j]);
+                    const float sc = fmaf(-2.0f, v[j], cn[(c0 + j) * CS]);
                     if (sc < sm[j & 3]) { sm[j & 3] = sc; am[j & 3] = c0 + j; }
                 }
             }
@@ -616,7 +620,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                 tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
                 uint32_t maybe = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[c0 + j]) <= lim) << j;
+                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[(c0 + j) * CS]) <= lim) << j;
                 const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
                 uint32_t word = own;
                 if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
@@ -745,13 +749,13 @@ cudaError_t make_map(CUtensorMap *m, CUtensorMapDataType dt, const void *ptr, ui
 
 // ncols: prepared columns held per column (npad, or ngroup * npad when stationary); nsegcap:
 // capacity of the segment table
-size_t tc_smem_bytes(int npad, int D, int sb, int sf, int ncols = 0, int nsegcap = kMaxSeg)
+size_t tc_smem_bytes(int npad, int D, int sb, int sf, int ncols = 0, int nsegcap = kMaxSeg, bool stat = false)
 {
     const int nkc = (D + KC - 1) / KC;
     if (ncols == 0) ncols = npad;
     size_t b = 1024;                                       // alignment slack
     b += (size_t)sf * F32_BOX + (size_t)sb * 2 * npad * 128;
-    b += sizeof(float) * (5 * (size_t)ncols + (size_t)nkc * KC + 8 * TM);
+    b += sizeof(float) * ((stat ? 4 : 5) * (size_t)ncols + (size_t)nkc * KC + 8 * TM);
     b += sizeof(uint32_t) * TM * kMaskWords;
     b += (sizeof(float4) + sizeof(TcSeg)) * nsegcap;
     b += sizeof(uint64_t) * (2 * sf + 2 * kMaxSA + 2 * kMaxSB + 8 + 1) + 16;   // barriers, TMEM slot, abort flag
@@ -839,8 +843,10 @@ cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const Cod
 }
 
 // Stationary mode: two FP32 feature boxes in flight (the features are read once per tile, then
-// every group's MMAs run on them) and two centroid stages.
-constexpr int STAT_SF = 2, STAT_SB = 2;
+// every group's MMAs run on them); four centroid stages for groups of 128 columns, two for 256
+// (twice the MMA work per stage).
+constexpr int STAT_SF = 2;
+int stat_sb(int gcols) { return gcols <= 128 ? 4 : 2; }
 
 int stat_max_groups(int D, int gcols)
 {
@@ -849,7 +855,8 @@ int stat_max_groups(int D, int gcols)
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int gmax = 0;
     for (int ng = 1; ng <= kMaxGroupsStat; ++ng)
-        if (tc_smem_bytes(gcols, D, STAT_SB, STAT_SF, ng * gcols, kMaxSegStat) <= (size_t)optin) gmax = ng;
+        if (tc_smem_bytes(gcols, D, stat_sb(gcols), STAT_SF, ng * gcols, kMaxSegStat, true) <= (size_t)optin)
+            gmax = ng;
     return gmax;
 }
 
@@ -879,7 +886,7 @@ cudaError_t launch_assign_bf16_stat(const float *X, long long n, int D, const Co
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = tc_smem_bytes(gcols, D, STAT_SB, STAT_SF, ngroup * gcols, kMaxSegStat);
+    const size_t smem = tc_smem_bytes(gcols, D, stat_sb(gcols), STAT_SF, ngroup * gcols, kMaxSegStat, true);
     if (smem > (size_t)optin) return cudaErrorNotSupported;
     const int krows = ngroup * gcols;
     CUtensorMap tmA, tmBhi, tmBlo;
@@ -899,7 +906,7 @@ cudaError_t launch_assign_bf16_stat(const float *X, long long n, int D, const Co
     a.krows = krows;
     a.npad = gcols;
     a.nkc = nkc;
-    a.sb = STAT_SB;
+    a.sb = stat_sb(gcols);
     a.sf = STAT_SF;
     a.nb = nb;
     a.sa = nkc;                                            // chunk kc in A stage kc
