@@ -582,60 +582,103 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             // max ||c_j*|| (cn = ||c*||^2 in FP32) and max ||c_j*||^2, with margins
             const float cnorm_max = MULTI ? sqrtf(mx.x) * 1.0001f : cnorm0;
             const float nrm_max = MULTI ? mx.x * 1.0001f : nrm0;
-            // pass 1: smallest score of the segment, lowest column on ties, as four
-            // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
-            float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
-            int am[4] = {cb, cb, cb, cb};
-            for (int c0 = cb; c0 < ce; c0 += 32) {
+            int cnt = 0, last = 0, amin = cb;
+            if (STAT && ce - cb == 32) {
+                // a one-block segment (k <= 32): both passes read the same registers, one
+                // tensor-memory load instead of two
                 float v[32];
-                tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+                tc_ld32(taddr + (uint32_t)(cb - cshift), v);
+                float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+                int am[4] = {cb, cb, cb, cb};
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float sc = fmaf(-2.0f, v[j], cn[(c0 + j) * CS]);
-                    if (sc < sm[j & 3]) { sm[j & 3] = sc; am[j & 3] = c0 + j; }
+                    const float sc = fmaf(-2.0f, v[j], cn[(cb + j) * CS]);
+                    if (sc < sm[j & 3]) { sm[j & 3] = sc; am[j & 3] = cb + j; }
                 }
-            }
-            float smin = sm[0];
-            int amin = am[0];
+                float smin = sm[0];
+                amin = am[0];
 #pragma unroll
-            for (int q = 1; q < 4; ++q)
-                if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
-            // U, the upper end of column amin's interval, bounds the smallest distance from
-            // above, so the nearest column j has s_j - B_j <= U.
-            const float4 ca = colc[amin];
-            const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
-            // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
-            // contraction's own error, so Bmax >= every B_j of this pixel in the segment (the
-            // float evaluation is monotone).  The nearest column has s_j <= U + B_j <= U + Bmax;
-            // the limit U + 2 Bmax also covers the rounding of that sum (u |U| < Bmax / 2
-            // because Bmax >= 4u |smin|).  A 32-column block where no lane has a column under
-            // the limit besides amin needs no per-column interval test: its only candidate is
-            // amin.
-            const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
-            const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
-            const float lim = U + 2.0f * Bmax;
-            int cnt = 0, last = amin;
-            for (int c0 = cb; c0 < ce; c0 += 32) {
-                float v[32];
-                tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+                for (int q = 1; q < 4; ++q)
+                    if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
+                const float4 ca = colc[amin];
+                const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+                const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
+                const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
+                const float lim = U + 2.0f * Bmax;
                 uint32_t maybe = 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[(c0 + j) * CS]) <= lim) << j;
-                const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[(cb + j) * CS]) <= lim) << j;
+                const uint32_t own = 1u << (amin & 31);
                 uint32_t word = own;
                 if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
                     word = 0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float4 c = colc[c0 + j];
+                        const float4 c = colc[cb + j];
                         const float sc = fmaf(-2.0f, v[j], c.x);
                         const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(sc), c.w))) * infl;
                         word |= (uint32_t)(sc - B <= U) << j;
                     }
                 }
-                cnt += __popc(word);
-                if (word) last = c0 + 31 - __clz(word);
-                maskbuf[r * kMaskWords + ((c0 - cb) >> 5)] = word;
+                cnt = __popc(word);
+                last = word ? cb + 31 - __clz(word) : amin;
+                maskbuf[r * kMaskWords] = word;
+            } else {
+                // pass 1: smallest score of the segment, lowest column on ties, as four
+                // interleaved running minima.  Padding columns hold +inf in cn (never chosen).
+                float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+                int am[4] = {cb, cb, cb, cb};
+                for (int c0 = cb; c0 < ce; c0 += 32) {
+                    float v[32];
+                    tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float sc = fmaf(-2.0f, v[j], cn[(c0 + j) * CS]);
+                        if (sc < sm[j & 3]) { sm[j & 3] = sc; am[j & 3] = c0 + j; }
+                    }
+                }
+                float smin = sm[0];
+                amin = am[0];
+#pragma unroll
+                for (int q = 1; q < 4; ++q)
+                    if (sm[q] < smin || (sm[q] == smin && am[q] < amin)) { smin = sm[q]; amin = am[q]; }
+                // U, the upper end of column amin's interval, bounds the smallest distance from
+                // above, so the nearest column j has s_j - B_j <= U.
+                const float4 ca = colc[amin];
+                const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+                // |s_j| <= ||c_j*||^2 + 2 ||x'|| ||c_j*|| (1 + 2^-6) + 1, with margin for the
+                // contraction's own error, so Bmax >= every B_j of this pixel in the segment (the
+                // float evaluation is monotone).  The nearest column has s_j <= U + B_j <= U + Bmax;
+                // the limit U + 2 Bmax also covers the rounding of that sum (u |U| < Bmax / 2
+                // because Bmax >= 4u |smin|).  A 32-column block where no lane has a column under
+                // the limit besides amin needs no per-column interval test: its only candidate is
+                // amin.
+                const float smax_abs = fmaf(2.0f * nx * 1.02f, cnorm_max, nrm_max) + 1.0f;
+                const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
+                const float lim = U + 2.0f * Bmax;
+                last = amin;
+                for (int c0 = cb; c0 < ce; c0 += 32) {
+                    float v[32];
+                    tc_ld32(taddr + (uint32_t)(c0 - cshift), v);
+                    uint32_t maybe = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) maybe |= (uint32_t)(fmaf(-2.0f, v[j], cn[(c0 + j) * CS]) <= lim) << j;
+                    const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                    uint32_t word = own;
+                    if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
+                        word = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float4 c = colc[c0 + j];
+                            const float sc = fmaf(-2.0f, v[j], c.x);
+                            const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(sc), c.w))) * infl;
+                            word |= (uint32_t)(sc - B <= U) << j;
+                        }
+                    }
+                    cnt += __popc(word);
+                    if (word) last = c0 + 31 - __clz(word);
+                    maskbuf[r * kMaskWords + ((c0 - cb) >> 5)] = word;
+                }
             }
             for (int w = (ce - cb) >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
             if (release) {                               // every accumulator of the buffer read
