@@ -40,11 +40,11 @@ OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,862,016 + 4,998,400 bytes),
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,954,432 + 5,192,192 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2147862016 + 4998400) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "b489483627cd9c6e1a203d81920e5cb4db3d8c7a708669f5be9115375c0fdd70"
+TC_TRAFFIC_PER_PX = (2147954432 + 5192192) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "d2d644ec7e70dddd8450fd4488401cf0a6c5b050ce2a54abe35eabea25ba5ce6"
 
 
 
