@@ -58,7 +58,7 @@ PRECS = ["fp32", "bf16"]
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("H,W,D,k", [
-    (256, 256, 64, 16),      # config-1 query
+    (256, 256, 64, 16),      # the small 256 x 256 workload
     (129, 67, 64, 16),       # ragged tail of the 128-pixel tile
     (33, 50, 512, 128),      # headline depth and codebook size
     (40, 41, 16, 8),
