@@ -11,7 +11,8 @@ Inputs are generated on the device from fixed seeds and stay resident (8 GiB of 
 larger than L2, so no flush is needed between steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32] [--impl reference]
-                  [--query-size S] [--no-compare] [--no-e2e] [--no-cpu-baseline]
+                  [--query-size S] [--no-compare] [--no-e2e] [--no-cpu-baseline] [--cpu-budget SEC]
+                  [--no-paper-bank] [--no-soft] [--soft-batch B] [--no-batch] [--batch-eager]
 
 ``--query-size`` shrinks the query to S x S (for profiler captures of the same kernels on a
 smaller case); the bench line itself is quoted on the default 2048.

@@ -19,6 +19,12 @@ Matching with Vector Quantized Nearest Neighbour Fields":
 * :func:`coarse_to_dilation`, :func:`coarse_direct` -- Algorithm 2 (dilation filter on the
   integral image) and the direct bin-weighted count it must reproduce.
 
+Every function above is pinned in ``tests/test_oracle_pins.py`` against exact brute force,
+closed forms and invariants.  One input is not: the layouts of the Haar coarse filters in the
+paper's bank (Sec. 4.2 "Filtering", supplementary c) are a reading, because the paper prints
+neither their signs nor their values.  For those banks the direct counts here are pinned, but
+parity of the bank itself is unpinned against the paper.
+
 The C source is compiled on first use (``gcc -O2 -fopenmp``) into ``oracle/liboracle.so``.
 """
 from __future__ import annotations
