@@ -28,8 +28,10 @@
  *            returns VQNNF_ECUDA.  Bounded device-side waits that give up record
  *            VQNNF_ETIMEOUT in a device error word that vqnnf_last_device_error() reads.
  *            No call aborts the process or traps on the device.
- * Threads.   The library keeps no host state: calls from several host threads on
- *            different streams are independent.
+ * Threads.   Calls from several host threads on different streams are independent, with
+ *            two exceptions, both process-wide: the profiling events of
+ *            vqnnf_set_kernel_events (set under a lock), and the one device scratch area
+ *            of vqnnf_assign_noalloc, which overlapping calls must not share.
  * Ties.      Nearest-neighbour ties go to the lowest centroid index; the heatmap maximum
  *            goes to the lowest row-major (y, then x) window.
  */

@@ -194,3 +194,45 @@ def test_match_host_workspace_and_refusals(lib):
     assert call(am=None) == _lib.EINVAL
     assert call(ws=None) == _lib.EINVAL
     assert call(wsb=256) == _lib.ENOMEM
+
+
+def test_soft_workspace_and_refusals(lib):
+    """Soft-VQ heatmap: workspace sizes and the host-side checks of both calls (nothing is
+    launched: every case below is refused before the stream is touched)."""
+    from paper_2306_15010_gb300 import _lib
+    nb = lib.vqnnf_soft_workspace_bytes(8, 512, 512, 256, 64, 64, 64, 3)
+    # at least the per-filter L1 maps of the backward pass: B x HO x WO x F float32
+    assert nb % 256 == 0 and nb >= 8 * 449 * 449 * 9 * 4
+    for args in [(0, 64, 64, 16, 8, 8, 8, 3),      # no query
+                 (1, 64, 64, 16, 8, 65, 8, 3),     # template taller than the query
+                 (1, 64, 64, 16, 0, 8, 8, 3),      # k = 0
+                 (1, 64, 64, 16, 8, 8, 8, 0),      # G = 0
+                 (1, 64, 64, 16, 8, 2, 8, 3)]:     # cells thinner than G
+        assert lib.vqnnf_soft_workspace_bytes(*args) == 0
+    fwd = lambda **kw: lib.vqnnf_soft_forward(
+        kw.get("Q", FAKE), kw.get("B", 2), 64, 64, kw.get("T", FAKE), 16, 16, kw.get("D", 32), FAKE,
+        kw.get("k", 16), ctypes.c_float(kw.get("tau", 0.1)), kw.get("G", 3), kw.get("wf", FAKE),
+        kw.get("heat", FAKE), kw.get("ws", FAKE), kw.get("wsb", 1 << 40), None)
+    assert fwd(Q=None) == _lib.EINVAL
+    assert fwd(T=None) == _lib.EINVAL
+    assert fwd(wf=None) == _lib.EINVAL
+    assert fwd(heat=None) == _lib.EINVAL
+    assert fwd(ws=FAKE + 16) == _lib.EINVAL           # misaligned workspace
+    assert fwd(tau=0.0) == _lib.EINVAL
+    assert fwd(tau=float("nan")) == _lib.EINVAL
+    assert fwd(tau=float("inf")) == _lib.EINVAL
+    assert fwd(wsb=256) == _lib.ENOMEM
+    assert fwd(k=129) == _lib.EUNSUPPORTED            # k > 128
+    assert fwd(D=513) == _lib.EUNSUPPORTED            # D > 512
+    assert fwd(k=128, D=512) == _lib.EUNSUPPORTED     # k D > 32768
+    assert fwd(G=5) == _lib.EUNSUPPORTED              # G > 4
+    bwd = lambda **kw: lib.vqnnf_soft_backward(
+        FAKE, 2, 64, 64, FAKE, 16, 16, 32, FAKE, 16, ctypes.c_float(kw.get("tau", 0.1)), 3, FAKE,
+        kw.get("dheat", FAKE), kw.get("dQ", FAKE), kw.get("dC", FAKE), kw.get("dwf", FAKE), FAKE,
+        kw.get("wsb", 1 << 40), None)
+    assert bwd(dheat=None) == _lib.EINVAL
+    assert bwd(dQ=None) == _lib.EINVAL
+    assert bwd(dC=None) == _lib.EINVAL
+    assert bwd(dwf=None) == _lib.EINVAL
+    assert bwd(tau=-1.0) == _lib.EINVAL
+    assert bwd(wsb=256) == _lib.ENOMEM
