@@ -234,6 +234,16 @@ const char *vqnnf_status_str(vqnnf_status s);
  * call. */
 vqnnf_status vqnnf_last_device_error(void *stream);
 
+/* Self-test of the failure detection above (the paper has no counterpart).  Enqueues on
+ * `stream` one single-thread kernel that waits on an mbarrier which nothing completes.  It
+ * uses the score kernels' bounded wait, but with a limit of `limit_cycles` SM cycles
+ * (1 .. 4,000,000,000, the kernels' own limit; else VQNNF_EINVAL, nothing enqueued).  The wait
+ * gives up, records VQNNF_ETIMEOUT in the device error word, and the kernel returns.  No copy
+ * is issued, so nothing is left in flight and the context stays usable.  The next
+ * vqnnf_last_device_error() on that stream returns VQNNF_ETIMEOUT and clears the word. */
+#define VQNNF_WAIT_LIMIT_CYCLES 4000000000LL
+vqnnf_status vqnnf_selftest_bounded_wait(long long limit_cycles, void *stream);
+
 /* ABI version of this header (major * 100 + minor). */
 int vqnnf_version(void);
 

@@ -14,6 +14,7 @@ from .api import (  # noqa: F401
     vqnnf_match_host,
     vqnnf_match_host_workspace_bytes,
     vqnnf_score,
+    vqnnf_selftest_bounded_wait,
     vqnnf_set_kernel_events,
     vqnnf_version,
     vqnnf_workspace_bytes,

@@ -28,6 +28,7 @@ SIGNATURES = {
     "vqnnf_score": (_i, [_vp, _i, _i, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _sz, _vp]),
     "vqnnf_status_str": (ctypes.c_char_p, [_i]),
     "vqnnf_last_device_error": (_i, [_vp]),
+    "vqnnf_selftest_bounded_wait": (_i, [ctypes.c_longlong, _vp]),
     "vqnnf_set_kernel_events": (_i, [_i, _vp, _vp]),
     "vqnnf_soft_workspace_bytes": (ctypes.c_size_t, [_i, _i, _i, _i, _i, _i, _i, _i]),
     "vqnnf_soft_forward": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _i, _vp, _i, ctypes.c_float, _i, _vp, _vp,

@@ -300,3 +300,11 @@ def vqnnf_set_kernel_events(op: int, start=None, stop=None) -> None:
 def vqnnf_last_device_error(stream=None) -> int:
     """Synchronise the stream and return (and clear) the device error status code."""
     return int(_lib.load().vqnnf_last_device_error(_stream(stream)))
+
+
+def vqnnf_selftest_bounded_wait(limit_cycles: int = 2_000_000, stream=None) -> None:
+    """Enqueue the bounded-wait self-test: a one-thread kernel whose mbarrier wait (nothing
+    completes it) gives up after ``limit_cycles`` SM cycles and records VQNNF_ETIMEOUT, which
+    the next :func:`vqnnf_last_device_error` on that stream returns."""
+    _lib.check("vqnnf_selftest_bounded_wait",
+               _lib.load().vqnnf_selftest_bounded_wait(int(limit_cycles), _stream(stream)))

@@ -681,6 +681,12 @@ vqnnf_status vqnnf_last_device_error(void *stream)
     return (err || err2) ? VQNNF_ETIMEOUT : VQNNF_OK;
 }
 
+vqnnf_status vqnnf_selftest_bounded_wait(long long limit_cycles, void *stream)
+{
+    if (limit_cycles < 1 || limit_cycles > VQNNF_WAIT_LIMIT_CYCLES) return VQNNF_EINVAL;
+    return from_cuda(launch_wait_selftest(limit_cycles, as_stream(stream)));
+}
+
 }  // extern "C"
 
 // ----------------------------------------------------------------------------------

@@ -38,18 +38,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait.  Returns false when the wait gave up; then *err is set to `code`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity, int *err, int code)
+// Bounded wait.  Returns false when the wait gave up after `limit` SM cycles; then *err is set
+// to `code`.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *b, uint32_t parity, int *err, int code, long long limit)
 {
     if (mbar_try(b, parity)) return true;
     const long long t0 = clock64();
     for (uint32_t i = 1;; ++i) {
         if (mbar_try(b, parity)) return true;
-        if ((i & 63) == 0 && clock64() - t0 > kWaitCycles) {
+        if ((i & 63) == 0 && clock64() - t0 > limit) {
             atomicExch(err, code);
             return false;
         }
     }
+}
+// The kernels' waits: bounded at kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity, int *err, int code)
+{
+    return mbar_wait_for(b, parity, err, code, kWaitCycles);
 }
 // Contiguous global -> shared copy completing on an mbarrier (16-byte aligned, size % 16 == 0).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)

@@ -633,6 +633,17 @@ __global__ void __launch_bounds__(STH) score_generic_kernel(const T *__restrict_
     }
 }
 
+// Self-test of the bounded waits: one thread waits on an mbarrier that nothing completes.  No
+// copy is issued, so nothing is in flight when the wait gives up after `limit` SM cycles and
+// records VQNNF_ETIMEOUT in the score kernels' error word.
+__global__ void wait_selftest_kernel(long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    ptx::mbar_init(&bar, 1);
+    ptx::fence_barrier_init();
+    (void)ptx::mbar_wait_for(&bar, 0, &g_score_error, (int)VQNNF_ETIMEOUT, limit);
+}
+
 __global__ void argmax_finish_kernel(const unsigned long long *amax, int WO, int32_t *out)
 {
     const unsigned idx = 0xFFFFFFFFu - (unsigned)(*amax & 0xFFFFFFFFull);
@@ -814,6 +825,12 @@ cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, 
                                           heat, amax, argmax_yx, s)
                : launch_score_t<uint32_t>(static_cast<const uint32_t *>(S), W, k, HO, WO, bs, gs, ws, tc,
                                           heat, amax, argmax_yx, s);
+}
+
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 1, 0, s>>>(limit_cycles);
+    return cudaGetLastError();
 }
 
 cudaError_t read_and_clear_score_error(int *out)

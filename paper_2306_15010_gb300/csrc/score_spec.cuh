@@ -78,5 +78,8 @@ cudaError_t launch_score(const void *S, bool u16, int W, int k, int HO, int WO, 
                          const GridSpec &gs, const WGridSpec &ws, const int32_t *tc, float *heat,
                          unsigned long long *amax, int32_t *argmax_yx, cudaStream_t s);
 cudaError_t read_and_clear_score_error(int *out);
+// One-thread kernel whose mbarrier wait gives up after limit_cycles (self-test of the bounded
+// waits; sets the error word that read_and_clear_score_error returns).
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s);
 
 }  // namespace vqnnf

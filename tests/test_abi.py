@@ -236,3 +236,11 @@ def test_soft_workspace_and_refusals(lib):
     assert bwd(dwf=None) == _lib.EINVAL
     assert bwd(tau=-1.0) == _lib.EINVAL
     assert bwd(wsb=256) == _lib.ENOMEM
+
+
+def test_selftest_wait_limit_refusals(lib):
+    """The bounded-wait self-test refuses limits outside 1 .. the kernels' own limit on the
+    host (nothing is enqueued)."""
+    from paper_2306_15010_gb300 import _lib
+    for bad in (0, -5, 4_000_000_001):
+        assert lib.vqnnf_selftest_bounded_wait(bad, None) == _lib.EINVAL
