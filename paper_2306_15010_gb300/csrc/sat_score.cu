@@ -16,9 +16,10 @@
 //   (2) band sums: per (band, strip), the column sums of the row prefixes (exact int32) =
 //       the band's carries plus the prefix along x of the band's per-column label counts;
 //   (3) exclusive prefix of the band sums over bands = S at every band's first row;
-//   (4) one warp per (band, strip, 8 clusters) sweeps its band from there and writes S;
-//       each lane owns two columns, the row prefix inside the strip is ballots + popcounts.
-//       Adjacent warps take adjacent strips, so the rows they write are contiguous runs.
+//   (4) one warp per (band, strip, 32 clusters) sweeps its band from there and writes S;
+//       each lane owns one cluster and the strip's 64 columns of its plane (in registers),
+//       and walks the strip's labels once per row.  Adjacent warps take adjacent strips, so
+//       the rows they write are contiguous runs.
 //
 // Score: one block per (window row, 512 windows).  The corner rows of its windows are
 // staged in shared memory one cluster at a time by bulk copies (one per row segment,
@@ -37,7 +38,6 @@ namespace {
 __device__ int g_score_error = 0;
 
 constexpr int SW = 64;     // columns per strip (two per lane)
-constexpr int CGW = 8;     // clusters per warp in the sweep
 constexpr int BH = 64;     // rows per band
 
 // carry[(y * nS + s) * k + j] = #{x' < 64 s : label(y, x') = j}
@@ -111,82 +111,136 @@ __global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict
     }
 }
 
-// One warp per (band, strip, cluster group); lane l owns the two S columns 2l and 2l + 1 of
-// its 64-column strip (one 4-byte store per lane for the 16-bit table).  Starts from the
-// band's prefix and writes its S rows.
+// One warp per (band, strip, 32 clusters); lane l owns cluster j = 32 cg + l and keeps the
+// band's running S values of the strip's 64 columns in registers.  Per row the strip's labels
+// are staged in shared memory (two bytes per lane, double-buffered) and read back whole by
+// every lane; the lane walks the 64 columns once, adding its row prefix (the carry plus one
+// for every earlier column labelled j) to each column's value.  The finished row of its plane
+// goes to a padded shared-memory row (conflict-free 16-byte stores) and from there to global
+// memory as one bulk copy, double-buffered: stores of 32 lanes to 32 different planes would
+// otherwise each touch a different line.  Columns past the image carry a label byte that no
+// lane of the warp owns, so they repeat the value of column W.
 template <typename T>
-__device__ __forceinline__ void store_pair(T *dst, int a, int b);
+struct SatSweep {
+    static constexpr int warps = sizeof(T) == 2 ? 4 : 2;        // warps per block
+    static constexpr int pitch = SW * (int)sizeof(T) + 16;       // staged row bytes (padded)
+};
+
+template <typename T>
+__device__ __forceinline__ void pack_row(uint8_t *dst, const int (&acc)[SW]);
 template <>
-__device__ __forceinline__ void store_pair<uint16_t>(uint16_t *dst, int a, int b)
+__device__ __forceinline__ void pack_row<uint16_t>(uint8_t *dst, const int (&acc)[SW])
 {
-    *reinterpret_cast<uint32_t *>(dst) = ((uint32_t)a & 0xFFFFu) | ((uint32_t)b << 16);
+#pragma unroll
+    for (int g = 0; g < SW / 8; ++g)
+        reinterpret_cast<uint4 *>(dst)[g] = make_uint4(__byte_perm(acc[8 * g], acc[8 * g + 1], 0x5410),
+                                                       __byte_perm(acc[8 * g + 2], acc[8 * g + 3], 0x5410),
+                                                       __byte_perm(acc[8 * g + 4], acc[8 * g + 5], 0x5410),
+                                                       __byte_perm(acc[8 * g + 6], acc[8 * g + 7], 0x5410));
 }
 template <>
-__device__ __forceinline__ void store_pair<uint32_t>(uint32_t *dst, int a, int b)
+__device__ __forceinline__ void pack_row<uint32_t>(uint8_t *dst, const int (&acc)[SW])
 {
-    *reinterpret_cast<uint2 *>(dst) = make_uint2((uint32_t)a, (uint32_t)b);
+#pragma unroll
+    for (int g = 0; g < SW / 4; ++g)
+        reinterpret_cast<uint4 *>(dst)[g] = make_uint4((uint32_t)acc[4 * g], (uint32_t)acc[4 * g + 1],
+                                                       (uint32_t)acc[4 * g + 2], (uint32_t)acc[4 * g + 3]);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) sat_write_kernel(const uint8_t *__restrict__ lab, int H, int W,
-                                                        int k, int P, int nS, int nB,
-                                                        const int *__restrict__ carry,
-                                                        const int *__restrict__ bandsum, T *__restrict__ S)
+__global__ void __launch_bounds__(32 * SatSweep<T>::warps, 4) sat_write_kernel(
+    const uint8_t *__restrict__ lab, int H, int W, int k, int P, int nS, int nB, const int *__restrict__ carry,
+    const int *__restrict__ bandsum, T *__restrict__ S)
 {
-    const int lane = threadIdx.x & 31;
-    const int ncg = (k + CGW - 1) / CGW;
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (gw >= (long long)nB * nS * ncg) return;
-    const int s = (int)(gw % nS);                        // adjacent warps: adjacent strips
+    constexpr int NW = SatSweep<T>::warps, PITCH = SatSweep<T>::pitch;
+    __shared__ __align__(16) uint8_t srow[NW][2][SW];
+    __shared__ __align__(16) uint8_t sout[NW][2][32][PITCH];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int ncg = (k + 31) >> 5;
+    const long long gw = (long long)blockIdx.x * NW + wi;
+    if (gw >= (long long)nB * nS * ncg) return;              // uniform over the warp
+    const int s = (int)(gw % nS);                            // adjacent warps: adjacent strips
     const int cg = (int)((gw / nS) % ncg);
     const int b = (int)(gw / ((long long)ncg * nS));
-    const int x = s * SW + 2 * lane;      // first of the two S columns owned by this lane
-    const bool xin = x < P;               // P is even, so x + 1 < P as well
-    const unsigned lt = (1u << lane) - 1u;
+    const int j = cg * 32 + lane;                            // < 256: k <= 256
+    const bool jin = j < k;
+    const int jc = jin ? j : k - 1;                          // clamped (every address in bounds)
+    const int x0 = s * SW;
+    const int ncolv = min(SW, P - x0);                       // S columns of the strip: a multiple of 8
+    const uint32_t row_bytes = (uint32_t)(ncolv * (int)sizeof(T));   // a multiple of 16
     const int y0 = b * BH, y1 = min(H, y0 + BH);
-    int acc0[CGW], acc1[CGW];
+    const uint32_t fill = (uint32_t)(((cg + 1) * 32) & 0xFF);   // outside [32 cg, 32 cg + 31]
+    const uint32_t jj = (uint32_t)j * 0x01010101u;
+    // S at the band's first row: the exclusive prefix of the band sums
+    int acc[SW];
+    {
+        const int *src = bandsum + ((size_t)b * k + jc) * P + x0;
 #pragma unroll
-    for (int q = 0; q < CGW; ++q) {
-        const int j = cg * CGW + q;
-        const int jc = min(j, k - 1), xc = min(x, P - 2);      // clamped addresses
-        const int2 v = *reinterpret_cast<const int2 *>(&bandsum[((size_t)b * k + jc) * P + xc]);
-        const bool in = j < k && xin;
-        acc0[q] = in ? v.x : 0;
-        acc1[q] = in ? v.y : 0;
-        if (b == 0 && in) store_pair<T>(&S[(size_t)j * P + x], 0, 0);   // row 0 of S
+        for (int g = 0; g < SW / 4; ++g) {
+            int4 v = make_int4(0, 0, 0, 0);
+            if (4 * g < ncolv) v = *reinterpret_cast<const int4 *>(src + 4 * g);
+            acc[4 * g] = v.x;
+            acc[4 * g + 1] = v.y;
+            acc[4 * g + 2] = v.z;
+            acc[4 * g + 3] = v.w;
+        }
     }
-    const int jl = min(cg * CGW + (lane & (CGW - 1)), k - 1);
-    const bool jlin = lane < CGW && cg * CGW + lane < k;
-    // labels and carry of the next row are loaded one row ahead
-    const int xa = x, xb = x + 1;
-    int la_n = 0, lb_n = 0, c_n = 0;
+    // row yrow of this lane's plane, through staging buffer bsel; a buffer is rewritten only
+    // once the copy committed two rows earlier has read it
+    auto emit = [&](int yrow, int bsel) {
+        if (!jin) return;
+        uint8_t *st = &sout[wi][bsel][lane][0];
+        ptx::bulk_wait_read<1>();
+        pack_row<T>(st, acc);
+        ptx::fence_proxy_async();
+        ptx::bulk_s2g(S + ((size_t)yrow * k + j) * P + x0, st, row_bytes);
+        ptx::bulk_commit();
+    };
+    if (b == 0) emit(0, 1);                                   // row 0 of S (all zero)
+    // labels and carry of the next row are loaded one row ahead; lane l stages columns
+    // x0 + 2l and x0 + 2l + 1
+    const int xa = x0 + 2 * lane;
+    uint32_t la_n = fill, lb_n = fill;
+    int c_n = 0;
     if (y0 < y1) {
         const uint8_t *row = lab + (size_t)y0 * W;
-        la_n = (int)row[min(xa, W - 1)];
-        lb_n = (int)row[min(xb, W - 1)];
-        c_n = carry[((size_t)y0 * nS + s) * k + jl];
+        if (xa < W) la_n = row[xa];
+        if (xa + 1 < W) lb_n = row[xa + 1];
+        c_n = carry[((size_t)y0 * nS + s) * k + jc];
     }
     for (int y = y0; y < y1; ++y) {
-        const int la = xa < W ? la_n : -1, lb = xb < W ? lb_n : -1;
-        const int cj = jlin ? c_n : 0;
+        uint8_t *buf = srow[wi][y & 1];
+        buf[2 * lane] = (uint8_t)la_n;
+        buf[2 * lane + 1] = (uint8_t)lb_n;
+        int rp = c_n;
         if (y + 1 < y1) {
             const uint8_t *row = lab + (size_t)(y + 1) * W;
-            la_n = (int)row[min(xa, W - 1)];
-            lb_n = (int)row[min(xb, W - 1)];
-            c_n = carry[((size_t)(y + 1) * nS + s) * k + jl];
+            la_n = xa < W ? row[xa] : fill;
+            lb_n = xa + 1 < W ? row[xa + 1] : fill;
+            c_n = carry[((size_t)(y + 1) * nS + s) * k + jc];
+        }
+        __syncwarp();
+        uint32_t wd[SW / 4];
+#pragma unroll
+        for (int q = 0; q < SW / 16; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(buf)[q];
+            wd[4 * q] = v.x;
+            wd[4 * q + 1] = v.y;
+            wd[4 * q + 2] = v.z;
+            wd[4 * q + 3] = v.w;
         }
 #pragma unroll
-        for (int q = 0; q < CGW; ++q) {
-            const int j = cg * CGW + q;
-            const unsigned ba = __ballot_sync(0xffffffffu, la == j);
-            const unsigned bb = __ballot_sync(0xffffffffu, lb == j);
-            // row prefix at column x: carry + both columns of every lower lane
-            const int r0 = __shfl_sync(0xffffffffu, cj, q) + __popc(ba & lt) + __popc(bb & lt);
-            acc0[q] += r0;
-            acc1[q] += r0 + (la == j ? 1 : 0);
-            if (j < k && xin) store_pair<T>(&S[((size_t)(y + 1) * k + j) * P + x], acc0[q], acc1[q]);
+        for (int q = 0; q < SW / 4; ++q) {
+            const uint32_t d = wd[q] ^ jj;                   // a zero byte: that column is labelled j
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[4 * q + u] += rp;
+                rp += (d & (0xFFu << (8 * u))) == 0u ? 1 : 0;
+            }
         }
+        emit(y + 1, y & 1);
     }
+    ptx::bulk_wait_read<0>();                                 // staging rows read before the block exits
 }
 
 // Exclusive prefix of the band sums over bands, per (cluster, column), in place.
@@ -692,9 +746,10 @@ cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, in
     band_sum_kernel<<<dim3(nS, nB), 256, csmem, s>>>(lab, H, W, k, P, nS, carry, bandsum);
     const long long kP = (long long)k * P;
     band_prefix_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, s>>>(bandsum, nB, kP);
-    const long long nwarps = (long long)nB * nS * ((k + CGW - 1) / CGW);
-    const unsigned blocks = (unsigned)((nwarps + 7) / 8);
-    sat_write_kernel<T><<<blocks, 256, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
+    const long long nwarps = (long long)nB * nS * ((k + 31) / 32);
+    constexpr int NW = SatSweep<T>::warps;
+    const unsigned blocks = (unsigned)((nwarps + NW - 1) / NW);
+    sat_write_kernel<T><<<blocks, 32 * NW, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
     return cudaGetLastError();
 }
 

@@ -205,7 +205,9 @@ def _check_heat(got_heat, got_am, ref_heat, rtol):
 @pytest.mark.parametrize("bank_name", ["grid2", "grid3", "grid3_nofull", "grid4", "full_only",
                                        "weighted"])
 @pytest.mark.parametrize("H,W,th,tw,k", [(96, 300, 37, 29, 11), (70, 64, 70, 64, 6),
-                                         (41, 260, 9, 5, 3)])
+                                         (41, 260, 9, 5, 3),
+                                         (80, 200, 20, 24, 45),      # two cluster groups, the second ragged
+                                         (66, 130, 16, 16, 256)])    # every label byte in use
 def test_score_from_oracle_labels(vq, bank_name, H, W, th, tw, k):
     r = np.random.default_rng(H + W)
     q = synth.query_map(H, W, 4, M=6, n_sp=max(8, H * W // 150), seed=H)
