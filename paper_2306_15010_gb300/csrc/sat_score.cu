@@ -3,7 +3,8 @@
 // Integral image (Supp. "Integral Image"; exclusive-prefix reading): for cluster j,
 //     S[y][j][x] = #{ (y', x') : y' < y, x' < x, label(y', x') = j },  0 <= y <= H, 0 <= x <= W
 // stored channel-planar: element (y, j, x) at (y * k + j) * P + x, P = W + 1 rounded up to a
-// multiple of 8 (16-byte rows for bulk copies).  A half-open rectangle's count is the
+// multiple of 64 (every 64-column strip of a row is whole, and a 16-bit strip row is one
+// 128-byte line).  A half-open rectangle's count is the
 // four-corner sum S(y1,x1) - S(y0,x1) - S(y1,x0) + S(y0,x0); a filter is a weighted sum of
 // such boxes, i.e. the dilation filter that Algorithm 2 builds on the integral image.
 //
@@ -851,7 +852,7 @@ size_t score_smem_bytes_for(size_t elem, const BankSpec &bs, const GridSpec &gs,
 }
 
 bool sat_is_u16(int th, int tw) { return (long long)th * tw <= 65535; }
-int sat_pitch(int W) { return (W + 1 + 7) / 8 * 8; }
+int sat_pitch(int W) { return (W + 1 + 63) / 64 * 64; }
 int sat_strips(int W) { return (W + 1 + SW - 1) / SW; }
 int sat_bands(int H) { return (H + BH - 1) / BH; }
 int score_ncol(int tw) { return (TXW + tw + 7) / 8 * 8; }
