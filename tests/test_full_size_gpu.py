@@ -1,6 +1,7 @@
-"""The whole path at the headline size (2048 x 2048 query, D = 512, k = 128, 128 x 128
-template, F = 10), run the way bench.py times it, against the FP64 oracle on what the
-oracle can compute one by one.
+"""The whole path at full size, run the way bench.py times it, against the FP64 oracle on
+what the oracle can compute one by one.  Two workloads: the headline one (2048 x 2048
+query, D = 512, k = 128, 128 x 128 template, F = 10) and the precision study's D = 1024
+variant (1024 x 1024 query, D = 1024, the same generator, codebook size and template).
 
 * codebook: bit-identical to the oracle's fit of the same template (BF16 and FP32 paths);
 * template labels: every pixel against the oracle (outside the 1e-6 near-tie band);
@@ -18,8 +19,12 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def run():
+# (H = W, D, superpixels): the superpixel count keeps the headline's superpixel size
+WORKLOADS = {"d512_2048": (2048, 512, 20000), "d1024_1024": (1024, 1024, 5000)}
+
+
+@pytest.fixture(scope="module", params=sorted(WORKLOADS))
+def run(request):
     from paper_2306_15010_gb300 import build
     build.build()
     import paper_2306_15010_gb300 as vq
@@ -27,6 +32,8 @@ def run():
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     cfg = dict(bench.HEADLINE)
+    side, D, n_sp = WORKLOADS[request.param]
+    cfg.update(H=side, W=side, D=D, n_sp=n_sp)
     q, T, info, bank = bench.make_workload(dev, cfg)
     s = torch.cuda.Stream(device=dev)
     out = {}

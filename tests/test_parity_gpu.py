@@ -61,6 +61,7 @@ PRECS = ["fp32", "bf16"]
     (256, 256, 64, 16),      # the small 256 x 256 workload
     (129, 67, 64, 16),       # ragged tail of the 128-pixel tile
     (33, 50, 512, 128),      # headline depth and codebook size
+    (21, 38, 1024, 128),     # the precision study's D = 1024 variant
     (40, 41, 16, 8),
     (17, 19, 32, 256),       # largest k (two 128-centroid passes)
     (9, 7, 4, 3),            # D = 4, partial k tile
