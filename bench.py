@@ -372,7 +372,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": kernels_per_step(cfg, args.prec) * K,
     }
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe)
+        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe, one_thread=True)
     return line
 
 
@@ -611,10 +611,11 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
     return out
 
 
-def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None):
-    """The FP64 oracle timed on bounded samples of the same workload, scaled to one step.
-    With ``pipe`` (the timed BF16 pipeline), this run's own results are also checked against
-    the oracle on the same samples."""
+def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=False):
+    """The FP64 oracle timed on bounded samples of the same workload, scaled to one step, on
+    all of the oracle's threads (and, with ``one_thread``, again on one thread).  With ``pipe``
+    (the timed BF16 pipeline), this run's own results are also checked against the oracle on
+    the same samples."""
     import numpy as np
     import oracle
     oracle.build()
@@ -624,12 +625,6 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None):
     L = cfg["H"] * cfg["W"]
     th, tw = cfg["th"], cfg["tw"]
     HO, WO = cfg["H"] - th + 1, cfg["W"] - tw + 1
-    t0 = time.perf_counter()
-    C = oracle.fit_codebook(Th, k, 1, cfg["fit_seed"])       # one Lloyd step
-    t_fit1 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    lab = oracle.assign(Xh, C)
-    t_asg = time.perf_counter() - t0
     px_asg = Xh.shape[0] * Xh.shape[1]
     # score sample: windows of a synthetic label field of the same size (labels for the
     # whole query would need the full assignment)
@@ -639,16 +634,35 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None):
     rng = np.random.default_rng(0)
     nwin = 64
     win = np.stack([rng.integers(0, HO, nwin), rng.integers(0, WO, nwin)], 1)
-    t0 = time.perf_counter()
-    oracle.score_at(ql, k, bank, tc, win)
-    t_sc = time.perf_counter() - t0
-    t_step = (t_fit1 * cfg["iters"] + t_asg * (L + th * tw) / px_asg
-              + t_sc * HO * WO / nwin)
+
+    def phases():
+        t0 = time.perf_counter()
+        C = oracle.fit_codebook(Th, k, 1, cfg["fit_seed"])   # one Lloyd step
+        t_fit1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.assign(Xh, C)
+        t_asg = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.score_at(ql, k, bank, tc, win)
+        t_sc = time.perf_counter() - t0
+        t_step = (t_fit1 * cfg["iters"] + t_asg * (L + th * tw) / px_asg + t_sc * HO * WO / nwin)
+        return t_step, {"fit_one_lloyd_step": round(t_fit1, 4), f"assign_{px_asg}_px": round(t_asg, 4),
+                        f"score_{nwin}_windows": round(t_sc, 4)}
+
+    threads = oracle.set_threads(0)                          # the count in effect, unchanged
+    t_step, ph = phases()
     out = {"value": round(L / t_step / 1e6, 6), "unit": "Mpix/s",
-           "cores": os.cpu_count(), "kind": "oracle",
+           "cores": threads, "kind": "oracle",
            "sample": (f"1 Lloyd step (x{cfg['iters']}), {px_asg} query pixels assigned, "
                       f"{nwin} windows scored; scaled to one full step"),
-           "step_s_estimate": round(t_step, 2)}
+           "step_s_estimate": round(t_step, 2), "phases_s": ph}
+    if one_thread:
+        prev = oracle.set_threads(1)
+        try:
+            t1, ph1 = phases()
+        finally:
+            oracle.set_threads(prev)
+        out["one_thread"] = {"value": round(L / t1 / 1e6, 6), "step_s_estimate": round(t1, 2), "phases_s": ph1}
     if pipe is not None:
         # this run's results on the same samples: the labels of the first 8 query rows under the
         # run's codebook (equal outside the oracle's near-tie band, relative gap < 1e-6), and the

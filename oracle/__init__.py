@@ -78,6 +78,8 @@ def _load():
             lib.oracle_kmeans_objective.argtypes = [_f32p, ctypes.c_int64, ctypes.c_int, _f32p,
                                                     ctypes.c_int]
             lib.oracle_kmeans_objective.restype = ctypes.c_double
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             lib.oracle_filter_counts.argtypes = [_i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _i32p, _i32p, _i64p]
             lib.oracle_filter_counts.restype = None
@@ -251,3 +253,9 @@ def coarse_direct(labels, wy: int, wx: int, cls: int, f_i, d_x: int, d_y: int) -
     r_w, r_h = f.shape
     return float(_load().oracle_coarse_direct(_p(lab, _i32p), lab.shape[1], wy, wx, cls,
                                               _p(f, _f64p), r_w, r_h, d_x, d_y))
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (timing only: results do not depend on it);
+    returns the previous count."""
+    return int(_load().oracle_set_threads(int(n)))

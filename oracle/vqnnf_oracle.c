@@ -34,6 +34,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number           */
@@ -333,4 +336,19 @@ double oracle_coarse_direct(const int32_t *labels, int W, int wy, int wx, int cl
             s += f_i[(int64_t)i * r_h + j] * (double)c;
         }
     return s;
+}
+
+/* Threads of the parallel loops above, for timing only: every loop computes independent
+ * elements, so the results do not depend on it.  n >= 1 sets the count; returns the count in
+ * effect before the call. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    const int prev = omp_get_max_threads();
+    if (n >= 1) omp_set_num_threads(n);
+    return prev;
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -48,3 +48,24 @@ def test_single_process_identity():
     assert not dist.is_initialized()
     assert bench.reduce_max_ms(7.25) == 7.25
     assert bench.job_value(5.0, 1, 1_000_000) == pytest.approx(200.0)
+
+
+def test_cpu_baseline_fields_on_a_small_workload():
+    """The oracle leg reports its thread count, per-phase times and a one-thread figure, and
+    scales the samples to a whole step (a small workload, so the oracle finishes at once)."""
+    import bench
+    import oracle
+    cfg = dict(bench.HEADLINE)
+    cfg.update(H=96, W=80, D=32, k=8, th=24, tw=20, iters=3, M=6, n_sp=40)
+    q, T, _, bank = bench.make_workload("cpu", cfg)
+    cb = bench.cpu_baseline(q, T, cfg, bank, one_thread=True)
+    assert cb["kind"] == "oracle" and cb["unit"] == "Mpix/s" and cb["value"] > 0
+    assert cb["cores"] == oracle.set_threads(0) >= 1
+    assert set(cb["phases_s"]) == {"fit_one_lloyd_step", "assign_640_px", "score_64_windows"}
+    assert cb["one_thread"]["value"] > 0 and set(cb["one_thread"]["phases_s"]) == set(cb["phases_s"])
+    # the step estimate is the phases scaled to the workload
+    ph = cb["phases_s"]
+    L, HO, WO = 96 * 80, 96 - 24 + 1, 80 - 20 + 1
+    est = ph["fit_one_lloyd_step"] * 3 + ph["assign_640_px"] * (L + 24 * 20) / 640 + \
+        ph["score_64_windows"] * HO * WO / 64
+    assert abs(est - cb["step_s_estimate"]) <= 0.01 + 0.01 * est
