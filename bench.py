@@ -632,7 +632,7 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=
     tl = ql[:th, :tw]
     tc = oracle.filter_counts(tl, k, bank)
     rng = np.random.default_rng(0)
-    nwin = 64
+    nwin = 1024
     win = np.stack([rng.integers(0, HO, nwin), rng.integers(0, WO, nwin)], 1)
 
     def phases():

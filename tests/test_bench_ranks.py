@@ -61,11 +61,11 @@ def test_cpu_baseline_fields_on_a_small_workload():
     cb = bench.cpu_baseline(q, T, cfg, bank, one_thread=True)
     assert cb["kind"] == "oracle" and cb["unit"] == "Mpix/s" and cb["value"] > 0
     assert cb["cores"] == oracle.set_threads(0) >= 1
-    assert set(cb["phases_s"]) == {"fit_one_lloyd_step", "assign_640_px", "score_64_windows"}
+    assert set(cb["phases_s"]) == {"fit_one_lloyd_step", "assign_640_px", "score_1024_windows"}
     assert cb["one_thread"]["value"] > 0 and set(cb["one_thread"]["phases_s"]) == set(cb["phases_s"])
     # the step estimate is the phases scaled to the workload
     ph = cb["phases_s"]
     L, HO, WO = 96 * 80, 96 - 24 + 1, 80 - 20 + 1
     est = ph["fit_one_lloyd_step"] * 3 + ph["assign_640_px"] * (L + 24 * 20) / 640 + \
-        ph["score_64_windows"] * HO * WO / 64
+        ph["score_1024_windows"] * HO * WO / 1024
     assert abs(est - cb["step_s_estimate"]) <= 0.01 + 0.01 * est
