@@ -213,7 +213,7 @@ def kernels_per_step(cfg, prec):
     assign = 2 + 1 + 1 + 1          # prep mean + prep centroids, contraction, rescore, stats
     fit = 1 + cfg["iters"] * (assign - 1 + 2)   # gather; per step: assign (no stats) + sort + update
     tpl = (assign - 1) + 1          # template NNF, template responses
-    score = 2 + 1 + 1               # row carry + sweep, score, argmax
+    score = 4 + 1 + 1               # row carries, band sums, band prefix, write pass; score; argmax
     return fit + tpl + assign + score
 
 

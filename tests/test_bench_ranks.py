@@ -69,3 +69,14 @@ def test_cpu_baseline_fields_on_a_small_workload():
     est = ph["fit_one_lloyd_step"] * 3 + ph["assign_640_px"] * (L + 24 * 20) / 640 + \
         ph["score_1024_windows"] * HO * WO / 1024
     assert abs(est - cb["step_s_estimate"]) <= 0.01 + 0.01 * est
+
+
+def test_launch_count_claim_matches_the_launch_sequence():
+    """gpu_launches counts the library's kernels per step.  The headline launch list
+    (profiles/launches_bench_headline_2048.md) shows 77 per BF16 step:
+    - 12 each of prep mean, prep centroids, contraction and re-scoring;
+    - 10 each of stable sort and update;
+    - one each of gather, template responses, stats, row carries, band sums, band prefix,
+      write pass, score and argmax."""
+    import bench
+    assert bench.kernels_per_step(bench.HEADLINE, "bf16") == 12 * 4 + 10 * 2 + 9
