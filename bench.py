@@ -12,7 +12,7 @@ larger than L2, so no flush is needed between steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32] [--impl reference]
                   [--query-size S] [--no-compare] [--no-e2e] [--no-cpu-baseline] [--cpu-budget SEC]
-                  [--no-paper-bank] [--no-soft] [--soft-batch B] [--no-batch] [--batch-eager]
+                  [--no-paper-bank] [--no-soft] [--soft-batch B] [--no-batch] [--batch-eager] [--no-small]
 
 ``--query-size`` shrinks the query to S x S (for profiler captures of the same kernels on a
 smaller case); the bench line itself is quoted on the default 2048.
@@ -373,6 +373,12 @@ def run_gpu(args, rank, world):
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe, one_thread=True)
+    if not args.no_small:
+        # last, after every other leg: a failure here leaves an error entry, not a missing line
+        try:
+            line["small_workload"] = run_small(vq, dev)
+        except Exception as exc:                          # noqa: BLE001
+            line["small_workload"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
     return line
 
 
@@ -558,6 +564,58 @@ def run_batch(vq, dev, reps=2, eager=False):
     return out
 
 
+SMALL = dict(H=256, W=256, D=64, k=16, th=32, tw=32, grid=3, iters=10, M=32, n_sp=200,
+             q_seed=1000, t_seed=2000, fit_seed=3000)
+
+
+def run_small(vq, dev, reps=50):
+    """The small plain workload: a 256 x 256 query, D = 64, k = 16, a 32 x 32 crop template,
+    F = 10 and 10 Lloyd steps. It is latency-bound, so it is reported per call, in both
+    precisions: the whole path as one CUDA-graph replay, and the same calls enqueued one by one
+    from Python. The difference is the launch and host overhead that the graph removes."""
+    import torch
+    import synth
+    cfg = dict(SMALL)
+    q = synth.query_map(cfg["H"], cfg["W"], cfg["D"], M=cfg["M"], n_sp=cfg["n_sp"], seed=cfg["q_seed"],
+                        device=dev)
+    T, _ = synth.crop_template(q, cfg["th"], cfg["tw"], seed=cfg["t_seed"])
+    bank = synth.grid_bank(cfg["th"], cfg["tw"], cfg["grid"])
+    s = torch.cuda.Stream(device=dev)
+    L = cfg["H"] * cfg["W"]
+    out = {"workload": "256x256 query, D=64, k=16, 32x32 crop template, F=10 (full + 3x3), 10 Lloyd steps; "
+                       "whole hot path per call", "launches_per_call": kernels_per_step(cfg, "fp32")}
+    for prec in ("fp32", "bf16"):
+        pipe = Pipeline(vq, q.X, T, cfg, bank, prec, s)
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                pipe.step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                pipe.step()
+            g.replay()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(s)
+        with torch.cuda.stream(s):
+            for _ in range(reps):
+                g.replay()
+        e[1].record(s)
+        with torch.cuda.stream(s):
+            for _ in range(reps):
+                pipe.step()
+        e[2].record(s)
+        torch.cuda.synchronize()
+        t_graph = e[0].elapsed_time(e[1]) / reps
+        t_calls = e[1].elapsed_time(e[2]) / reps
+        out[prec] = {"us_per_call": round(1e3 * t_graph, 1), "value": round(L / (t_graph * 1e-3) / 1e6, 3),
+                     "unit": "Mpix/s", "us_per_call_enqueued_one_by_one": round(1e3 * t_calls, 1),
+                     "overhead_removed_by_graph_us": round(1e3 * (t_calls - t_graph), 1)}
+        del g, pipe
+    return out
+
+
 def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
     """End to end through the C ABI with host buffers: vqnnf_match_host takes the pinned host
     feature maps and writes the host heatmap and maximum, every step.  The host link (~210 GB/s
@@ -731,6 +789,8 @@ def main():
                          "(for profilers that do not follow the replay of a large graph)")
     ap.add_argument("--no-paper-bank", action="store_true",
                     help="skip scoring with the paper's own filter bank")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small latency-bound workload (256^2, D=64, k=16)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision on the same inputs")
     args = ap.parse_args()
