@@ -741,6 +741,11 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step runs the bounded sample of cpu_baseline
+    (one Lloyd step, 16,384 query pixels assigned, 1,024 windows scored) on the host cores.
+    ``steps`` and ``ms_per_step`` are what actually ran (the sample's wall time per step);
+    ``value`` is the metric, the sample's per-phase times scaled to one whole step, and
+    ``full_step_ms_estimate`` that scaled step time."""
     if rank != 0:
         return None
     import torch
@@ -755,15 +760,19 @@ def run_reference(args, rank, world):
         vals.append(cpu_baseline(q, T, cfg, bank))
     wall = time.perf_counter() - t0
     v = statistics.median(x["value"] for x in vals)
+    full_s = statistics.median(x["step_s_estimate"] for x in vals)
     cb = dict(vals[-1])
     cb["value"] = v
     return {"metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(1e3 * vals[-1]["step_s_estimate"], 1),
+            "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(1, args.steps), 1),
+            "ms_per_step_basis": "wall time of the sampled step that ran (not the whole workload)",
+            "full_step_ms_estimate": round(1e3 * full_s, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
                                    "(full + 3x3), 10 Lloyd steps; whole hot path per step",
-                       "sampled": True, "wall_s": round(wall, 1), "torch_threads": torch.get_num_threads()},
+                       "sampled": True, "sample": cb["sample"], "wall_s": round(wall, 1),
+                       "torch_threads": torch.get_num_threads()},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

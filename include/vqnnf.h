@@ -134,18 +134,20 @@ vqnnf_status vqnnf_assign(const float *X, int H, int W, int D, const float *C, i
                           void *ws, size_t ws_bytes, void *stream);
 
 /* Allocation-free variant of vqnnf_assign.  The paper has no counterpart: this entry point
- * exists for callers that cannot allocate device memory at all -- code running while a
- * stream is being captured into a CUDA graph (where cudaMalloc is not allowed), plug-ins
- * whose host application owns every device allocation, and real-time loops that must not
- * call the allocator.  Such callers cannot provide the scratch workspace vqnnf_assign needs,
- * so this call uses a fixed scratch area compiled into the library instead:
+ * exists for callers that cannot allocate device memory themselves -- plug-ins whose host
+ * application owns every device allocation, and loops that must never wait on the allocator
+ * (cudaMalloc and cudaFree can synchronise the whole device).  Such callers cannot provide
+ * the scratch workspace vqnnf_assign needs, so this call uses a fixed scratch area compiled
+ * into the library instead:
  *   - the area is VQNNF_NOALLOC_SCRATCH_BYTES (16 MiB) of device memory, held on every GPU
  *     that loads the library until the process exits;
  *   - a request whose workspace (vqnnf_workspace_bytes(VQNNF_OP_ASSIGN, ...)) exceeds it is
  *     rejected with VQNNF_ENOMEM before anything is enqueued (about 450,000 pixels at D=512,
  *     k=128; use vqnnf_assign with a caller workspace for larger images);
  *   - the first call on a device looks up the area's device address (with that device
- *     current); make that first call before any stream capture begins;
+ *     current) and keeps it for the life of the process; make that first call before any
+ *     stream capture begins.  A device reset (cudaDeviceReset) invalidates the kept address:
+ *     do not call this entry point again in that process after one;
  *   - every call on a device shares the one area: calls whose work overlaps on the GPU (on
  *     different streams, or from different host threads) race and give wrong labels --
  *     order them on one stream.  The area keeps the last call's contents; the call clears

@@ -20,6 +20,9 @@ hard one of Eq. 2 (pinned in the tests).
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 
@@ -36,11 +39,22 @@ def soft_assign(X, C, tau: float):
     the largest logit subtracted before exponentiation)."""
     X = np.asarray(X, np.float64)
     C = np.asarray(C, np.float64)
-    d = ((X[..., None, :] - C) ** 2).sum(-1)
-    z = -d / tau
-    z -= z.max(-1, keepdims=True)
-    e = np.exp(z)
-    return e / e.sum(-1, keepdims=True)
+    shape = X.shape[:-1]
+    X = X.reshape(-1, X.shape[-1])
+    p = np.empty((X.shape[0], C.shape[0]))
+    step = 2048                       # pixels per pass, to bound the (pixels, k, D) temporary
+
+    def rows(i):
+        d = ((X[i:i + step, None, :] - C) ** 2).sum(-1)
+        z = -d / tau
+        z -= z.max(-1, keepdims=True)
+        e = np.exp(z)
+        p[i:i + step] = e / e.sum(-1, keepdims=True)
+
+    # independent pixel blocks (numpy releases the GIL inside each array operation)
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(rows, range(0, X.shape[0], step)))
+    return p.reshape(shape + (C.shape[0],))
 
 
 def _box_all(p, y0, y1, x0, x1, HO, WO):
@@ -78,14 +92,15 @@ def _softmax_back(p, g, tau: float):
     return -(p * (g - (p * g).sum(-1, keepdims=True))) / tau
 
 
-def soft_backward(Qf, Tf, C, tau: float, G: int, wf, Gw):
-    """Gradients of L = sum Gw * H: dQf (B, H, W, D), dC (k, D), dwf (F,)."""
+def soft_backward(Qf, Tf, C, tau: float, G: int, wf, Gw, forward=None):
+    """Gradients of L = sum Gw * H: dQf (B, H, W, D), dC (k, D), dwf (F,).  ``forward``: the
+    result of soft_forward for the same arguments, if already computed."""
     Qf = np.asarray(Qf, np.float64)
     Tf = np.asarray(Tf, np.float64)
     C = np.asarray(C, np.float64)
     wf = np.asarray(wf, np.float64)
     Gw = np.asarray(Gw, np.float64)
-    f = soft_forward(Qf, Tf, C, tau, G, wf)
+    f = soft_forward(Qf, Tf, C, tau, G, wf) if forward is None else forward
     B, H, W, _ = Qf.shape
     HO, WO = Gw.shape[1:]
     k = C.shape[0]

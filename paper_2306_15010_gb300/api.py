@@ -41,6 +41,15 @@ def _need(t: torch.Tensor, name: str, dtype: torch.dtype) -> None:
         raise ValueError(f"{name} must be contiguous")
 
 
+def _stats_ptr(stats) -> int:
+    if stats is None:
+        return 0
+    _need(stats, "stats", torch.int64)
+    if stats.numel() < _STATS_WORDS:
+        raise ValueError("stats needs 4 int64 words")
+    return stats.data_ptr()
+
+
 def _prec(prec) -> int:
     if isinstance(prec, str):
         try:
@@ -151,17 +160,14 @@ def vqnnf_assign(X: torch.Tensor, C: torch.Tensor, prec="fp32", *,
     else:
         H, W, D = X.shape
     k = C.shape[0]
-    if C.shape[1] != D:
+    if C.dim() != 2 or C.shape[1] != D:
         raise ValueError("codebook width differs from the feature depth")
     if labels is None:
         labels = torch.empty(X.shape[:-1], dtype=torch.uint8, device=X.device)
     _need(labels, "labels", torch.uint8)
-    sp = 0
-    if stats is not None:
-        _need(stats, "stats", torch.int64)
-        if stats.numel() < _STATS_WORDS:
-            raise ValueError("stats needs 4 int64 words")
-        sp = stats.data_ptr()
+    if labels.numel() < H * W:
+        raise ValueError(f"labels holds {labels.numel()} bytes, the feature map has {H * W} pixels")
+    sp = _stats_ptr(stats)
     p = _prec(prec)
     nb = vqnnf_workspace_bytes(_lib.OP_ASSIGN, H, W, D, k, prec=p)
     if nb == 0:
@@ -178,10 +184,12 @@ def vqnnf_assign_noalloc(X: torch.Tensor, C: torch.Tensor, prec="fp32", *,
                          labels: torch.Tensor, stats: torch.Tensor | None = None,
                          stream=None) -> torch.Tensor:
     """vqnnf_assign without a workspace, for callers that cannot allocate device memory
-    (e.g. while a CUDA graph is being captured): the library's fixed 16 MiB scratch area is
-    used instead.  ``labels`` must be passed in; nothing is allocated here either.  Calls
-    that overlap on the GPU share that area and race; requests that need more scratch than
-    it holds raise (status VQNNF_ENOMEM)."""
+    themselves (a plug-in whose host application owns every device allocation, or a loop
+    that must never wait on the allocator): the library's fixed 16 MiB scratch area is used
+    instead.  ``labels`` must be passed in; nothing is allocated here either.  Calls that
+    overlap on the GPU share that area and race; requests that need more scratch than it
+    holds raise (status VQNNF_ENOMEM).  Every shape check of vqnnf_assign is made here too,
+    before anything is enqueued."""
     _need(X, "X", torch.float32)
     _need(C, "C", torch.float32)
     _need(labels, "labels", torch.uint8)
@@ -189,10 +197,11 @@ def vqnnf_assign_noalloc(X: torch.Tensor, C: torch.Tensor, prec="fp32", *,
         H, W, D = 1, X.shape[0], X.shape[1]
     else:
         H, W, D = X.shape
-    sp = 0
-    if stats is not None:
-        _need(stats, "stats", torch.int64)
-        sp = stats.data_ptr()
+    if C.dim() != 2 or C.shape[1] != D:
+        raise ValueError("codebook width differs from the feature depth")
+    if labels.numel() < H * W:
+        raise ValueError(f"labels holds {labels.numel()} bytes, the feature map has {H * W} pixels")
+    sp = _stats_ptr(stats)
     st = _lib.load().vqnnf_assign_noalloc(X.data_ptr(), H, W, D, C.data_ptr(), C.shape[0],
                                           _prec(prec), labels.data_ptr(), sp, _stream(stream))
     _lib.check("vqnnf_assign_noalloc", st)

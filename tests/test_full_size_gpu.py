@@ -7,8 +7,16 @@ variant (1024 x 1024 query, D = 1024, the same generator, codebook size and temp
 * template labels: every pixel against the oracle (outside the 1e-6 near-tie band);
 * query labels: BF16 == FP32 on every pixel outside the band, and both against the oracle on
   a seeded sample plus every pixel where the two paths disagree;
-* template counts: exact; heatmap: sampled windows against the oracle's score of the GPU
-  labels within 1e-5 of max |H|, and the reported argmax is a maximum of the heatmap.
+* template counts: exact;
+* heatmap, at every window the score kernel's tiling could get wrong (the four corners, the
+  whole first and last valid rows and columns, both sides of every 256-window seam, which
+  covers tile widths of 256, 512 and 1024) plus seeded random windows and the maximum,
+  against the oracle's Eq. 2 of the GPU labels:
+  - |H_gpu - H_ref| < min_f(w_f / A_f) / 2.  Every per-filter L1 sum is an integer and the
+    float part is F float32 terms (about 1e-5 here), so a single count error anywhere shows;
+  - every per-filter L1 sum exactly: the bank is scored again once per filter with that
+    filter's weight 1 and the others 0 (same rectangles, same kernel), which gives
+    H = -(1 / A_f) L1_f, and the integer L1_f recovered from it equals the oracle's.
 """
 import numpy as np
 import pytest
@@ -89,20 +97,50 @@ def test_query_labels(run):
     assert bool(band[in_diff].all())
 
 
-def test_heatmap_sampled_windows(run):
+def _windows(HO, WO, am, seed=11, seam=256):
+    ys, xs = np.arange(HO), np.arange(WO)
+    col = lambda x: np.stack([ys, np.full(HO, x)], 1)
+    row = lambda y: np.stack([np.full(WO, y), xs], 1)
+    parts = [row(0), row(HO - 1), col(0), col(WO - 1), np.asarray(am)[None]]
+    for s0 in range(seam, WO, seam):
+        parts += [col(s0 - 1), col(s0)]
+    rng = np.random.default_rng(seed)
+    parts.append(np.stack([rng.integers(0, HO, 256), rng.integers(0, WO, 256)], 1))
+    return np.unique(np.concatenate(parts).astype(np.int32), axis=0)
+
+
+def _unit_bank(bank, f):
+    """The same filters with weight 1 for filter f and 0 for every other one."""
+    return [dict(flt, w_f=1.0 if i == f else 0.0) for i, flt in enumerate(bank)]
+
+
+def test_heatmap_exact_at_edges_and_seams(run):
+    import paper_2306_15010_gb300 as vq
     cfg, q, T, bank, out = run
     k, th, tw = cfg["k"], cfg["th"], cfg["tw"]
+    coef = np.array([f["w_f"] / f["area"] for f in bank])
     for prec in ("bf16", "fp32"):
-        ql = out[prec]["ql"].cpu().numpy().astype(np.int32)
-        tc = out[prec]["tc"].cpu().numpy()
+        ql_d, tc_d = out[prec]["ql"], out[prec]["tc"]
+        ql = ql_d.cpu().numpy().astype(np.int32)
+        tc = tc_d.cpu().numpy()
         heat = out[prec]["heat"]
         HO, WO = heat.shape
-        rng = np.random.default_rng(11)
-        win = np.stack([rng.integers(0, HO, 256), rng.integers(0, WO, 256)], 1)
         am = out[prec]["am"].cpu().numpy()
-        win = np.concatenate([win, am[None]], 0)
+        win = _windows(HO, WO, am)
+        wy = torch.as_tensor(win[:, 0], device=heat.device, dtype=torch.long)
+        wx = torch.as_tensor(win[:, 1], device=heat.device, dtype=torch.long)
         ref = oracle.score_at(ql, k, bank, tc, win)
-        got = heat.cpu().numpy()[win[:, 0], win[:, 1]]
-        scale = float(heat.abs().max())
-        assert np.max(np.abs(got - ref)) <= 1e-5 * scale, prec
+        got = heat[wy, wx].cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref)
+        assert err.max() < 0.5 * coef.min(), (prec, float(err.max()), win[int(err.argmax())])
         assert float(heat[am[0], am[1]]) == float(heat.max()), prec
+        # every per-filter L1 sum, as an integer
+        for f in range(len(bank)):
+            ub = _unit_bank(bank, f)
+            hf, _ = vq.vqnnf_score(ql_d, k, th, tw, ub, tc_d)
+            c32 = np.float32(coef[f])
+            l1_gpu = np.rint(-hf[wy, wx].cpu().numpy().astype(np.float64) / np.float64(c32))
+            l1_ref = np.rint(-oracle.score_at(ql, k, [dict(bank[f], w_f=1.0)], tc[f:f + 1], win) *
+                             bank[f]["area"])
+            bad = np.flatnonzero(l1_gpu != l1_ref)
+            assert bad.size == 0, (prec, f, win[bad[:5]], l1_gpu[bad[:5]], l1_ref[bad[:5]])

@@ -5,7 +5,11 @@ Tolerances (from the arithmetic, see the design notes):
   distances is >= 1e-6 (the near-tie band); duplicate centroids must give the lowest index;
 * codebook: bit-identical (same FP64 additions in the same order, same roundings);
 * counts: exact integers;
-* heatmap from identical labels: |H_gpu - H_ref| <= 1e-5 * max|H_ref| (F float32 terms);
+* heatmap from identical labels: |H_gpu - H_ref| < min_f(w_f / A_f) / 2 at every window.
+  Each per-filter L1 sum of Eq. 2 is an exact integer and the float part is F float32 terms
+  (far below that bound here), so one count error in any filter shows.  The wide-row case
+  also recovers every per-filter L1 sum as an integer (one run per filter with the other
+  weights 0) and compares it with the oracle's;
   heatmap of the whole path: <= 1e-4 * max|H_ref|.
 """
 import numpy as np
@@ -191,10 +195,25 @@ def test_filter_responses_exact(vq, bank_name):
     assert np.array_equal(got, oracle.filter_counts(t, k, bank))
 
 
-def _check_heat(got_heat, got_am, ref_heat, rtol):
+def _exact_bound(bank):
+    """Half the smallest change of H that one count of one rectangle can make:
+    w_f / A_f times the rectangle's weight (the filter's L1 sum moves by at least that)."""
+    return 0.5 * min(abs(f["w_f"]) / f["area"] * min(abs(r[4]) for r in f["rects"])
+                     for f in bank if f["w_f"] != 0)
+
+
+def _check_heat(got_heat, got_am, ref_heat, rtol, bank=None):
     scale = max(np.abs(ref_heat).max(), 1e-30)
-    err = np.abs(got_heat - ref_heat).max() / scale
-    assert err <= rtol, f"heatmap relative error {err:.3g}"
+    if bank is not None:
+        # identical labels: every per-filter sum is exact
+        err = np.abs(got_heat - ref_heat)
+        i = int(err.argmax())
+        assert err.max() < _exact_bound(bank), \
+            f"heatmap error {err.max():.3g} at {divmod(i, got_heat.shape[1])}"
+        rtol = _exact_bound(bank) / scale
+    else:
+        err = np.abs(got_heat - ref_heat).max() / scale
+        assert err <= rtol, f"heatmap relative error {err:.3g}"
     y, x = got_am
     # the reported maximum is a maximum of the oracle heatmap up to the tolerance, and the
     # lowest row-major index among the GPU's own maxima
@@ -220,7 +239,62 @@ def test_score_from_oracle_labels(vq, bank_name, H, W, th, tw, k):
     ref, _ = oracle.score(ql, k, th, tw, bank, tc)
     heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank,
                               _dev(tc.astype(np.int32)))
-    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5, bank)
+
+
+@pytest.mark.parametrize("bank_name", ["grid3", "grid2", "grid4", "full_only", "weighted"])
+@pytest.mark.parametrize("k", [3, 45, 256])
+def test_score_wide_rows_every_filter_exact(vq, bank_name, k):
+    """More than 1,024 windows per row (so every block seam of the score kernels along x is
+    crossed) and a ragged last tile; every window element by element, and every per-filter
+    L1 sum as an integer: the bank is scored once per filter with that filter's weight 1 and
+    the others 0 (same rectangles, so the same kernel), giving H = -(1 / A_f) L1_f."""
+    H, W, th, tw = 80, 1200, 24, 24
+    r = np.random.default_rng(k + 5)
+    q = synth.query_map(H, W, 4, M=6, n_sp=H * W // 120, seed=k)
+    ql = (q.sp_id.numpy() * 7 % k).astype(np.int32)
+    ql[r.random(ql.shape) < 0.08] = r.integers(0, k)
+    t = ql[30:30 + th, 1000:1000 + tw].copy()
+    bank = _banks(th, tw)[bank_name]
+    tc = oracle.filter_counts(t, k, bank)
+    ql_d, tc_d = _dev(ql.astype(np.uint8)), _dev(tc.astype(np.int32))
+    ref, _ = oracle.score(ql, k, th, tw, bank, tc)
+    heat, am = vq.vqnnf_score(ql_d, k, th, tw, bank, tc_d)
+    assert heat.shape[1] > 1024
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5, bank)
+    for f, flt in enumerate(bank):
+        unit = [dict(g, w_f=1.0 if i == f else 0.0) for i, g in enumerate(bank)]
+        hf, _ = vq.vqnnf_score(ql_d, k, th, tw, unit, tc_d)
+        c32 = np.float64(np.float32(1.0 / flt["area"]))
+        l1_gpu = np.rint(-hf.cpu().numpy().astype(np.float64) / c32)
+        rf, _ = oracle.score(ql, k, th, tw, [dict(flt, w_f=1.0)], tc[f:f + 1])
+        l1_ref = np.rint(-rf * flt["area"])
+        bad = np.argwhere(l1_gpu != l1_ref)
+        assert bad.size == 0, (f, bad[:5])
+
+
+@pytest.mark.parametrize("th,tw,G", [(127, 129, 1),   # one cell of 16,383 pixels
+                                     (128, 128, 1),   # 16,384 pixels
+                                     (130, 131, 1),
+                                     (200, 240, 2),   # cells of 12,000 pixels, full window 48,000
+                                     (255, 257, 1)])  # 65,535 pixels: the largest 16-bit table
+def test_score_counts_near_the_table_modulus(vq, th, tw, G):
+    """Large grid cells on the 16-bit table (counts mod 2^16): regions of one label make the
+    counts reach the cell area, up to the largest template the 16-bit table takes."""
+    H, W, k = th + 37, tw + 300, 7
+    r = np.random.default_rng(th + tw)
+    q = synth.query_map(H, W, 4, M=6, n_sp=H * W // 3000, seed=th)
+    ql = (q.sp_id.numpy() * 3 % k).astype(np.int32)
+    ql[:, : W // 3] = 2                                     # a large one-label region
+    ql[r.random(ql.shape) < 0.01] = r.integers(0, k)
+    t = ql[5:5 + th, 11:11 + tw].copy()
+    t[: th // 2] = 2
+    for full in (True, False):
+        bank = synth.grid_bank(th, tw, G, full=full)
+        tc = oracle.filter_counts(t, k, bank)
+        ref, _ = oracle.score(ql, k, th, tw, bank, tc)
+        heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank, _dev(tc.astype(np.int32)))
+        _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5, bank)
 
 
 @pytest.mark.parametrize("filters,S,gauss", [("2,3-rect", 3, "equal"), ("2,3-rect", 3, "exp"),
@@ -241,7 +315,7 @@ def test_score_paper_bank(vq, filters, S, gauss):
     assert np.array_equal(got_tc.cpu().numpy(), tc)
     ref, _ = oracle.score(ql, k, th, tw, bank, tc)
     heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank, _dev(tc.astype(np.int32)))
-    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5, bank)
     assert tuple(am.cpu().tolist()) == (20, 61) or ref[20, 61] == ref.max()
 
 
@@ -334,5 +408,5 @@ def test_score_large_template_uses_32bit_table(vq):
     tc = oracle.filter_counts(t, k, bank)
     ref, _ = oracle.score(ql, k, th, tw, bank, tc)
     heat, am = vq.vqnnf_score(_dev(ql.astype(np.uint8)), k, th, tw, bank, _dev(tc.astype(np.int32)))
-    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5)
+    _check_heat(heat.cpu().numpy(), tuple(am.cpu().tolist()), ref, 1e-5, bank)
     assert am.cpu().tolist() == [10, 7]

@@ -1,10 +1,12 @@
 """The allocation-free assignment entry point (vqnnf_assign_noalloc).
 
-It serves callers that cannot allocate device memory -- e.g. code running while a CUDA
-graph is being captured, or a plug-in whose host owns every allocation -- by using the
-library's fixed scratch area instead of a caller workspace.  Its labels and counters must
-equal those of vqnnf_assign on the same inputs, call after call (the area keeps the previous
-call's contents, which must not leak into the next result).
+It serves callers that cannot allocate device memory themselves -- a plug-in whose host
+application owns every device allocation, or a loop that must never wait on the allocator --
+by using the library's fixed scratch area instead of a caller workspace.  Its labels and
+counters must equal those of vqnnf_assign on the same inputs, call after call, in both
+contraction precisions (the area keeps the previous call's contents, which must not leak into
+the next result); the BF16 tensor-core route, whose tensor maps point into that area, is also
+checked against the FP64 oracle outside the near-tie band.
 
 This file is named so that pytest collects it last.
 """
@@ -59,14 +61,39 @@ def _noalloc(lib, X, C, prec):
     return lab, st
 
 
-def test_noalloc_matches_assign_on_consecutive_calls(lib):
-    prec = 0   # FP32 contraction with re-scoring
+@pytest.mark.parametrize("prec", [0, 1])     # FP32 SIMT / BF16 tcgen05 contraction, re-scored
+def test_noalloc_matches_assign_on_consecutive_calls(lib, prec):
     cases = [_case(200, 180, 64, 16, 11), _case(97, 131, 128, 32, 12)]
     for X, C in cases + cases[:1]:       # three calls in a row, the first input repeated
         want_lab, want_st = _reference(lib, X, C, prec)
         got_lab, got_st = _noalloc(lib, X, C, prec)
         assert torch.equal(got_lab, want_lab)
         assert torch.equal(got_st, want_st)
+        # and against the FP64 oracle, outside its near-tie band
+        ref, d1, d2 = oracle.assign(X.cpu().numpy(), C.cpu().numpy(), return_dist=True)
+        band = oracle.relative_gap(d1, d2) < 1e-6
+        got = got_lab.cpu().numpy().astype(np.int32)
+        assert int(((got != ref) & ~band).sum()) == 0
+
+
+def test_noalloc_binding_refuses_mis_sized_arguments(lib):
+    """The binding checks every size the kernels would trust, before anything is enqueued."""
+    import paper_2306_15010_gb300 as vq
+    X, C = _case(40, 30, 64, 16, 13)
+    lab = torch.empty((40, 30), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):                                    # codebook width != D
+        vq.vqnnf_assign_noalloc(X, C[:, :32].contiguous(), labels=lab)
+    with pytest.raises(ValueError):                                    # labels too short
+        vq.vqnnf_assign_noalloc(X, C, labels=lab[:20])
+    with pytest.raises(ValueError):                                    # stats too short
+        vq.vqnnf_assign_noalloc(X, C, labels=lab, stats=torch.zeros(2, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):                                    # the same checks in vqnnf_assign
+        vq.vqnnf_assign(X, C, labels=lab[:20])
+    with pytest.raises(ValueError):
+        vq.vqnnf_assign(X, C, stats=torch.zeros(3, dtype=torch.int64, device="cuda"))
+    vq.vqnnf_assign_noalloc(X, C, labels=lab)                          # well-formed: accepted
+    torch.cuda.synchronize()
+    assert torch.equal(lab, vq.vqnnf_assign(X, C))
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(lib):
