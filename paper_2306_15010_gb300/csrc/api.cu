@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -32,7 +33,7 @@ AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
     w.prep.a = c.take<float>((size_t)k);
     w.prep.v = c.take<float>((size_t)k);
     w.prep.b = c.take<float>((size_t)k);
-    w.fl.count = c.take<unsigned int>(64);     // count + stats share one memset
+    w.fl.count = c.take<unsigned int>(64);     // count + stats, zeroed together
     w.fl.stats = c.base ? reinterpret_cast<unsigned long long *>(w.fl.count + 16) : nullptr;
     w.fl.pix = c.take<unsigned int>((size_t)n);
     w.fl.mask = c.take<unsigned int>((size_t)n * kMaskWords);
@@ -112,6 +113,16 @@ static cudaEvent_t g_ev[4][2] = {};
 
 }  // namespace vqnnf
 
+bool vqnnf::pdl_enabled()
+{
+    // VQNNF_PDL=0 launches every kernel without programmatic stream serialization (for A/B timing)
+    static const bool on = [] {
+        const char *v = getenv("VQNNF_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 cudaError_t vqnnf::record_kernel_event(int op, int which, cudaStream_t s)
 {
     cudaEvent_t ev;
@@ -128,8 +139,7 @@ namespace vqnnf {
 vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
                         uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(w.fl.count, 0, 64 * sizeof(unsigned), s);
-    if (e == cudaSuccess) e = launch_prep_codebook(C, k, D, prec, w.prep, s);
+    cudaError_t e = launch_prep_codebook(C, k, D, prec, w.prep, s, w.fl.count);
     if (e == cudaSuccess) {
         e = record_kernel_event(VQNNF_OP_ASSIGN, 0, s);
         if (e == cudaSuccess)

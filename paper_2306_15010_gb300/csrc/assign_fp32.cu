@@ -20,6 +20,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace vqnnf {
 namespace {
@@ -33,8 +34,11 @@ constexpr double kU32 = 5.9604644775390625e-08;  // 2^-24
 // for any m); the codebook mean keeps the centred norms small.  Four interleaved FP32 partial
 // sums in a fixed order: deterministic and short.
 __global__ void __launch_bounds__(256) prep_mean_kernel(const float *__restrict__ C, int k, int D,
-                                                        float *mean)
+                                                        float *mean, unsigned *zero64)
 {
+    ptx::pdl_enter();
+    // the flag list's counter and statistics words start at zero (one launch fewer than a memset)
+    if (zero64 && blockIdx.x == 0 && threadIdx.x < 64) zero64[threadIdx.x] = 0u;
     // block: 32 dimensions x 8 row groups; partial sums combined in a fixed order
     __shared__ float part[8][33];
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -85,6 +89,7 @@ __device__ __forceinline__ float bf16_value(uint32_t h) { return __uint_as_float
 __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restrict__ C, int k,
                                                             int D, int prec, CodebookPrep p)
 {
+    ptx::pdl_enter();
     const int j = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ float red[8][8];
@@ -245,6 +250,7 @@ __global__ void __launch_bounds__(NT, 2) assign_fp32_kernel(const float *__restr
                                                          int D, int k, CodebookPrep p,
                                                          uint8_t *__restrict__ labels, FlagList fl)
 {
+    ptx::pdl_enter();
     extern __shared__ __align__(16) float smem[];
     const int kp = (k + BN - 1) / BN * BN;
     const int sp = kp + 1;
@@ -416,6 +422,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
                                                       uint8_t *__restrict__ labels, FlagList fl,
                                                       unsigned cap)
 {
+    ptx::pdl_enter();
     const int lane = threadIdx.x & 31;
     const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nw = (gridDim.x * blockDim.x) >> 5;
@@ -514,6 +521,7 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
 
 __global__ void finish_stats_kernel(FlagList fl, vqnnf_assign_stats *out)
 {
+    ptx::pdl_enter();
     out->n_flagged = *fl.count;
     out->n_candidates = fl.stats[1];
     out->n_deep = fl.stats[2];
@@ -523,10 +531,16 @@ __global__ void finish_stats_kernel(FlagList fl, vqnnf_assign_stats *out)
 }  // namespace
 
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
-                                 cudaStream_t s)
+                                 cudaStream_t s, unsigned *zero64)
 {
-    prep_mean_kernel<<<(D + 31) / 32, 256, 0, s>>>(C, k, D, p.mean);
-    prep_centroid_kernel<<<k, 256, 0, s>>>(C, k, D, prec, p);
+    {
+        const cudaError_t le_ = launch_pdl(prep_mean_kernel, dim3((D + 31) / 32), dim3(256), 0, s, C, k, D, p.mean, zero64);
+        if (le_ != cudaSuccess) return le_;
+    }
+    {
+        const cudaError_t le_ = launch_pdl(prep_centroid_kernel, dim3(k), dim3(256), 0, s, C, k, D, prec, p);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
@@ -544,7 +558,10 @@ cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k, const 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long blocks = (n + BM - 1) / BM;
-    assign_fp32_kernel<<<(unsigned)blocks, NT, smem, s>>>(X, n, D, k, p, labels, fl);
+    {
+        const cudaError_t le_ = launch_pdl(assign_fp32_kernel, dim3((unsigned)blocks), dim3(NT), smem, s, X, n, D, k, p, labels, fl);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
@@ -554,13 +571,19 @@ cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, i
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    rescore_kernel<<<sms * 8, 256, 0, s>>>(X, D, C, k, labels, fl, (unsigned)n);
+    {
+        const cudaError_t le_ = launch_pdl(rescore_kernel, dim3(sms * 8), dim3(256), 0, s, X, D, C, k, labels, fl, (unsigned)n);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s)
 {
-    finish_stats_kernel<<<1, 1, 0, s>>>(fl, out);
+    {
+        const cudaError_t le_ = launch_pdl(finish_stats_kernel, dim3(1), dim3(1), 0, s, fl, out);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 

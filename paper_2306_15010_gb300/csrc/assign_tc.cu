@@ -39,6 +39,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace vqnnf {
 namespace {
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                                                           const __grid_constant__ CUtensorMap tmBlo,
                                                           const __grid_constant__ TcArgs g)
 {
+    ptx::pdl_enter();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int npad = g.npad, D = g.D, nkc = g.nkc, SB = g.sb, SF = g.sf, NB = g.nb, SA = g.sa;
@@ -875,12 +877,18 @@ cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const Cod
         e = cudaFuncSetAttribute(assign_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        assign_tc_kernel<false, false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+        {
+        const cudaError_t le_ = launch_pdl(assign_tc_kernel<false, false>, dim3((unsigned)grid), dim3(NT), smem, s, tmA, tmBhi, tmBlo, a);
+        if (le_ != cudaSuccess) return le_;
+    }
     } else {
         e = cudaFuncSetAttribute(assign_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        assign_tc_kernel<true, false><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+        {
+        const cudaError_t le_ = launch_pdl(assign_tc_kernel<true, false>, dim3((unsigned)grid), dim3(NT), smem, s, tmA, tmBhi, tmBlo, a);
+        if (le_ != cudaSuccess) return le_;
+    }
     }
     return cudaGetLastError();
 }
@@ -963,7 +971,10 @@ cudaError_t launch_assign_bf16_stat(const float *X, long long n, int D, const Co
     const long long grid = a.ntiles < sms ? a.ntiles : sms;
     e = cudaFuncSetAttribute(assign_tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    assign_tc_kernel<true, true><<<(unsigned)grid, NT, smem, s>>>(tmA, tmBhi, tmBlo, a);
+    {
+        const cudaError_t le_ = launch_pdl(assign_tc_kernel<true, true>, dim3((unsigned)grid), dim3(NT), smem, s, tmA, tmBhi, tmBlo, a);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 

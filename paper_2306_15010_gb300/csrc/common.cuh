@@ -45,8 +45,9 @@ struct TcSeg {
 };
 
 // Host-side launchers (defined in the .cu files).
+// zero64: if not null, 64 words zeroed by the first kernel (a flag list's counter and statistics).
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
-                                 cudaStream_t s);
+                                 cudaStream_t s, unsigned *zero64 = nullptr);
 cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k,
                                const CodebookPrep &p, uint8_t *labels, FlagList fl,
                                cudaStream_t s);
@@ -69,6 +70,28 @@ int stat_max_groups(int D, int gcols);
 cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, int k,
                            uint8_t *labels, FlagList fl, cudaStream_t s);
 cudaError_t launch_finish_stats(FlagList fl, vqnnf_assign_stats *out, cudaStream_t s);
+
+// Launch with programmatic stream serialization: the kernel's blocks may be scheduled before the
+// preceding kernel of the stream finishes; every kernel launched this way calls ptx::pdl_enter()
+// before it touches global memory, so the order of effects is the stream order.  The launch
+// latency and the tail of the previous kernel overlap instead of adding up.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Records the caller's profiling event `which` (0 = start, 1 = stop) of operation `op` on s,
 // when vqnnf_set_kernel_events has set one; otherwise does nothing.

@@ -7,6 +7,7 @@
 // FP64 sum is the same sequence of additions as a plain loop over pixels -- the centroids
 // do not depend on scheduling.
 #include "common.cuh"
+#include "ptx.cuh"
 
 namespace vqnnf {
 
@@ -15,6 +16,7 @@ namespace {
 __global__ void gather_init_kernel(const float *__restrict__ T, int D, int k, InitIdx ii,
                                    float *__restrict__ C)
 {
+    ptx::pdl_enter();
     const int j = blockIdx.x;
     const float *src = T + (size_t)ii.idx[j] * D;
     for (int i = threadIdx.x; i < D; i += blockDim.x) C[(size_t)j * D + i] = src[i];
@@ -30,6 +32,7 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
                                                            int l, int k, int *cnt, int *off,
                                                            int *members)
 {
+    ptx::pdl_enter();
     __shared__ int wc[32][kMaxK];   // per-warp counts, then per-warp running slots
     __shared__ int tot[kMaxK];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -150,6 +153,7 @@ __global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restr
                                                          const int *__restrict__ cnt, const int *__restrict__ off,
                                                          const int *__restrict__ members, float *__restrict__ C)
 {
+    ptx::pdl_enter();
     // the 128-bit partial sums, later reused for the staged member values of the FP64 route
     __shared__ __align__(16) unsigned __int128 sacc[3][UW][32];
     __shared__ int slow[UW][32], shish[UW][32];
@@ -264,17 +268,26 @@ __global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restr
 cudaError_t launch_gather_init(const float *T, int D, int k, const InitIdx &ii, float *C,
                                cudaStream_t s)
 {
-    gather_init_kernel<<<k, 128, 0, s>>>(T, D, k, ii, C);
+    {
+        const cudaError_t le_ = launch_pdl(gather_init_kernel, dim3(k), dim3(128), 0, s, T, D, k, ii, C);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8_t *lab, int *cnt,
                                 int *off, int *members, float *C, cudaStream_t s)
 {
-    stable_sort_kernel<<<1, 1024, 0, s>>>(lab, l, k, cnt, off, members);
+    {
+        const cudaError_t le_ = launch_pdl(stable_sort_kernel, dim3(1), dim3(1024), 0, s, lab, l, k, cnt, off, members);
+        if (le_ != cudaSuccess) return le_;
+    }
     // one block of UW warps per (32 dimensions, cluster)
     dim3 g((D + 31) / 32, k);
-    update_kernel<<<g, 32 * UW, 0, s>>>(T, D, k, cnt, off, members, C);
+    {
+        const cudaError_t le_ = launch_pdl(update_kernel, dim3(g), dim3(32 * UW), 0, s, T, D, k, cnt, off, members, C);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 

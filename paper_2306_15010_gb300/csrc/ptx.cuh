@@ -77,6 +77,12 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Programmatic dependent launch: wait until the preceding kernel of the stream has completed
+// and its memory is visible (a no-op for a kernel launched without the attribute).  No early
+// trigger: the next kernel is released as this one's blocks finish, so its blocks never sit
+// waiting beside this kernel's.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Waits until at most N of this thread's committed bulk groups are still reading their source.
 template <int N>

@@ -45,6 +45,7 @@ constexpr int BH = 64;     // rows per band
 __global__ void row_carry_kernel(const uint8_t *__restrict__ lab, int W, int k, int nS,
                                  int *__restrict__ carry)
 {
+    ptx::pdl_enter();
     extern __shared__ int hist[];     // [nS][k]
     const int y = blockIdx.x;
     for (int q = threadIdx.x; q < nS * k; q += blockDim.x) hist[q] = 0;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict
                                                        int k, int P, int nS, const int *__restrict__ carry,
                                                        int *__restrict__ bandsum)
 {
+    ptx::pdl_enter();
     extern __shared__ int cc[];                          // [SW][k] label counts per column, then [k] carry sums
     int *csum_s = cc + SW * k;
     const int s = blockIdx.x, b = blockIdx.y;
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(32 * SatSweep<T>::warps, 4) sat_write_kernel(
     const uint8_t *__restrict__ lab, int H, int W, int k, int P, int nS, int nB, const int *__restrict__ carry,
     const int *__restrict__ bandsum, T *__restrict__ S)
 {
+    ptx::pdl_enter();
     constexpr int NW = SatSweep<T>::warps, PITCH = SatSweep<T>::pitch;
     __shared__ __align__(16) uint8_t srow[NW][2][SW];
     __shared__ __align__(16) uint8_t sout[NW][2][32][PITCH];
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(32 * SatSweep<T>::warps, 4) sat_write_kernel(
 // Exclusive prefix of the band sums over bands, per (cluster, column), in place.
 __global__ void band_prefix_kernel(int *__restrict__ bandsum, int nB, long long kP)
 {
+    ptx::pdl_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kP) return;
     int run = 0;
@@ -274,6 +278,7 @@ __global__ void band_prefix_kernel(int *__restrict__ bandsum, int nB, long long 
 __global__ void filter_responses_kernel(const uint8_t *__restrict__ lab, int w, int k,
                                         BankSpec bs, int32_t *__restrict__ counts)
 {
+    ptx::pdl_enter();
     __shared__ int hist[kMaxK];
     const int f = blockIdx.x;
     for (int j = threadIdx.x; j < k; j += blockDim.x) hist[j] = 0;
@@ -338,6 +343,7 @@ __global__ void __launch_bounds__(STH, 6) score_grid_kernel(const T *__restrict_
                                                          float *__restrict__ heat,
                                                          unsigned long long *amax)
 {
+    ptx::pdl_enter();
     // For a single-rectangle filter q and clusters j, with t = template count and n = query
     // count (every pixel carries one label < k, so sum_j n_qj = area_q):
     //     L1_q = sum_j |t_qj - n_qj| = area_q + sum_{j : t_qj > 0} (|t_qj - n_qj| - n_qj)
@@ -484,6 +490,7 @@ __global__ void __launch_bounds__(STH, 6) score_wgrid_kernel(const T *__restrict
                                                           float *__restrict__ heat,
                                                           unsigned long long *amax)
 {
+    ptx::pdl_enter();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const int ncol = ws.ncol;
     constexpr int chunk_elems = 4 * NCOLP;                    // one cluster, four corner rows
@@ -617,6 +624,7 @@ __global__ void __launch_bounds__(STH) score_generic_kernel(const T *__restrict_
                                                             float *__restrict__ heat,
                                                             unsigned long long *amax)
 {
+    ptx::pdl_enter();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const int ncol = bs.ncol, nrow = bs.nrow;
     T *buf0 = reinterpret_cast<T *>(smem_raw);
@@ -701,6 +709,7 @@ __global__ void wait_selftest_kernel(long long limit)
 
 __global__ void argmax_finish_kernel(const unsigned long long *amax, int WO, int32_t *out)
 {
+    ptx::pdl_enter();
     const unsigned idx = 0xFFFFFFFFu - (unsigned)(*amax & 0xFFFFFFFFull);
     out[0] = (int32_t)(idx / (unsigned)WO);
     out[1] = (int32_t)(idx % (unsigned)WO);
@@ -719,12 +728,18 @@ cudaError_t launch_grid(const T *S, int P, int k, int HO, int WO, const GridSpec
         e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL, TXW + 128>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        score_grid_kernel<T, G, FULL, TXW + 128><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+        {
+        const cudaError_t le_ = launch_pdl(score_grid_kernel<T, G, FULL, TXW + 128>, dim3(grid), dim3(STH), smem, s, S, P, k, HO, WO, gs, tc, heat, amax);
+        if (le_ != cudaSuccess) return le_;
+    }
     } else {
         e = cudaFuncSetAttribute(score_grid_kernel<T, G, FULL, TXW + 256>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        score_grid_kernel<T, G, FULL, TXW + 256><<<grid, STH, smem, s>>>(S, P, k, HO, WO, gs, tc, heat, amax);
+        {
+        const cudaError_t le_ = launch_pdl(score_grid_kernel<T, G, FULL, TXW + 256>, dim3(grid), dim3(STH), smem, s, S, P, k, HO, WO, gs, tc, heat, amax);
+        if (le_ != cudaSuccess) return le_;
+    }
     }
     return cudaGetLastError();
 }
@@ -740,17 +755,29 @@ cudaError_t launch_sat_t(const uint8_t *lab, int H, int W, int k, int *carry, in
     cudaError_t e = cudaFuncSetAttribute(row_carry_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
     if (e != cudaSuccess) return e;
-    row_carry_kernel<<<H, 256, hsmem, s>>>(lab, W, k, nS, carry);
+    {
+        const cudaError_t le_ = launch_pdl(row_carry_kernel, dim3(H), dim3(256), hsmem, s, lab, W, k, nS, carry);
+        if (le_ != cudaSuccess) return le_;
+    }
     const size_t csmem = sizeof(int) * ((size_t)SW * k + k);
     e = cudaFuncSetAttribute(band_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
     if (e != cudaSuccess) return e;
-    band_sum_kernel<<<dim3(nS, nB), 256, csmem, s>>>(lab, H, W, k, P, nS, carry, bandsum);
+    {
+        const cudaError_t le_ = launch_pdl(band_sum_kernel, dim3(dim3(nS, nB)), dim3(256), csmem, s, lab, H, W, k, P, nS, carry, bandsum);
+        if (le_ != cudaSuccess) return le_;
+    }
     const long long kP = (long long)k * P;
-    band_prefix_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, s>>>(bandsum, nB, kP);
+    {
+        const cudaError_t le_ = launch_pdl(band_prefix_kernel, dim3((unsigned)((kP + 255) / 256)), dim3(256), 0, s, bandsum, nB, kP);
+        if (le_ != cudaSuccess) return le_;
+    }
     const long long nwarps = (long long)nB * nS * ((k + 31) / 32);
     constexpr int NW = SatSweep<T>::warps;
     const unsigned blocks = (unsigned)((nwarps + NW - 1) / NW);
-    sat_write_kernel<T><<<blocks, 32 * NW, 0, s>>>(lab, H, W, k, P, nS, nB, carry, bandsum, S);
+    {
+        const cudaError_t le_ = launch_pdl(sat_write_kernel<T>, dim3(blocks), dim3(32 * NW), 0, s, lab, H, W, k, P, nS, nB, carry, bandsum, S);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
@@ -765,12 +792,18 @@ cudaError_t launch_wgrid(const T *S, int P, int k, int HO, int WO, const WGridSp
         e = cudaFuncSetAttribute(score_wgrid_kernel<T, NG, TXW + 128>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        score_wgrid_kernel<T, NG, TXW + 128><<<grid, STH, smem, s>>>(S, P, k, HO, WO, ws, tc, heat, amax);
+        {
+        const cudaError_t le_ = launch_pdl(score_wgrid_kernel<T, NG, TXW + 128>, dim3(grid), dim3(STH), smem, s, S, P, k, HO, WO, ws, tc, heat, amax);
+        if (le_ != cudaSuccess) return le_;
+    }
     } else {
         e = cudaFuncSetAttribute(score_wgrid_kernel<T, NG, TXW + 256>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        score_wgrid_kernel<T, NG, TXW + 256><<<grid, STH, smem, s>>>(S, P, k, HO, WO, ws, tc, heat, amax);
+        {
+        const cudaError_t le_ = launch_pdl(score_wgrid_kernel<T, NG, TXW + 256>, dim3(grid), dim3(STH), smem, s, S, P, k, HO, WO, ws, tc, heat, amax);
+        if (le_ != cudaSuccess) return le_;
+    }
     }
     return cudaGetLastError();
 }
@@ -814,13 +847,19 @@ cudaError_t launch_score_t(const T *S, int W, int k, int HO, int WO, const BankS
                                  (int)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((WO + TXW - 1) / TXW, HO);
-        score_generic_kernel<T><<<grid, STH, smem, s>>>(S, P, k, HO, WO, bs, tc, heat, amax);
+        {
+        const cudaError_t le_ = launch_pdl(score_generic_kernel<T>, dim3(grid), dim3(STH), smem, s, S, P, k, HO, WO, bs, tc, heat, amax);
+        if (le_ != cudaSuccess) return le_;
+    }
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
     if ((e = record_kernel_event(VQNNF_OP_SCORE, 1, s)) != cudaSuccess) return e;
     if (argmax_yx && amax) {
-        argmax_finish_kernel<<<1, 1, 0, s>>>(amax, WO, argmax_yx);
+        {
+        const cudaError_t le_ = launch_pdl(argmax_finish_kernel, dim3(1), dim3(1), 0, s, amax, WO, argmax_yx);
+        if (le_ != cudaSuccess) return le_;
+    }
         e = cudaGetLastError();
     }
     return e;
@@ -869,7 +908,10 @@ cudaError_t launch_filter_responses(const uint8_t *lab, int h, int w, int k, con
                                     int32_t *counts, cudaStream_t s)
 {
     (void)h;
-    filter_responses_kernel<<<bs.F, 256, 0, s>>>(lab, w, k, bs, counts);
+    {
+        const cudaError_t le_ = launch_pdl(filter_responses_kernel, dim3(bs.F), dim3(256), 0, s, lab, w, k, bs, counts);
+        if (le_ != cudaSuccess) return le_;
+    }
     return cudaGetLastError();
 }
 
