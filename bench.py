@@ -304,33 +304,57 @@ def run_gpu(args, rank, world):
     am = pipe.am.cpu().tolist()
     clocks = clk.summary(t_on, t_off)
 
-    # the other precision on the same inputs, same GPU, for the BF16-vs-FP32 comparison
-    other = "fp32" if args.prec == "bf16" else "bf16"
-    ms2, same_labels = None, None
+    # the other precisions on the same inputs, same GPU: the BF16-vs-FP32 comparison and the
+    # FP8 e4m3 contraction (every path returns exact labels; the report says what each costs)
+    others = {}
     if not args.no_compare:
-        pipe2 = Pipeline(vq, X, T, cfg, bank, other, s)
-        with torch.cuda.stream(s):
-            for _ in range(args.warmup):
-                pipe2.step()
-        torch.cuda.synchronize()
-        graph2 = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(s):
-            with torch.cuda.graph(graph2, stream=s):
-                pipe2.step()
-            graph2.replay()
-        torch.cuda.synchronize()
-        st2 = torch.cuda.Event(enable_timing=True)
-        sp2 = torch.cuda.Event(enable_timing=True)
-        st2.record(s)
-        with torch.cuda.stream(s):
-            for i in range(K):
+        for other in [p for p in ("fp32", "bf16", "fp8") if p != args.prec]:
+            pipe2 = Pipeline(vq, X, T, cfg, bank, other, s)
+            with torch.cuda.stream(s):
+                for _ in range(args.warmup):
+                    pipe2.step()
+            torch.cuda.synchronize()
+            graph2 = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(graph2, stream=s):
+                    pipe2.step()
                 graph2.replay()
-        sp2.record(s)
-        torch.cuda.synchronize()
-        ms2 = st2.elapsed_time(sp2) / K
-        same_labels = bool(torch.equal(pipe.ql, pipe2.ql))
-        del graph2, pipe2
-
+            torch.cuda.synchronize()
+            st2 = torch.cuda.Event(enable_timing=True)
+            sp2 = torch.cuda.Event(enable_timing=True)
+            st2.record(s)
+            with torch.cuda.stream(s):
+                for i in range(K):
+                    graph2.replay()
+            sp2.record(s)
+            torch.cuda.synchronize()
+            ms2 = st2.elapsed_time(sp2) / K
+            # one call-by-call step with events around its segments and its contraction
+            ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            kev2 = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            for e in kev2:
+                e.record(s)
+            with torch.cuda.stream(s):
+                pipe2.step(ev2, kev2)
+            torch.cuda.synchronize()
+            st = pipe2.stats.cpu().tolist()
+            ndiff = int((pipe.ql != pipe2.ql).sum().item())
+            hd = float((pipe.heat - pipe2.heat).abs().max().item()) / max(float(pipe.heat.abs().max().item()), 1e-30)
+            others[other] = {
+                "value": round(world * cfg["H"] * cfg["W"] / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+                "ms_per_step": round(ms2, 4),
+                "segments_ms": {"template_side": round(ev2[0].elapsed_time(ev2[1]), 4),
+                                "query_assign": round(ev2[1].elapsed_time(ev2[2]), 4),
+                                "query_score": round(ev2[2].elapsed_time(ev2[3]), 4)},
+                "query_contraction_ms": round(kev2[0].elapsed_time(kev2[1]), 4),
+                "assign_stats": {"n_flagged": st[0], "n_candidates": st[1], "n_deep": st[2],
+                                 "flagged_pct": round(100.0 * st[0] / (cfg["H"] * cfg["W"]), 3)},
+                "labels_identical": ndiff == 0, "query_labels_differing": ndiff,
+                "heat_max_rel_diff_vs_main": hd,
+            }
+            del graph2
+            others[other]["_pipe"] = pipe2
+            del pipe2
     # end to end through the same API: pinned host inputs in, argmax + heatmap out, per step
     e2e = None if args.no_e2e else run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=am)
     paper = None if args.no_paper_bank else run_paper_bank(vq, pipe, cfg, s, dev)
@@ -350,7 +374,7 @@ def run_gpu(args, rank, world):
         "execution": {"timed": "CUDA graph replay of one whole step per iteration",
                       "ms_per_step_call_by_call": round(ms_calls, 4)},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if args.prec == "bf16" else "f32", "data": "synthetic",
+        "dtype": {"bf16": "bf16", "fp8": "fp8e4m3", "fp32": "f32"}[args.prec], "data": "synthetic",
         "config": {"workload": f"{cfg['H']}x{cfg['W']} query, D=512, k=128, 128x128 template, F=10 "
                                "(full + 3x3), 10 Lloyd steps; whole hot path per step",
                    "prec": args.prec, "query_px": L, "l2": "inputs larger than L2 (8 GiB features)",
@@ -364,15 +388,20 @@ def run_gpu(args, rank, world):
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
         "roofline": roof, "roofline_score": roof_score, "clocks": clocks, "e2e": e2e,
         "paper_bank": paper, "soft_vq": soft_vq, "batch": batch,
-        f"{other}_path": None if ms2 is None else {
-            "value": round(world * L / (ms2 * 1e-3) / 1e6, 3), "unit": "Mpix/s",
-            "ms_per_step": round(ms2, 4),
-            "speedup_bf16_over_fp32": round((ms2 / ms) if other == "fp32" else (ms / ms2), 3),
-            "labels_identical": same_labels},
+        **{f"{o}_path": {kk: vv for kk, vv in d.items() if kk != "_pipe"}
+           for o, d in others.items()},
         "gpu_launches": kernels_per_step(cfg, args.prec) * K,
     }
+    if "fp32" in others and args.prec == "bf16":
+        line["fp32_path"]["speedup_bf16_over_fp32"] = round(others["fp32"]["ms_per_step"] / ms, 3)
+    if "fp8" in others:
+        line["fp8_path"]["speedup_fp8_over_main"] = round(ms / others["fp8"]["ms_per_step"], 3)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe, one_thread=True)
+        line["cpu_baseline"] = cpu_baseline(q, T, cfg, bank, budget_s=args.cpu_budget, pipe=pipe, one_thread=True,
+                                            other_pipes={o: d["_pipe"] for o, d in others.items()})
+    for d in others.values():
+        d.pop("_pipe", None)
+    others.clear()
     if not args.no_small:
         # last, after every other leg: a failure here leaves an error entry, not a missing line
         try:
@@ -669,7 +698,7 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
     return out
 
 
-def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=False):
+def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=False, other_pipes=None):
     """The FP64 oracle timed on bounded samples of the same workload, scaled to one step, on
     all of the oracle's threads (and, with ``one_thread``, again on one thread).  With ``pipe``
     (the timed BF16 pipeline), this run's own results are also checked against the oracle on
@@ -737,7 +766,24 @@ def cpu_baseline(q, T, cfg, bank, budget_s=20.0, steps=1, pipe=None, one_thread=
                                "near_tie_band_pixels": int(band.sum()),
                                "heat_windows_checked": int(nwin), "heat_max_rel_err": rel,
                                "heat_bound": 1e-4}
+        # the other precisions' labels and heatmaps on the same samples (their codebooks equal
+        # the main path's: the fit is exact in every precision)
+        for name, p2 in (other_pipes or {}).items():
+            g2 = p2.ql[: 8].cpu().numpy().astype(np.int32).reshape(-1)
+            diff = g2 != ref.reshape(-1)
+            h2ref = oracle.score_at(p2.ql.cpu().numpy().astype(np.int32), k, bank, p2.tc.cpu().numpy(), win)
+            h2 = p2.heat.cpu().numpy()[win[:, 0], win[:, 1]].astype(np.float64)
+            out["oracle_check"][f"{name}_path"] = {
+                "codebook_equal_to_main": bool(torch_equal(p2.C, pipe.C)),
+                "label_mismatches_outside_band": int((diff & ~band).sum()),
+                "label_mismatches_inside_band": int((diff & band).sum()),
+                "heat_max_rel_err": float(np.abs(h2 - h2ref).max() / max(float(np.abs(h2ref).max()), 1e-30))}
     return out
+
+
+def torch_equal(a, b):
+    import torch
+    return torch.equal(a, b)
 
 
 def run_reference(args, rank, world):
@@ -782,7 +828,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--prec", choices=["bf16", "fp32", "fp8"], default="bf16")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")

@@ -57,7 +57,13 @@ typedef enum vqnnf_status {
 /* Arithmetic of the nearest-neighbour distance contraction (Sec. 4.2: exact L2 NN). */
 typedef enum vqnnf_prec {
     VQNNF_PREC_FP32 = 0,     /* FP32 SIMT dot products                                   */
-    VQNNF_PREC_BF16 = 1      /* BF16 tensor cores (tcgen05), FP32 accumulation            */
+    VQNNF_PREC_BF16 = 1,     /* BF16 tensor cores (tcgen05), FP32 accumulation            */
+    VQNNF_PREC_FP8 = 2       /* FP8 e4m3 tensor cores (tcgen05 kind::f8f6f4) with a power-of-
+                              * two scale per feature row and per centroid, FP32
+                              * accumulation; the features are quantised by the call itself
+                              * (workspace: H*W*D bytes more).  D % 16 == 0 and
+                              * ceil(k / 32) * 32 * D <= 131072 (the codebook stays in shared
+                              * memory: k <= 256 at D <= 512, k <= 128 at D <= 1024) */
 } vqnnf_prec;
 /* Both precisions return the exact nearest neighbour of the FP32 inputs: every pixel
  * whose two best distances are closer than a proven bound on the contraction's error is
@@ -126,7 +132,10 @@ vqnnf_status vqnnf_fit_codebook(const float *T, int h, int w, int D, int k, int 
 /* Nearest-neighbour field (Algorithm 1): labels[p] = argmin_j ||X[p] - C[j]||^2.
  *   X       device, H x W x D float32 features (query or template)
  *   C       device, k x D float32 codebook, 1 <= k <= 256
- *   prec    VQNNF_PREC_FP32 (D % 4 == 0) or VQNNF_PREC_BF16 (D % 16 == 0)
+ *   prec    VQNNF_PREC_FP32 (D % 4 == 0), VQNNF_PREC_BF16 (D % 16 == 0) or VQNNF_PREC_FP8
+ *           (see vqnnf_prec); every precision returns the exact nearest neighbour: pixels whose
+ *           contraction result is ambiguous under its proven error bound are re-scored from
+ *           the FP32 inputs
  *   labels  device, H x W uint8, written
  *   stats   device vqnnf_assign_stats, overwritten; may be NULL */
 vqnnf_status vqnnf_assign(const float *X, int H, int W, int D, const float *C, int k,

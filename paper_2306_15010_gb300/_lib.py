@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvqnnf.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
-PREC = {"fp32": 0, "bf16": 1}
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 OP_FIT, OP_ASSIGN, OP_FILTER_RESPONSES, OP_SCORE = range(4)
 NOALLOC_SCRATCH_BYTES = 16 << 20      # VQNNF_NOALLOC_SCRATCH_BYTES
 

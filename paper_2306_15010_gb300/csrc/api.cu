@@ -22,9 +22,10 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 // ----------------------------------------------------------------------------------
 // Workspace layouts (the same code computes sizes with a null base).
 // ----------------------------------------------------------------------------------
-AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
+AssignWs carve_assign(WsCursor &c, long long n, int D, int k, int prec)
 {
     AssignWs w;
+    memset(&w, 0, sizeof(w));
     w.prep.mean = c.take<float>((size_t)D);
     w.prep.cc = c.take<float>((size_t)k * D);
     w.prep.chi = c.take<uint16_t>((size_t)k * D);
@@ -37,13 +38,19 @@ AssignWs carve_assign(WsCursor &c, long long n, int D, int k)
     w.fl.stats = c.base ? reinterpret_cast<unsigned long long *>(w.fl.count + 16) : nullptr;
     w.fl.pix = c.take<unsigned int>((size_t)n);
     w.fl.mask = c.take<unsigned int>((size_t)n * kMaskWords);
+    if (prec == VQNNF_PREC_FP8) {
+        w.prep.cq8 = c.take<uint8_t>((size_t)k * D);
+        w.prep.csc = c.take<float>((size_t)k);
+        w.f8.q = c.take<uint8_t>((size_t)n * D);
+        w.f8.rs = c.take<float2>((size_t)n);
+    }
     return w;
 }
 
-FitWs carve_fit(WsCursor &c, long long l, int D, int k)
+FitWs carve_fit(WsCursor &c, long long l, int D, int k, int prec)
 {
     FitWs w;
-    w.as = carve_assign(c, l, D, k);
+    w.as = carve_assign(c, l, D, k, prec);
     w.lab = c.take<uint8_t>((size_t)l);
     w.cnt = c.take<int>((size_t)k);
     w.off = c.take<int>((size_t)k + 1);
@@ -73,7 +80,7 @@ struct HostWs {
     ScoreWs sc;
 };
 
-HostWs carve_host(WsCursor &c, int H, int W, int D, int k, int th, int tw, int F)
+HostWs carve_host(WsCursor &c, int H, int W, int D, int k, int th, int tw, int F, int prec)
 {
     HostWs w;
     const long long n = (long long)H * W, l = (long long)th * tw;
@@ -85,8 +92,8 @@ HostWs carve_host(WsCursor &c, int H, int W, int D, int k, int th, int tw, int F
     w.ql = c.take<uint8_t>((size_t)n);
     w.tc = c.take<int32_t>((size_t)F * k);
     w.am = c.take<int32_t>(2);
-    w.fit = carve_fit(c, l, D, k);
-    w.as = carve_assign(c, n, D, k);
+    w.fit = carve_fit(c, l, D, k, prec);
+    w.as = carve_assign(c, n, D, k, prec);
     w.sc = carve_score(c, H, W, k, th, tw);
     return w;
 }
@@ -103,7 +110,7 @@ vqnnf_status from_cuda(cudaError_t e)
 bool check_prec(int prec, int D)
 {
     if (prec == VQNNF_PREC_FP32) return D % 4 == 0;
-    if (prec == VQNNF_PREC_BF16) return D % 16 == 0;
+    if (prec == VQNNF_PREC_BF16 || prec == VQNNF_PREC_FP8) return D % 16 == 0;
     return false;
 }
 
@@ -143,8 +150,9 @@ vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int 
     if (e == cudaSuccess) {
         e = record_kernel_event(VQNNF_OP_ASSIGN, 0, s);
         if (e == cudaSuccess)
-            e = prec == VQNNF_PREC_BF16 ? launch_assign_bf16(X, n, D, k, w.prep, labels, w.fl, s)
-                                        : launch_assign_fp32(X, n, D, k, w.prep, labels, w.fl, s);
+            e = prec == VQNNF_PREC_BF16  ? launch_assign_bf16(X, n, D, k, w.prep, labels, w.fl, s)
+                : prec == VQNNF_PREC_FP8 ? launch_assign_fp8(X, n, D, k, w.prep, w.f8, labels, w.fl, s)
+                                         : launch_assign_fp32(X, n, D, k, w.prep, labels, w.fl, s);
         if (e == cudaSuccess) e = record_kernel_event(VQNNF_OP_ASSIGN, 1, s);
     }
     if (e == cudaSuccess) e = launch_rescore(X, n, D, C, k, labels, w.fl, s);
@@ -419,16 +427,16 @@ const char *vqnnf_status_str(vqnnf_status s)
 
 size_t vqnnf_workspace_bytes(int op, int H, int W, int D, int k, int th, int tw, int F, int prec)
 {
-    (void)F; (void)prec;
+    (void)F;
     WsCursor c{nullptr, 0};
     switch (op) {
     case VQNNF_OP_FIT:
         if (H < 1 || W < 1 || D < 1 || k < 1 || k > kMaxK) return 0;
-        carve_fit(c, (long long)H * W, D, k);
+        carve_fit(c, (long long)H * W, D, k, prec);
         break;
     case VQNNF_OP_ASSIGN:
         if (H < 1 || W < 1 || D < 1 || k < 1 || k > kMaxK) return 0;
-        carve_assign(c, (long long)H * W, D, k);
+        carve_assign(c, (long long)H * W, D, k, prec);
         break;
     case VQNNF_OP_FILTER_RESPONSES:
         return 256;
@@ -449,13 +457,14 @@ vqnnf_status vqnnf_assign(const float *X, int H, int W, int D, const float *C, i
     if (!X || !C || !labels || !ws || H < 1 || W < 1 || D < 1 || k < 1) return VQNNF_EINVAL;
     if (!aligned(X, 16) || !aligned(C, 16) || !aligned(ws, 256)) return VQNNF_EINVAL;
     if (k > kMaxK) return VQNNF_EUNSUPPORTED;
-    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_FP8 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (prec == VQNNF_PREC_FP8 && !fp8_supported(D, k)) return VQNNF_EUNSUPPORTED;
     const long long n = (long long)H * W;
     if (n >= (1ll << 32)) return VQNNF_EUNSUPPORTED;
     if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_ASSIGN, H, W, D, k, 0, 0, 0, prec))
         return VQNNF_ENOMEM;
     WsCursor c{static_cast<char *>(ws), 0};
-    AssignWs w = carve_assign(c, n, D, k);
+    AssignWs w = carve_assign(c, n, D, k, prec);
     return run_assign(X, n, D, C, k, prec, labels, stats, w, as_stream(stream));
 }
 
@@ -468,12 +477,13 @@ vqnnf_status vqnnf_fit_codebook(const float *T, int h, int w, int D, int k, int 
     const long long l = (long long)h * w;
     if (k > l) return VQNNF_EINVAL;
     if (k > kMaxK) return VQNNF_EUNSUPPORTED;
-    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_FP8 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (prec == VQNNF_PREC_FP8 && !fp8_supported(D, k)) return VQNNF_EUNSUPPORTED;
     if (l > (1ll << 30)) return VQNNF_EUNSUPPORTED;
     if (ws_bytes < vqnnf_workspace_bytes(VQNNF_OP_FIT, h, w, D, k, 0, 0, 0, prec))
         return VQNNF_ENOMEM;
     WsCursor c{static_cast<char *>(ws), 0};
-    FitWs fw = carve_fit(c, l, D, k);
+    FitWs fw = carve_fit(c, l, D, k, prec);
     return run_fit(T, l, D, k, iters, seed, prec, C, fw, as_stream(stream));
 }
 
@@ -530,7 +540,8 @@ static vqnnf_status match_host_check(int H, int W, int D, int k, int th, int tw,
     if (H < 1 || W < 1 || D < 1 || k < 1 || th < 1 || tw < 1 || th > H || tw > W || F < 1) return VQNNF_EINVAL;
     if ((long long)k > (long long)th * tw) return VQNNF_EINVAL;
     if (k > kMaxK) return VQNNF_EUNSUPPORTED;
-    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_FP8 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (prec == VQNNF_PREC_FP8 && !fp8_supported(D, k)) return VQNNF_EUNSUPPORTED;
     if ((long long)H * W >= (1ll << 32) || (long long)th * tw > (1ll << 30) ||
         (long long)(H + 1) * (W + 1) >= (1ll << 31))
         return VQNNF_EUNSUPPORTED;
@@ -541,7 +552,7 @@ size_t vqnnf_match_host_workspace_bytes(int H, int W, int D, int k, int th, int 
 {
     if (match_host_check(H, W, D, k, th, tw, F, prec) != VQNNF_OK) return 0;
     WsCursor c{nullptr, 0};
-    carve_host(c, H, W, D, k, th, tw, F);
+    carve_host(c, H, W, D, k, th, tw, F, prec);
     return (c.off + 255) & ~size_t(255);
 }
 
@@ -565,7 +576,7 @@ vqnnf_status vqnnf_match_host(const float *X_host, int H, int W, int D, const fl
                                   : score_smem_bytes_for(u16 ? 2 : 4, bs, gs, k);
     if (smem > (size_t)device_smem_optin()) return VQNNF_EUNSUPPORTED;
     WsCursor cur{static_cast<char *>(ws), 0};
-    HostWs w = carve_host(cur, H, W, D, k, th, tw, F);
+    HostWs w = carve_host(cur, H, W, D, k, th, tw, F, prec);
     const cudaStream_t s = as_stream(stream), cs = stream2 ? as_stream(stream2) : s;
     const long long l = (long long)th * tw;
     constexpr int kBands = 8;
@@ -741,7 +752,8 @@ extern "C" vqnnf_status vqnnf_assign_noalloc(const float *X, int H, int W, int D
     if (!X || !C || !labels || H < 1 || W < 1 || D < 1 || k < 1) return VQNNF_EINVAL;
     if (!aligned(X, 16) || !aligned(C, 16)) return VQNNF_EINVAL;
     if (k > kMaxK) return VQNNF_EUNSUPPORTED;
-    if (!check_prec(prec, D)) return prec > VQNNF_PREC_BF16 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (!check_prec(prec, D)) return prec > VQNNF_PREC_FP8 ? VQNNF_EINVAL : VQNNF_EUNSUPPORTED;
+    if (prec == VQNNF_PREC_FP8 && !fp8_supported(D, k)) return VQNNF_EUNSUPPORTED;
     const long long n = (long long)H * W;
     if (n >= (1ll << 32)) return VQNNF_EUNSUPPORTED;
     const size_t need = vqnnf_workspace_bytes(VQNNF_OP_ASSIGN, H, W, D, k, 0, 0, 0, prec);
@@ -749,6 +761,6 @@ extern "C" vqnnf_status vqnnf_assign_noalloc(const float *X, int H, int W, int D
     void *base = nullptr;
     if (noalloc_scratch(&base) != cudaSuccess) return VQNNF_ECUDA;
     WsCursor c{static_cast<char *>(base), 0};
-    AssignWs w = carve_assign(c, n, D, k);
+    AssignWs w = carve_assign(c, n, D, k, prec);
     return run_assign(X, n, D, C, k, prec, labels, stats, w, as_stream(stream));
 }

@@ -16,6 +16,7 @@
 // with per-centroid a_j, v_j, b_j written by prep_codebook (derivation in the design
 // notes: contraction accumulation error, rounding of the centred codebook and of x').
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cfloat>
 
@@ -81,6 +82,19 @@ __device__ __forceinline__ uint32_t bf16_round_exact(float f, float e)
 
 __device__ __forceinline__ float bf16_value(uint32_t h) { return __uint_as_float(h << 16); }
 
+// The power of two s with s >= amax / 448 > s / 2 (at least 2^-100): dividing by s is exact in
+// FP32 and brings every value of magnitude <= amax to at most 448, the largest e4m3 value.
+__device__ __forceinline__ float pow2_scale(float amax)
+{
+    const float t = amax * (1.0f / 448.0f);           // correctly rounded; checked below
+    if (!(t > 0x1p-100f)) return 0x1p-100f;
+    int e;
+    frexpf(t, &e);                                    // t = f 2^e, f in [0.5, 1)
+    float s = ldexpf(1.0f, e);                        // s >= t
+    if (amax / s > 448.0f) s *= 2.0f;                 // t rounded below amax / 448
+    return s;
+}
+
 // One block per centroid, FP32 error-free arithmetic (the FP64 pipe of this GPU is narrow):
 // c* = c - m exactly as cf + d32 (TwoSum), the BF16 splits hi = bf16(c*), lo = bf16(c* - hi)
 // of the exact values, ||c*||^2 as a compensated sum of the exact squares (FMA products),
@@ -93,6 +107,25 @@ __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restr
     const int j = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ float red[8][8];
+    __shared__ float s_amax[8];
+    // FP8 path: the centroid's power-of-two scale s = 2^ceil(log2(max |fl32(c*)| / 448)), so
+    // that every fl32(c*_i) / s is exact in FP32 and at most 448 (the largest e4m3 value)
+    float csc = 1.0f;
+    if (prec == VQNNF_PREC_FP8) {
+        float am = 0.f;
+        for (int i = threadIdx.x; i < D; i += blockDim.x) {
+            float cf, d32;
+            two_sum(C[(size_t)j * D + i], -p.mean[i], cf, d32);
+            am = fmaxf(am, fabsf(cf));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        if (lane == 0) s_amax[w] = am;
+        __syncthreads();
+        am = s_amax[0];
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) am = fmaxf(am, s_amax[q]);
+        csc = pow2_scale(am);
+    }
     float S = 0.f, Sc = 0.f, Q = 0.f;                 // ||c*||^2: main sum, its compensation, small terms
     float s_cc2 = 0.f, s_d32 = 0.f, s_hi2 = 0.f, s_lo2 = 0.f, s_d16 = 0.f;
     for (int i = threadIdx.x; i < D; i += blockDim.x) {
@@ -109,6 +142,8 @@ __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restr
         const float d16 = fabsf(__fsub_rn(rf, lf)) + fabsf(rd);   // >= |r - lo| (rf - lf exact)
         p.chi[(size_t)j * D + i] = (uint16_t)hb;
         p.clo[(size_t)j * D + i] = (uint16_t)lb;
+        if (prec == VQNNF_PREC_FP8)                   // cf / csc is exact (power-of-two scale)
+            p.cq8[(size_t)j * D + i] = (uint8_t)__nv_cvt_float_to_fp8(cf / csc, __NV_SATFINITE, __NV_E4M3);
         // c*^2 = cf^2 + 2 cf d32 + d32^2, cf^2 = pp + pe exactly
         const float pp = __fmul_rn(cf, cf), pe = fmaf(cf, cf, -pp);
         float t, te;
@@ -173,6 +208,22 @@ __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restr
             const double gD = (double)D * u / (1.0 - (double)D * u);
             a = 2.0 * gD * ncc + 2.0 * (1.0 + 2.0 * u) * nd32;
             v = 2.0 * (ncc > nc ? ncc : nc);
+        } else if (prec == VQNNF_PREC_FP8) {
+            // e4m3 of fl32(c*) / s, round to nearest: each element within 2^-4 of its value, or
+            // within 2^-10 s absolute below the normal range; so with q the centroid's FP8 row,
+            //   ||c* - s q|| <= 2^-4 ||fl32(c*)|| + 2^-10 s sqrt(D) + ||c* - fl32(c*)||  (= dc)
+            //   ||s q||      <= (1 + 2^-4) ||fl32(c*)|| + 2^-10 s sqrt(D)              (= nq)
+            // The products of two e4m3 values are exact in FP32; the accumulation order and
+            // rounding of the tensor core are not documented: four times the sequential FP32
+            // bound (gacc).  The dot product's error is then at most
+            //   X (dc + gacc nq) + ||x' - s_x q_x|| ||c*||,  X >= ||s_x q_x||
+            const double sub = 0.0009765625 * (double)csc * sqrt((double)D) * margin;
+            const double dc = 0.0625 * ncc + sub + nd32;
+            const double nq = (1.0 + 0.0625) * ncc + sub;
+            const double gacc = (double)D * 4.0 * u;
+            a = 2.0 * (dc + gacc * nq) * (1.0 + 4.0 * u);
+            v = 2.0 * nc;
+            p.csc[j] = csc;
         } else {
             // Three BF16 products x_hi.hi + x_hi.lo + x_lo.hi.  Tensor-core accumulation
             // order and rounding are not documented: take four times the sequential FP32

@@ -32,6 +32,7 @@
 // and the tensor memory is released before the kernel returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <cfloat>
@@ -762,6 +763,327 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
     }
 }
 
+// ------------------------------------------------------------------ FP8 e4m3 path
+// Feature quantisation: one warp per pixel row.  x' = fl(x - m) (as the BF16 converters form
+// it), s_x = 2^ceil(log2(max |x'| / 448)) so that x' / s_x is exact and at most 448, and
+// q = e4m3(x' / s_x) rounded to nearest; rs = (s_x, an upper bound of ||x'||).
+__device__ __forceinline__ float pow2_scale_f8(float amax)
+{
+    const float t = amax * (1.0f / 448.0f);
+    if (!(t > 0x1p-100f)) return 0x1p-100f;
+    int e;
+    frexpf(t, &e);
+    float sc = ldexpf(1.0f, e);
+    if (amax / sc > 448.0f) sc *= 2.0f;
+    return sc;
+}
+
+__global__ void __launch_bounds__(256) fp8_quant_kernel(const float *__restrict__ X, long long n, int D,
+                                                      const float *__restrict__ mean, uint8_t *__restrict__ q,
+                                                      float2 *__restrict__ rs)
+{
+    ptx::pdl_enter();
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += nw) {
+        const float *x = X + row * D;
+        float am = 0.f, x2 = 0.f;
+        for (int i0 = 4 * lane; i0 < D; i0 += 128) {   // D % 16 == 0: whole float4 groups
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0));
+            const float4 m = __ldg(reinterpret_cast<const float4 *>(mean + i0));
+            const float a = v.x - m.x, b = v.y - m.y, c = v.z - m.z, d = v.w - m.w;
+            am = fmaxf(am, fmaxf(fmaxf(fabsf(a), fabsf(b)), fmaxf(fabsf(c), fabsf(d))));
+            x2 = fmaf(a, a, fmaf(b, b, fmaf(c, c, fmaf(d, d, x2))));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+            x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+        }
+        const float sx = pow2_scale_f8(am);
+        const float inv = 1.0f / sx;                         // a power of two: exact, and so is x' * inv
+        for (int i0 = 4 * lane; i0 < D; i0 += 128) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(x + i0));
+            const float4 m = __ldg(reinterpret_cast<const float4 *>(mean + i0));
+            const __nv_fp8x2_storage_t lo =
+                __nv_cvt_float2_to_fp8x2(make_float2((v.x - m.x) * inv, (v.y - m.y) * inv), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi =
+                __nv_cvt_float2_to_fp8x2(make_float2((v.z - m.z) * inv, (v.w - m.w) * inv), __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint32_t *>(q + row * D + i0) = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        // ||x'|| from an FP32 sum of D non-negative terms: within (D + 8) u of the exact norm
+        if (lane == 0) rs[row] = make_float2(sx, sqrtf(x2) * (1.0f + (float)(D + 8) * (float)kU));
+    }
+}
+
+constexpr int F8_NT = 256;             // 8 warps
+constexpr int F8_KC = 128;             // K elements (= bytes) per chunk
+constexpr int F8_BOX = TM * F8_KC;     // 16 KB: 128 rows x 128 bytes
+constexpr int F8_SA = 4;               // A stages
+constexpr int F8_BMAX = 131072;        // resident codebook bytes (npad x padded D)
+
+struct F8Args {
+    long long n;
+    int D, k, npad, nkc;
+    long long ntiles;
+    CodebookPrep p;
+    const float2 *rs;
+    uint8_t *labels;
+    FlagList fl;
+};
+
+// D (+)= A . B^T, A (128 rows x 32 e4m3) and B (npad rows x 32 e4m3) in shared memory.
+__device__ __forceinline__ void tc_mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Instruction descriptor: E4M3 x E4M3 -> F32, both K-major, M = 128, N = npad.
+__host__ __device__ constexpr uint32_t f8_idesc(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// One CTA per SM over 128-pixel tiles.  The FP8 codebook (npad rows x D bytes) is loaded once
+// and stays in shared memory; the FP8 features stream through F8_SA stages of 128 x 128 bytes.
+//   warp 0   TMA producer (codebook once, then the feature boxes)
+//   warp 1   TMEM allocation; lane 0 issues the MMAs (K = 32 per instruction)
+//   warps 4-7  epilogue: accumulators times s_x s_j give the dot products; the interval test
+//            of the BF16 path with the FP8 bound terms; labels and flags
+// Every mbarrier wait is bounded, as in assign_tc_kernel.
+__global__ void __launch_bounds__(F8_NT, 1) assign_fp8_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                              const __grid_constant__ CUtensorMap tmB,
+                                                              const __grid_constant__ F8Args g)
+{
+    ptx::pdl_enter();
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int npad = g.npad, D = g.D, nkc = g.nkc, k = g.k;
+    uint8_t *as = base;                                            // F8_SA x 16 KB
+    uint8_t *bsm = as + F8_SA * F8_BOX;                            // nkc chunks x npad rows x 128 B
+    float4 *colc = reinterpret_cast<float4 *>(bsm + (size_t)nkc * npad * 128);   // {||c*||^2, a, v, b}
+    float *cn = reinterpret_cast<float *>(colc + npad);            // ||c*||^2 (+inf for padding)
+    float *csc = cn + npad;                                        // per-column scale s_j
+    uint32_t *maskbuf = reinterpret_cast<uint32_t *>(csc + npad);  // [128][8]
+    float4 *segmx = reinterpret_cast<float4 *>(maskbuf + TM * kMaskWords);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(segmx + 1);
+    uint64_t *a_full = bar, *a_empty = bar + F8_SA, *b_full = bar + 2 * F8_SA;
+    uint64_t *acc_full = b_full + 1, *acc_empty = acc_full + 2, *drain = acc_empty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tmem_cols = 2 * npad <= 32 ? 32 : 2 * npad <= 64 ? 64 : 2 * npad <= 128 ? 128
+                             : 2 * npad <= 256 ? 256 : 512;
+    for (int j = tid; j < npad; j += F8_NT) {
+        const bool ok = j < k;
+        const int jc = ok ? j : k - 1;
+        const float nrm = ok ? g.p.nrm[jc] : FLT_MAX;               // padding columns never win nor qualify
+        cn[j] = nrm;
+        colc[j] = make_float4(nrm, ok ? g.p.a[jc] : 0.f, ok ? g.p.v[jc] : 0.f, ok ? g.p.b[jc] : 0.f);
+        csc[j] = ok ? g.p.csc[jc] : 0.f;
+    }
+    if (tid == 0) {
+        for (int q = 0; q < F8_SA; ++q) { mbar_init(&a_full[q], 1); mbar_init(&a_empty[q], 1); }
+        mbar_init(b_full, 1);
+        for (int q = 0; q < 2; ++q) { mbar_init(&acc_full[q], 1); mbar_init(&acc_empty[q], TM); }
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            mbar_expect_tx(b_full, (uint32_t)(nkc * npad * 128));
+            for (int kc = 0; kc < nkc; ++kc) tma_load_2d(bsm + (size_t)kc * npad * 128, &tmB, kc * F8_KC, 0, b_full);
+            uint32_t st = 0, ph = 0;
+            bool ok = true;
+            long long issued = 0, last[F8_SA] = {-1, -1, -1, -1};
+            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x)
+                for (int kc = 0; kc < nkc; ++kc, ++issued) {
+                    if (!(ok = mbar_wait(&a_empty[st], ph ^ 1, abort))) break;
+                    mbar_expect_tx(&a_full[st], F8_BOX);
+                    tma_load_2d(as + st * F8_BOX, &tmA, kc * F8_KC, (int)(tile * TM), &a_full[st]);
+                    last[st] = issued;
+                    if (++st == (uint32_t)F8_SA) { st = 0; ph ^= 1; }
+                }
+            // every copy issued has landed before the block can leave (bounded)
+            volatile int no_abort = 0;
+            mbar_wait(b_full, 0, &no_abort);
+            if (!ok)
+                for (int q = 0; q < F8_SA; ++q)
+                    if (last[q] >= 0) mbar_wait(&a_full[q], (uint32_t)((last[q] / F8_SA) & 1), &no_abort);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = f8_idesc(TM, npad);
+            const uint64_t adesc0 = sw128_desc(smem_u32(as)), bdesc0 = sw128_desc(smem_u32(bsm));
+            uint32_t st = 0, ph = 0, tl = 0;
+            bool ok = mbar_wait(b_full, 0, abort);
+            tc_fence_after();
+            for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+                const uint32_t buf = tl & 1;
+                if (!(ok = mbar_wait(&acc_empty[buf], ((tl >> 1) & 1) ^ 1, abort))) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + buf * npad;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    if (!(ok = mbar_wait(&a_full[st], ph, abort))) break;
+                    tc_fence_after();
+                    const uint64_t ad = adesc0 + (uint64_t)((st * F8_BOX) >> 4);
+                    const uint64_t bd = bdesc0 + (uint64_t)(((size_t)kc * npad * 128) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < F8_KC / 32; ++ks)    // K = 32 bytes per MMA: +2 in 16-byte units
+                        tc_mma_f8(d_tmem, ad + 2 * ks, bd + 2 * ks, idesc, (kc | ks) != 0);
+                    tc_commit(&a_empty[st]);
+                    if (++st == (uint32_t)F8_SA) { st = 0; ph ^= 1; }
+                }
+                if (ok) tc_commit(&acc_full[buf]);
+            }
+            tc_commit(drain);                                 // every MMA done before TMEM is released
+            volatile int no_abort = 0;
+            mbar_wait(drain, 0, &no_abort);
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------------- epilogue
+        const int grp = warp & 3;                 // TMEM lane group this warp may read
+        const int r = grp * 32 + lane;
+        const float u = (float)kU;
+        const float u4 = 4.0f * u;
+        const float infl = 1.0f + 0.00390625f;
+        const float sqD = sqrtf((float)D) * 1.0001f;
+        if (warp == 4) {
+            float nm = 0.f, am = 0.f, vm = 0.f, bm = 0.f;
+            for (int j = lane; j < k; j += 32) {
+                const float4 c = colc[j];
+                nm = fmaxf(nm, c.x); am = fmaxf(am, c.y); vm = fmaxf(vm, c.z); bm = fmaxf(bm, c.w);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+                am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+                vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+                bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+            }
+            if (lane == 0) *segmx = make_float4(nm, am, vm, bm);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");       // the four epilogue warps
+        const float4 mx = *segmx;
+        const float cnorm_max = sqrtf(mx.x) * 1.0001f, nrm_max = mx.x * 1.0001f;
+        uint32_t tl = 0;
+        bool ok = true;
+        for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
+            const uint32_t buf = tl & 1;
+            const long long pix = tile * TM + r;
+            const bool valid = pix < g.n;
+            const float2 rsv = valid ? g.rs[pix] : make_float2(1.0f, 0.0f);
+            ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (tl >> 1) & 1, abort));
+            if (!ok) break;
+            tc_fence_after();
+            // pixel side: ||x' - s_x q_x|| <= 2^-4 ||x'|| + 2^-10 s_x sqrt(D) (= Dl) and
+            // ||s_x q_x|| <= ||x'|| + Dl (= X); Y adds the rounding of x' = fl(x - m)
+            const float sx = rsv.x, nx = rsv.y;
+            const float Dl = (0.0625f * nx + 0.0009765625f * sx * sqD) * 1.0001f + 1e-30f;
+            const float X = (nx + Dl) * infl;
+            const float Y = Dl + u * (X * 1.01f + Dl) * (1.0f + 4.0f * u);
+            const uint32_t taddr = tmem_base + ((uint32_t)(grp * 32) << 16) + buf * npad;
+            // pass 1: smallest score, lowest column on ties (four interleaved running minima);
+            // s_j = ||c*||^2 - 2 s_x s_j acc_j, the scales powers of two (exact products)
+            float sm[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};
+            int amv[4] = {0, 0, 0, 0};
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + (uint32_t)c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float sc = fmaf(-2.0f, v[j] * (sx * csc[c0 + j]), cn[c0 + j]);
+                    if (sc < sm[j & 3]) { sm[j & 3] = sc; amv[j & 3] = c0 + j; }
+                }
+            }
+            float smin = sm[0];
+            int amin = amv[0];
+#pragma unroll
+            for (int q = 1; q < 4; ++q)
+                if (sm[q] < smin || (sm[q] == smin && amv[q] < amin)) { smin = sm[q]; amin = amv[q]; }
+            const float4 ca = colc[amin];
+            const float U = smin + fmaf(X, ca.y, fmaf(Y, ca.z, fmaf(u4, fabsf(smin), ca.w))) * infl;
+            const float smax_abs = fmaf(2.0f * X * 1.02f, cnorm_max, nrm_max) + 1.0f;
+            const float Bmax = fmaf(X, mx.y, fmaf(Y, mx.z, fmaf(u4, smax_abs, mx.w))) * infl;
+            const float lim = U + 2.0f * Bmax;
+            int cnt = 0, last = amin;
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                float v[32];
+                tc_ld32(taddr + (uint32_t)c0, v);
+                uint32_t maybe = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    maybe |= (uint32_t)(fmaf(-2.0f, v[j] * (sx * csc[c0 + j]), cn[c0 + j]) <= lim) << j;
+                const uint32_t own = (amin >> 5) == (c0 >> 5) ? 1u << (amin & 31) : 0u;
+                uint32_t word = own;
+                if (__any_sync(0xffffffffu, (maybe & ~own) != 0u)) {
+                    word = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float4 c = colc[c0 + j];
+                        const float sc = fmaf(-2.0f, v[j] * (sx * csc[c0 + j]), c.x);
+                        const float B = fmaf(X, c.y, fmaf(Y, c.z, fmaf(u4, fabsf(sc), c.w))) * infl;
+                        word |= (uint32_t)(sc - B <= U) << j;
+                    }
+                }
+                cnt += __popc(word);
+                if (word) last = c0 + 31 - __clz(word);
+                maskbuf[r * kMaskWords + (c0 >> 5)] = word;
+            }
+            for (int w = npad >> 5; w < kMaskWords; ++w) maskbuf[r * kMaskWords + w] = 0u;
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);                    // every accumulator of the buffer read
+            const int lab = cnt == 1 ? last : amin;
+            if (valid) g.labels[pix] = (uint8_t)lab;
+            const bool flagged = valid && cnt > 1;
+            const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+            if (ballot) {
+                const int leader = __ffs(ballot) - 1;
+                unsigned basei = 0;
+                if (lane == leader) basei = atomicAdd(g.fl.count, (unsigned)__popc(ballot));
+                basei = __shfl_sync(0xffffffffu, basei, leader);
+                if (flagged) {
+                    const unsigned slot = basei + __popc(ballot & ((1u << lane) - 1u));
+                    if (slot < (unsigned long long)g.n) {
+                        g.fl.pix[slot] = (unsigned)pix;
+#pragma unroll
+                        for (int w = 0; w < kMaskWords; ++w)
+                            g.fl.mask[(size_t)slot * kMaskWords + w] = maskbuf[r * kMaskWords + w];
+                    }
+                }
+            }
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tmem_cols)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -989,6 +1311,71 @@ cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k, const 
     one.labels = labels;
     one.fl = fl;
     return launch_assign_bf16_seg(X, n, D, p, k, &one, 1, 0, -1, s);
+}
+
+bool fp8_supported(int D, int k)
+{
+    const int npad = (k + 31) / 32 * 32;
+    const int dpad = (D + F8_KC - 1) / F8_KC * F8_KC;
+    return D % 16 == 0 && k >= 1 && k <= kMaxK && (long long)npad * dpad <= F8_BMAX;
+}
+
+static size_t f8_smem_bytes(int npad, int D)
+{
+    const int nkc = (D + F8_KC - 1) / F8_KC;
+    size_t b = 1024;                                       // alignment slack
+    b += (size_t)F8_SA * F8_BOX + (size_t)nkc * npad * 128;
+    b += sizeof(float4) * npad + sizeof(float) * 2 * npad + sizeof(uint32_t) * TM * kMaskWords + sizeof(float4);
+    b += sizeof(uint64_t) * (2 * F8_SA + 1 + 4 + 1) + 16;
+    return b;
+}
+
+cudaError_t launch_assign_fp8(const float *X, long long n, int D, int k, const CodebookPrep &p, Fp8Feat f8,
+                              uint8_t *labels, FlagList fl, cudaStream_t s)
+{
+    if (!fp8_supported(D, k) || n < 1 || !f8.q || !f8.rs || !p.cq8 || !p.csc) return cudaErrorNotSupported;
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int npad = (k + 31) / 32 * 32;
+    const size_t smem = f8_smem_bytes(npad, D);
+    if (smem > (size_t)optin) return cudaErrorNotSupported;
+    {
+        const cudaError_t le_ = launch_pdl(fp8_quant_kernel, dim3(sms * 16), dim3(256), 0, s, X, n, D,
+                                           (const float *)p.mean, f8.q, f8.rs);
+        if (le_ != cudaSuccess) return le_;
+    }
+    CUtensorMap tmA, tmB;
+    if ((e = make_map(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, f8.q, (uint64_t)D, (uint64_t)n, (uint64_t)D, F8_KC,
+                      TM)) != cudaSuccess)
+        return e;
+    if ((e = make_map(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, p.cq8, (uint64_t)D, (uint64_t)k, (uint64_t)D, F8_KC,
+                      (uint32_t)npad)) != cudaSuccess)
+        return e;
+    F8Args a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.D = D;
+    a.k = k;
+    a.npad = npad;
+    a.nkc = (D + F8_KC - 1) / F8_KC;
+    a.ntiles = (n + TM - 1) / TM;
+    a.p = p;
+    a.rs = f8.rs;
+    a.labels = labels;
+    a.fl = fl;
+    e = cudaFuncSetAttribute(assign_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if ((e = record_kernel_event(VQNNF_OP_ASSIGN, 0, s)) != cudaSuccess) return e;
+    const long long grid = a.ntiles < sms ? a.ntiles : sms;
+    {
+        const cudaError_t le_ = launch_pdl(assign_fp8_kernel, dim3((unsigned)grid), dim3(F8_NT), smem, s, tmA, tmB, a);
+        if (le_ != cudaSuccess) return le_;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t read_and_clear_tc_error(int *out)

@@ -22,6 +22,14 @@ struct CodebookPrep {
     float *a;         // k       bound coefficient of ||x'||
     float *v;         // k       bound coefficient of the per-pixel rounding residual
     float *b;         // k       bound constant (error of nrm)
+    uint8_t *cq8;     // k x D   FP8 e4m3 of (c_j - m) / s_j                 (FP8 path)
+    float *csc;       // k       the power-of-two scale s_j                  (FP8 path)
+};
+
+// FP8 path: the features quantised per row (x - m = s_x q + residual, s_x a power of two).
+struct Fp8Feat {
+    uint8_t *q;       // n x D   FP8 e4m3 of (x - m) / s_x
+    float2 *rs;       // n       (s_x, upper bound of ||fl(x - m)||)
 };
 
 // List of pixels whose contraction result is ambiguous, with their candidate sets.
@@ -54,6 +62,10 @@ cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k,
 cudaError_t launch_assign_bf16(const float *X, long long n, int D, int k,
                                const CodebookPrep &p, uint8_t *labels, FlagList fl,
                                cudaStream_t s);
+// FP8 e4m3 contraction (quantisation of the features into f8, then tcgen05 kind::f8f6f4).
+bool fp8_supported(int D, int k);
+cudaError_t launch_assign_fp8(const float *X, long long n, int D, int k, const CodebookPrep &p, Fp8Feat f8,
+                              uint8_t *labels, FlagList fl, cudaStream_t s);
 // Several codebooks in one contraction: p holds krows prepared rows (the segments' columns,
 // padding rows included); the sum of the segments' ncol is at most 256.
 cudaError_t launch_assign_bf16_seg(const float *X, long long n, int D, const CodebookPrep &p, int krows,

@@ -11,6 +11,7 @@ namespace vqnnf {
 struct AssignWs {
     CodebookPrep prep;
     FlagList fl;
+    Fp8Feat f8;       // FP8 path only (null otherwise)
 };
 
 struct FitWs {
@@ -33,8 +34,8 @@ vqnnf_status from_cuda(cudaError_t e);
 bool check_prec(int prec, int D);
 int device_smem_optin();
 
-AssignWs carve_assign(WsCursor &c, long long n, int D, int k);
-FitWs carve_fit(WsCursor &c, long long l, int D, int k);
+AssignWs carve_assign(WsCursor &c, long long n, int D, int k, int prec = VQNNF_PREC_FP32);
+FitWs carve_fit(WsCursor &c, long long l, int D, int k, int prec = VQNNF_PREC_FP32);
 ScoreWs carve_score(WsCursor &c, int H, int W, int k, int th, int tw);
 
 // Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).

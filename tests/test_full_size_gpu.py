@@ -3,10 +3,10 @@ what the oracle can compute one by one.  Two workloads: the headline one (2048 x
 query, D = 512, k = 128, 128 x 128 template, F = 10) and the precision study's D = 1024
 variant (1024 x 1024 query, D = 1024, the same generator, codebook size and template).
 
-* codebook: bit-identical to the oracle's fit of the same template (BF16 and FP32 paths);
+* codebook: bit-identical to the oracle's fit of the same template (BF16, FP32 and FP8 paths);
 * template labels: every pixel against the oracle (outside the 1e-6 near-tie band);
-* query labels: BF16 == FP32 on every pixel outside the band, and both against the oracle on
-  a seeded sample plus every pixel where the two paths disagree;
+* query labels: BF16 == FP8 == FP32 on every pixel outside the band, and all three against the
+  oracle on a seeded sample plus every pixel where the paths disagree;
 * template counts: exact;
 * heatmap, at every window the score kernel's tiling could get wrong (the four corners, the
   whole first and last valid rows and columns, both sides of every 256-window seam, which
@@ -45,7 +45,7 @@ def run(request):
     q, T, info, bank = bench.make_workload(dev, cfg)
     s = torch.cuda.Stream(device=dev)
     out = {}
-    for prec in ("bf16", "fp32"):
+    for prec in ("bf16", "fp32", "fp8"):
         pipe = bench.Pipeline(vq, q.X, T, cfg, bank, prec, s)
         with torch.cuda.stream(s):
             pipe.step()
@@ -60,7 +60,7 @@ def run(request):
 def test_codebook_bit_exact(run):
     cfg, q, T, bank, out = run
     C_ref = oracle.fit_codebook(T.cpu().numpy(), cfg["k"], cfg["iters"], cfg["fit_seed"])
-    for prec in ("bf16", "fp32"):
+    for prec in ("bf16", "fp32", "fp8"):
         assert np.array_equal(out[prec]["C"].cpu().numpy(), C_ref), prec
 
 
@@ -69,7 +69,7 @@ def test_template_labels_and_counts(run):
     C = out["fp32"]["C"].cpu().numpy()
     ref, d1, d2 = oracle.assign(T.cpu().numpy(), C, return_dist=True)
     band = oracle.relative_gap(d1, d2) < 1e-6
-    for prec in ("bf16", "fp32"):
+    for prec in ("bf16", "fp32", "fp8"):
         got = out[prec]["tl"].cpu().numpy().astype(np.int32)
         assert int(((got != ref) & ~band).sum()) == 0, prec
         tc = oracle.filter_counts(got, cfg["k"], bank)
@@ -81,17 +81,18 @@ def test_query_labels(run):
     C = out["fp32"]["C"].cpu().numpy()
     lb = out["bf16"]["ql"].view(-1)
     lf = out["fp32"]["ql"].view(-1)
-    diff = (lb != lf).nonzero().view(-1)
+    l8 = out["fp8"]["ql"].view(-1)
+    diff = ((lb != lf) | (l8 != lf)).nonzero().view(-1)
     rng = np.random.default_rng(7)
     sample = torch.as_tensor(rng.choice(lb.numel(), 4096, replace=False), device=lb.device)
     idx = torch.unique(torch.cat([diff[:20000], sample]))
     X = q.X.view(-1, cfg["D"])[idx].cpu().numpy()
     ref, d1, d2 = oracle.assign(X[None], C, return_dist=True)
     ref, band = ref[0], (oracle.relative_gap(d1, d2) < 1e-6)[0]
-    for name, lab in (("bf16", lb), ("fp32", lf)):
+    for name, lab in (("bf16", lb), ("fp32", lf), ("fp8", l8)):
         got = lab[idx].cpu().numpy().astype(np.int32)
         assert int(((got != ref) & ~band).sum()) == 0, name
-    # every disagreement between the two paths lies in the near-tie band
+    # every disagreement between the paths lies in the near-tie band
     assert diff.numel() <= 20000
     in_diff = torch.isin(idx, diff).cpu().numpy()
     assert bool(band[in_diff].all())
@@ -119,7 +120,7 @@ def test_heatmap_exact_at_edges_and_seams(run):
     cfg, q, T, bank, out = run
     k, th, tw = cfg["k"], cfg["th"], cfg["tw"]
     coef = np.array([f["w_f"] / f["area"] for f in bank])
-    for prec in ("bf16", "fp32"):
+    for prec in ("bf16", "fp32", "fp8"):
         ql_d, tc_d = out[prec]["ql"], out[prec]["tc"]
         ql = ql_d.cpu().numpy().astype(np.int32)
         tc = tc_d.cpu().numpy()

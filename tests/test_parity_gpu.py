@@ -57,7 +57,7 @@ def _codebook_case(H, W, D, k, seed, iters=3):
     return q, T, C
 
 
-PRECS = ["fp32", "bf16"]
+PRECS = ["fp32", "bf16", "fp8"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -73,8 +73,8 @@ PRECS = ["fp32", "bf16"]
 ])
 def test_assign_parity(vq, prec, H, W, D, k):
     q, _, C = _codebook_case(H, W, D, k, seed=H * 7 + W)
-    if prec == "bf16" and D % 16:
-        # the tensor path needs D % 16 == 0: refused on the host, nothing launched
+    if prec != "fp32" and D % 16:
+        # the tensor paths need D % 16 == 0: refused on the host, nothing launched
         with pytest.raises(vq.VqnnfError) as e:
             vq.vqnnf_assign(_dev(q.X), _dev(C), prec)
         assert e.value.status == 5
@@ -86,6 +86,25 @@ def test_assign_parity(vq, prec, H, W, D, k):
     assert bad == 0, f"{bad} labels differ outside the near-tie band ({inband} in band)"
     n_flag, n_cand, n_deep, _ = stats.cpu().tolist()
     assert 0 <= n_flag <= H * W and n_cand >= 2 * n_flag and n_deep <= n_flag
+
+
+def test_assign_fp8_limits_and_wide_range_rows(vq):
+    """FP8: a codebook too large to stay in shared memory is refused on the host; rows whose
+    values span many binades (most of them quantise to zero or to the subnormal range of e4m3)
+    still get exact labels, the bound flagging what the contraction cannot decide."""
+    X = torch.zeros((4, 4, 1024), device="cuda")
+    C = torch.zeros((129, 1024), device="cuda")
+    with pytest.raises(vq.VqnnfError) as e:
+        vq.vqnnf_assign(X, C, "fp8")
+    assert e.value.status == 5
+    r = np.random.default_rng(12)
+    Xh = (r.random((33, 29, 128)) * np.exp2(r.integers(-30, 4, (33, 29, 128)))).astype(np.float32)
+    Ch = Xh.reshape(-1, 128)[r.choice(33 * 29, 24, replace=False)] * np.float32(1.001)
+    ref, d1, d2 = oracle.assign(Xh, Ch, return_dist=True)
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    got = vq.vqnnf_assign(_dev(Xh), _dev(Ch), "fp8", stats=stats).cpu().numpy()
+    bad, _ = _labels_ok(got, ref, d1, d2)
+    assert bad == 0
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -61,7 +61,7 @@ def _noalloc(lib, X, C, prec):
     return lab, st
 
 
-@pytest.mark.parametrize("prec", [0, 1])     # FP32 SIMT / BF16 tcgen05 contraction, re-scored
+@pytest.mark.parametrize("prec", [0, 1, 2])  # FP32 SIMT / BF16 / FP8 tcgen05 contraction, re-scored
 def test_noalloc_matches_assign_on_consecutive_calls(lib, prec):
     cases = [_case(200, 180, 64, 16, 11), _case(97, 131, 128, 32, 12)]
     for X, C in cases + cases[:1]:       # three calls in a row, the first input repeated
