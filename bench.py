@@ -41,11 +41,11 @@ OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,954,432 + 5,192,192 bytes),
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,862,784 + 5,067,520 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2147954432 + 5192192) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "d2d644ec7e70dddd8450fd4488401cf0a6c5b050ce2a54abe35eabea25ba5ce6"
+TC_TRAFFIC_PER_PX = (2147862784 + 5067520) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "b4ab6b74f3123c4ec705890da47c9d6f21dfa07067a9867f0d6cef30517b5ac2"
 
 
 
@@ -432,6 +432,16 @@ def roofline(cfg, prec, kernel_ms, peaks, src):
                 "kernel": "assign_tc_kernel (tcgen05 BF16 contraction + interval test), query launch",
                 "kernel_ms": round(float(kernel_ms), 4),
                 "algorithmic_bytes_per_px": D * 4 + 1, "peak_source": src + " (burst copy)"}
+    if prec == "fp8":
+        # HBM-bound: the e4m3 features (D bytes), the row's scale and norm (8) and the label (1)
+        bytes_ = L * (D + 8 + 1)
+        ach = bytes_ / (kernel_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": None,
+                "kernel": "assign_fp8_kernel (tcgen05 e4m3 contraction + interval test), query launch",
+                "kernel_ms": round(float(kernel_ms), 4),
+                "algorithmic_bytes_per_px": D + 9, "peak_source": src + " (burst copy)"}
     # FP32 SIMT: bound by the FP32 FMA pipes, 152 SMs x 128 lanes x 2 flop x max SM clock
     flops = 2.0 * L * D * k
     ach = flops / (kernel_ms * 1e-3) / 1e12
