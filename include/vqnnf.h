@@ -207,8 +207,8 @@ vqnnf_status vqnnf_score(const uint8_t *q_labels, int H, int W, int k, int th, i
  *   C     device, k x D;  tau > 0;  1 <= G <= 4;  wf: device, G*G float32
  *   heat  device, B x (H - th + 1) x (W - tw + 1) float32, written
  *   ws    device workspace of vqnnf_soft_workspace_bytes() bytes, 256-byte aligned; it keeps
- *         the template soft counts, the query cell sums and the per-filter L1 maps for the
- *         backward call with the same arguments (the softmax itself is recomputed there).
+ *         the soft assignments, the template soft counts, the query cell sums and the
+ *         per-filter L1 maps for the backward call with the same arguments.
  * Limits: k <= 128, D <= 512, k * D <= 32768, B * k <= 65535, H <= 65535, W <= 12288,
  * B * k * H < 2^31, B * k * H * W < 2^40 (else VQNNF_EUNSUPPORTED). */
 size_t vqnnf_soft_workspace_bytes(int B, int H, int W, int D, int k, int th, int tw, int G);

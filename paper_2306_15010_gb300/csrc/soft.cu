@@ -16,7 +16,7 @@
 //   m_fj(y,x)    = -(w_f / A_f) Gw(y,x) sign(Q_fj(y,x) - T_fj)          (dL/dQ_fj)
 //   dL/dT_fj     = - sum_{y,x} m_fj(y,x)
 //   g_j(u)       = sum_f sum_{windows whose cell f covers u} m_fj         (adjoint box sums)
-//   a_j(u)       = -(1/tau) p_j (g_j - sum_i p_i g_i)                    (softmax recomputed)
+//   a_j(u)       = -(1/tau) p_j (g_j - sum_i p_i g_i)                    (p kept from the forward)
 //   dL/dx_u      = 2 (sum_j a_j) x_u - 2 sum_j a_j c_j
 //   dL/dc_j      = -2 sum_u a_j(u) x_u + 2 (sum_u a_j(u)) c_j   (query and template pixels)
 #include <cfloat>
@@ -255,22 +255,26 @@ __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__r
 //   Z[x'] = sum over cells f of class s with window (y' - y0_f, x' - x0_f) valid of
 //           m_fj = -(w_f / A_f) dheat sign(Q_fj - T_fj), Q_fj(window) = BX[y'][x'], x' <= W - w,
 // kept in shared memory, then the row pass of the adjoint box sum
-//   R2[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[x']   (direct sums).
-// Also dT_fj += -m_fj (block sums, then one atomic per block and filter).  The class's cells
-// (at most G * G) are staged in shared memory first, so the per-pixel loop has uniform guards
-// and its dheat loads do not wait on one another.
-constexpr int GROWS = 4;           // rows per block of the gradient gather
+//   R2[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[x']
+// as a difference of two prefix sums of Z (a warp scan per 32 entries; two warps per row).
+// Prefix sums are safe here although the forward avoids them: these are gradient entries with
+// a tolerance relative to the largest one, and the prefix of a row of ~W terms rounds at
+// ~W * 2^-24 of its own magnitude.  Also dT_fj += -m_fj (block sums, then one atomic per block
+// and filter).  The class's cells (at most G * G) are staged in shared memory first, with a
+// row pointer into dheat per cell, so the per-pixel loop has uniform guards and no division.
+constexpr int GROWS = 4;           // rows per block of the gradient gather (two warps per row)
 template <int MC>                  // MC >= number of cells in class s
 __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
                                                           const float *__restrict__ T, const float *__restrict__ wf,
                                                           int H, int W, int k, int HO, int WO, SoftGrid sg, int s,
                                                           float *__restrict__ R2, float *__restrict__ dT)
 {
-    extern __shared__ float zrow[];                           // [GROWS][W]
+    extern __shared__ float zrow[];                           // [GROWS][W]: Z, then its prefix sums
     __shared__ int c_y0[MC], c_x0[MC], c_f[MC];
     __shared__ float c_t[MC], c_coef[MC];
     __shared__ int n_cell;
     __shared__ float red[MC][8];
+    __shared__ float half_tot[GROWS];
     const int h = sg.hgt[sg.size_h[s]], w = sg.wid[sg.size_w[s]];
     const int nrow = H - h + 1, nrb = (nrow + GROWS - 1) / GROWS;
     const long long bj = blockIdx.x / nrb;
@@ -296,39 +300,66 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
     for (int c = 0; c < MC; ++c) dt[c] = 0.f;
     const int xm = W - w;
     const int nr = min(GROWS, nrow - yb);
-    for (int e = threadIdx.x; e < nr * (xm + 1); e += blockDim.x) {
-        const int r = e / (xm + 1), x = e % (xm + 1), y = yb + r;
-        const float q = BX[((size_t)(b * sg.ns + s) * k + j) * H * W + (size_t)y * W + x];
-        float z = 0.f;
+    const float *bxp = BX + ((size_t)(b * sg.ns + s) * k + j) * H * W;
+    for (int r = 0; r < nr; ++r) {
+        const int y = yb + r;
+        const float *brow = bxp + (size_t)y * W;
+        float *zr = zrow + r * W;
+        for (int x = threadIdx.x; x <= xm; x += blockDim.x) {
+            const float q = brow[x];
+            float z = 0.f;
 #pragma unroll
-        for (int c = 0; c < MC; ++c) {
-            if (c >= nc) break;                               // uniform
-            const int wy = y - c_y0[c], wx = x - c_x0[c];
-            const bool ok = wy >= 0 && wy < HO && wx >= 0 && wx < WO;
-            const float d = ok ? dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
-            const float t = c_t[c];
-            const float sgn = q > t ? 1.f : (q < t ? -1.f : 0.f);
-            const float m = c_coef[c] * d * sgn;
-            z += m;
-            dt[c] -= m;
+            for (int c = 0; c < MC; ++c) {
+                if (c >= nc) break;                           // uniform
+                const int wy = y - c_y0[c], wx = x - c_x0[c];
+                const bool ok = wy >= 0 && wy < HO && wx >= 0 && wx < WO;
+                const float d = ok ? dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
+                const float t = c_t[c];
+                const float sgn = q > t ? 1.f : (q < t ? -1.f : 0.f);
+                const float m = c_coef[c] * d * sgn;
+                z += m;
+                dt[c] -= m;
+            }
+            zr[x] = z;
         }
-        zrow[r * W + x] = z;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * W; e += blockDim.x) {
-        const int r = e / W, ux = e % W;
-        const float *zr = zrow + r * W;
-        const int lo = max(0, ux - w + 1), hi = min(ux, xm);
-        float a0 = 0.f, a1 = 0.f;
-        int xp = lo;
-        for (; xp + 1 <= hi; xp += 2) {
-            a0 += zr[xp];
-            a1 += zr[xp + 1];
-        }
-        if (xp <= hi) a0 += zr[xp];
-        R2[((size_t)bj * H + yb + r) * W + ux] = a0 + a1;
-    }
+    // inclusive prefix sums of Z[0 .. xm] per row: warp 2r + hf scans half hf of row r
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int len = xm + 1, mid = ((len + 63) >> 6) << 5;    // first half: a multiple of 32 entries
+    {
+        const int r = wp >> 1, hf = wp & 1;
+        const int x_lo = hf ? mid : 0, x_hi = hf ? len : min(mid, len);
+        float carry = 0.f;
+        if (r < nr) {
+            float *zr = zrow + r * W;
+            for (int x0 = x_lo; x0 < x_hi; x0 += 32) {
+                const int x = x0 + lane;
+                float v = x < x_hi ? zr[x] : 0.f;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
+                }
+                v += carry;
+                if (x < x_hi) zr[x] = v;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+            if (hf == 0 && lane == 0) half_tot[r] = carry;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < nr; ++r) {
+        const float *zr = zrow + r * W;
+        const float off = half_tot[r];
+        float *out = R2 + ((size_t)bj * H + yb + r) * W;
+        for (int ux = threadIdx.x; ux < W; ux += blockDim.x) {
+            const int a = min(ux, xm), l = ux - w;
+            const float sa = zr[a] + (a >= mid ? off : 0.f);
+            const float sl = l >= 0 ? zr[l] + (l >= mid ? off : 0.f) : 0.f;
+            out[ux] = sa - sl;
+        }
+    }
 #pragma unroll
     for (int c = 0; c < MC; ++c) {
         if (c >= nc) break;                                   // uniform
@@ -383,30 +414,39 @@ __global__ void tmpl_grad_kernel(const float *__restrict__ dT, int th, int tw, i
     Gt[e] = s;
 }
 
-// Softmax backward with the softmax recomputed: a_j = -(1/tau) p_j (g_j - sum_i p_i g_i),
-// A pixel-major; dX = 2 (sum_j a_j) x - 2 sum_j a_j c_j (skipped when dX is null).
+// Softmax backward from the forward's soft assignment P (planar, as soft_p_kernel wrote it):
+// a_j = -(1/tau) p_j (g_j - sum_i p_i g_i), A pixel-major; dX = 2 (sum_j a_j) x - 2 sum_j a_j c_j
+// (skipped when dX is null).
 template <int KI>
 __global__ void __launch_bounds__(256) soft_back_kernel(const float *__restrict__ X, long long n, long long npi,
                                                         int D, const float *__restrict__ C, int k, float tau,
-                                                        const float *__restrict__ Gp, float *__restrict__ A,
-                                                        float *__restrict__ dX)
+                                                        const float *__restrict__ P, const float *__restrict__ Gp,
+                                                        float *__restrict__ A, float *__restrict__ dX)
 {
     extern __shared__ __align__(16) float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
     float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
     float *as = sm + (PT + 16 * KI) * (DCH + 1);             // [PT][k + 1]: g, then a
     float *asum_s = as + PT * (16 * KI + 1);                  // [PT]
+    float *ps = asum_s + PT + 16 * KI * (PT + 4);             // [PT][k + 1]: p
     const long long p0 = (long long)blockIdx.x * PT;
-    float pr[PPT][KI];
-    tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
     const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
-    // g of the tile's pixels, coalesced along pixels of each plane
+    // p and g of the tile's pixels, coalesced along pixels of each plane
     const long long it0 = p0 / npi, of0 = p0 - it0 * npi;
     for (int e = t; e < k * PT; e += blockDim.x) {
         const int j = e / PT, pp = e % PT;
-        as[pp * (k + 1) + j] = p0 + pp < n ? Gp[planar_index(it0, of0, pp, j, k, npi)] : 0.f;
+        const bool in = p0 + pp < n;
+        const long long o = in ? planar_index(it0, of0, pp, j, k, npi) : 0;
+        as[pp * (k + 1) + j] = in ? Gp[o] : 0.f;
+        ps[pp * (k + 1) + j] = in ? P[o] : 0.f;
     }
     __syncthreads();
+    float pr[PPT][KI];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r)
+#pragma unroll
+        for (int i = 0; i < KI; ++i)
+            pr[r][i] = cl + 16 * i < k ? ps[(pg * PPT + r) * (k + 1) + cl + 16 * i] : 0.f;
     const float it = 1.0f / tau;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
@@ -583,21 +623,31 @@ cudaError_t launch_soft_p(const float *X, long long n, long long npi, int D, con
 
 template <int KI>
 cudaError_t launch_soft_back_ki(const float *X, long long n, long long npi, int D, const float *C, int k,
-                                float tau, const float *Gp, float *A, float *dX, cudaStream_t s)
+                                float tau, const float *P, const float *Gp, float *A, float *dX, cudaStream_t s)
 {
-    const size_t sm = sizeof(float) * ((PT + 16 * KI) * (DCH + 1) + PT * (16 * KI + 1) + PT + 16 * KI * (PT + 4));
+    const size_t sm = sizeof(float) * ((PT + 16 * KI) * (DCH + 1) + 2 * PT * (16 * KI + 1) + PT + 16 * KI * (PT + 4));
     cudaError_t e = cudaFuncSetAttribute(soft_back_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    soft_back_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, Gp, A, dX);
+    soft_back_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, P, Gp, A, dX);
     return cudaGetLastError();
 }
 
 cudaError_t launch_soft_back(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
-                             const float *Gp, float *A, float *dX, cudaStream_t s)
+                             const float *P, const float *Gp, float *A, float *dX, cudaStream_t s)
 {
-    if (k <= 32) return launch_soft_back_ki<2>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
-    if (k <= 64) return launch_soft_back_ki<4>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
-    return launch_soft_back_ki<8>(X, n, npi, D, C, k, tau, Gp, A, dX, s);
+    if (k <= 32) return launch_soft_back_ki<2>(X, n, npi, D, C, k, tau, P, Gp, A, dX, s);
+    if (k <= 64) return launch_soft_back_ki<4>(X, n, npi, D, C, k, tau, P, Gp, A, dX, s);
+    return launch_soft_back_ki<8>(X, n, npi, D, C, k, tau, P, Gp, A, dX, s);
+}
+
+template <int MC>
+cudaError_t launch_gather(dim3 grid, size_t zs, const SoftWs &w, const float *dheat, const float *wf, int H, int W,
+                          int k, int HO, int WO, const SoftGrid &sg, int is, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(soft_gather_kernel<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
+    if (e != cudaSuccess) return e;
+    soft_gather_kernel<MC><<<grid, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -654,7 +704,7 @@ SoftWs carve_soft(WsCursor &c, int B, int H, int W, int D, int k, int th, int tw
     w.Pt = c.take<float>((size_t)k * th * tw);
     w.T = c.take<float>((size_t)sg.F * k);
     w.L1 = c.take<float>((size_t)B * sg.F * (H - th + 1) * (W - tw + 1));
-    w.R2 = w.P;                                               // and the soft-assignment area
+    w.R2 = c.take<float>((size_t)B * k * plane);
     w.G = c.take<float>((size_t)B * k * plane);
     w.A = c.take<float>((size_t)B * k * plane);
     w.At = c.take<float>((size_t)k * th * tw);
@@ -710,22 +760,19 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
         int ncell = 0;
         for (int f = 0; f < sg.F; ++f) ncell += sg.cell[f].s == is;
         const dim3 gg((unsigned)(planes * ((H - h + GROWS) / GROWS)));
-        const size_t zs = sizeof(float) * GROWS * W;
-        if (ncell <= 4)
-            soft_gather_kernel<4><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
-        else if (ncell <= 9)
-            soft_gather_kernel<9><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
-        else
-            soft_gather_kernel<kSoftMaxG * kSoftMaxG><<<gg, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg,
-                                                                         is, w.R2, w.dT);
+        const size_t zs = sizeof(float) * GROWS * W;          // up to 192 KB (W <= 12288)
+        e = ncell <= 4 ? launch_gather<4>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s)
+            : ncell <= 9 ? launch_gather<9>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s)
+                         : launch_gather<kSoftMaxG * kSoftMaxG>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s);
+        if (e != cudaSuccess) return e;
         dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
         adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
     }
-    e = launch_soft_back(Qf, nq, (long long)H * W, D, C, k, tau, w.G, w.A, dQf, s);
+    e = launch_soft_back(Qf, nq, (long long)H * W, D, C, k, tau, w.P, w.G, w.A, dQf, s);
     if (e != cudaSuccess) return e;
     // template side: pixel gradients from dT, then its softmax backward (no feature gradient)
     tmpl_grad_kernel<<<(unsigned)((k * nt + 255) / 256), 256, 0, s>>>(w.dT, th, tw, k, sg, w.G);
-    e = launch_soft_back(Tf, nt, nt, D, C, k, tau, w.G, w.At, nullptr, s);
+    e = launch_soft_back(Tf, nt, nt, D, C, k, tau, w.Pt, w.G, w.At, nullptr, s);
     if (e != cudaSuccess) return e;
     dim3 gp((k + 63) / 64, (D + 63) / 64, kSoftSlices);
     dc_partial_kernel<<<gp, 256, 0, s>>>(w.A, Qf, nq, D, k, kSoftSlices, w.part);

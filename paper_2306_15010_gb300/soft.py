@@ -3,8 +3,8 @@
 ``soft_heatmap(Qf, Tf, C, wf, tau, G)`` is a ``torch.autograd.Function``: the forward is
 ``vqnnf_soft_forward`` (soft assignment p_j = softmax(-||x - c_j||^2 / tau), soft counts over
 the G x G template grid cells, Eq. 2 with the L1 norm), the backward ``vqnnf_soft_backward``
-(gradients for the query features, the centroids and the filter weights; the softmax is
-recomputed there, the workspace of the forward keeps the cell sums).  All work runs in the
+(gradients for the query features, the centroids and the filter weights; the workspace of
+the forward keeps the soft assignments and the cell sums for it).  All work runs in the
 library's kernels; this module only marshals tensors.
 """
 from __future__ import annotations
