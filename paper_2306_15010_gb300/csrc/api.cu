@@ -696,10 +696,11 @@ vqnnf_status vqnnf_set_kernel_events(int op, void *start_event, void *stop_event
 vqnnf_status vqnnf_last_device_error(void *stream)
 {
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return VQNNF_ECUDA;
-    int err = 0, err2 = 0;
+    int err = 0, err2 = 0, err3 = 0;
     if (read_and_clear_tc_error(&err) != cudaSuccess) return VQNNF_ECUDA;
     if (read_and_clear_score_error(&err2) != cudaSuccess) return VQNNF_ECUDA;
-    return (err || err2) ? VQNNF_ETIMEOUT : VQNNF_OK;
+    if (read_and_clear_soft_error(&err3) != cudaSuccess) return VQNNF_ECUDA;
+    return (err || err2 || err3) ? VQNNF_ETIMEOUT : VQNNF_OK;
 }
 
 vqnnf_status vqnnf_selftest_bounded_wait(long long limit_cycles, void *stream)

@@ -710,6 +710,7 @@ SoftWs carve_soft(WsCursor &c, int B, int H, int W, int D, int k, int th, int tw
     w.At = c.take<float>((size_t)k * th * tw);
     w.dT = c.take<float>((size_t)sg.F * k);
     w.part = c.take<float>((size_t)2 * kSoftSlices * ((size_t)k * D + k));
+    w.ct = c.take<uint8_t>(soft_ct_image_bytes(D));
     return w;
 }
 
@@ -767,6 +768,21 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
         if (e != cudaSuccess) return e;
         dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
         adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
+    }
+    const size_t kDk = (size_t)k * D + k;
+    if (soft_tc_supported(D, k)) {                            // tensor-core contractions
+        int nqs = 0, nts = 0;
+        e = launch_soft_ct_image(C, k, D, w.ct, s);
+        if (e != cudaSuccess) return e;
+        e = launch_soft_grad_tc(Qf, nq, (long long)H * W, D, k, tau, w.P, w.G, w.ct, dQf, w.part, kSoftSlices,
+                                &nqs, s);
+        if (e != cudaSuccess) return e;
+        tmpl_grad_kernel<<<(unsigned)((k * nt + 255) / 256), 256, 0, s>>>(w.dT, th, tw, k, sg, w.G);
+        e = launch_soft_grad_tc(Tf, nt, nt, D, k, tau, w.Pt, w.G, w.ct, nullptr, w.part + (size_t)nqs * kDk,
+                                kSoftSlices, &nts, s);
+        if (e != cudaSuccess) return e;
+        dc_reduce_kernel<<<(k * D + 255) / 256, 256, 0, s>>>(w.part, nqs + nts, D, k, C, dC);
+        return cudaGetLastError();
     }
     e = launch_soft_back(Qf, nq, (long long)H * W, D, C, k, tau, w.P, w.G, w.A, dQf, s);
     if (e != cudaSuccess) return e;

@@ -39,9 +39,22 @@ struct SoftWs {
     float *At;     // th x tw x k       dL/dd of the template pixels
     float *dT;     // F x k             dL/dT
     float *part;   // 2 kSoftSlices x (k D + k) partial centroid gradients (query, template)
+    uint8_t *ct;   // C^T hi/lo image of the tensor-core gradient kernel (soft_tc.cu)
 };
 
 bool soft_grid(int th, int tw, int G, SoftGrid &sg);
+
+// Tensor-core gradient contractions (soft_tc.cu): dX = 2 (sum_j a_j) x - 2 A C and the per-CTA
+// partials Y_j = sum_u a_j(u) x_u, S_j = sum_u a_j(u) in part[slice][j D + d], part[slice][k D + j]
+// (slices = CTAs launched, written to *slices).  Supported when k <= 64 and the operands fit in
+// shared memory (soft_tc_supported); dX may be null.
+bool soft_tc_supported(int D, int k);
+size_t soft_ct_image_bytes(int D);
+cudaError_t launch_soft_ct_image(const float *C, int k, int D, uint8_t *img, cudaStream_t s);
+cudaError_t launch_soft_grad_tc(const float *X, long long n, long long npi, int D, int k, float tau,
+                                const float *P, const float *G, const uint8_t *ct_img, float *dX, float *part,
+                                int max_slices, int *slices, cudaStream_t s);
+cudaError_t read_and_clear_soft_error(int *out);
 size_t soft_workspace_bytes(int B, int H, int W, int D, int k, int th, int tw, const SoftGrid &sg);
 SoftWs carve_soft(WsCursor &c, int B, int H, int W, int D, int k, int th, int tw, const SoftGrid &sg);
 cudaError_t soft_forward(const float *Qf, int B, int H, int W, const float *Tf, int th, int tw, int D,
