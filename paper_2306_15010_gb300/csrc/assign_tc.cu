@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
         bool ok = true;
         for (long long tile = blockIdx.x; ok && tile < g.ntiles; tile += gridDim.x, ++tl) {
             const uint32_t nb = tl & 1;
-            float xa2 = 0.f, xb2 = 0.f;                     // partial ||x'||^2 of this quarter
+            float2 x2 = make_float2(0.f, 0.f);              // partial ||x'||^2 of this quarter (even, odd columns)
             for (int kc = 0; kc < nkc; ++kc) {
                 ok = __all_sync(0xffffffffu, mbar_wait(&a_empty[sa], pa ^ 1, abort));
                 ok = __all_sync(0xffffffffu, ok && mbar_wait(&full_f[sf], pf, abort));
@@ -510,16 +510,22 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
                         const float4 m0 = *reinterpret_cast<const float4 *>(mean + d0);
                         const float4 m1 = *reinterpret_cast<const float4 *>(mean + d0 + 4);
                         const float4 v0 = v[2 * cc], v1 = v[2 * cc + 1];
-                        const float xs[8] = {v0.x - m0.x, v0.y - m0.y, v0.z - m0.z, v0.w - m0.w,
-                                             v1.x - m1.x, v1.y - m1.y, v1.z - m1.z, v1.w - m1.w};
+                        // pairs of columns on the packed FP32 lanes, each rounded as the scalar
+                        // operation: x' = fma(m, -1, x) = fl(x - m), the residual x' - hi (exact)
+                        // and the norm's FMA
+                        const float2 xv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
+                                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
+                        const float2 mv[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w),
+                                              make_float2(m1.x, m1.y), make_float2(m1.z, m1.w)};
+                        const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            const float xa = xs[2 * q], xb = xs[2 * q + 1];
+                            const float2 xs = __ffma2_rn(mv[q], neg1, xv[q]);
                             float ha, hb, la, lb;
-                            hw[4 * cc + q] = pack_bf16(xa, xb, ha, hb);
-                            xa2 = fmaf(xa, xa, xa2);
-                            xb2 = fmaf(xb, xb, xb2);
-                            lw[4 * cc + q] = pack_bf16(xa - ha, xb - hb, la, lb);   // exact residuals
+                            hw[4 * cc + q] = pack_bf16(xs.x, xs.y, ha, hb);
+                            x2 = __ffma2_rn(xs, xs, x2);
+                            const float2 rs = __ffma2_rn(make_float2(ha, hb), neg1, xs);
+                            lw[4 * cc + q] = pack_bf16(rs.x, rs.y, la, lb);   // exact residuals
                         }
                     } else {
 #pragma unroll
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(NT, 1) assign_tc_kernel(const __grid_constant_
             if (!ok) break;
             ok = __all_sync(0xffffffffu, mbar_wait(&nrm_empty[nb], ((tl >> 1) & 1) ^ 1, abort));
             if (!ok) break;
-            norms[(nb * 4 + qt) * TM + r] = xa2 + xb2;
+            norms[(nb * 4 + qt) * TM + r] = x2.x + x2.y;
             mbar_arrive(&nrm_full[nb]);
         }
     } else if (warp >= 18 && warp < 22) {

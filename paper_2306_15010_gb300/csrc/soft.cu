@@ -47,18 +47,22 @@ __device__ __forceinline__ long long planar_index(long long it0, long long of0, 
 
 // Distances of a 64-pixel tile to all k centroids and the softmax over each pixel's k logits.
 // Thread t = 16 pg + cl owns pixels 4 pg .. 4 pg + 3 and centroids cl, cl + 16, ...; the 16
-// threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.
+// threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.  The
+// direct differences run on packed pairs of pixels (two FP32 lanes per instruction, each
+// rounded as the scalar subtraction and FMA would be): the centroid chunk is staged negated
+// and duplicated, cs[j][dd] = (-c, -c), so one add and one FMA cover two (pixel, centroid)
+// pairs.
 template <int KI>
 __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long long n, long long p0, int D,
                                              const float *__restrict__ C, int k, float tau, float (*xs)[DCH + 1],
-                                             float (*cs)[DCH + 1], float (*pr)[KI])
+                                             float2 (*cs)[DCH + 1], float (*pr)[KI])
 {
     const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
-    float acc[PPT][KI];
+    float2 acc[PPT / 2][KI];
 #pragma unroll
-    for (int r = 0; r < PPT; ++r)
+    for (int r = 0; r < PPT / 2; ++r)
 #pragma unroll
-        for (int i = 0; i < KI; ++i) acc[r][i] = 0.f;
+        for (int i = 0; i < KI; ++i) acc[r][i] = make_float2(0.f, 0.f);
     for (int d0 = 0; d0 < D; d0 += DCH) {
         __syncthreads();
         for (int e = t; e < PT * DCH; e += blockDim.x) {
@@ -68,46 +72,51 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
         }
         for (int e = t; e < k * DCH; e += blockDim.x) {
             const int j = e / DCH, dd = e % DCH;
-            cs[j][dd] = d0 + dd < D ? C[(size_t)j * D + d0 + dd] : 0.f;
+            const float c = d0 + dd < D ? -C[(size_t)j * D + d0 + dd] : 0.f;
+            cs[j][dd] = make_float2(c, c);
         }
         __syncthreads();
 #pragma unroll 2
         for (int dd = 0; dd < DCH; ++dd) {
-            float xv[PPT], cv[KI];
+            float2 xv[PPT / 2], cv[KI];
 #pragma unroll
-            for (int r = 0; r < PPT; ++r) xv[r] = xs[pg * PPT + r][dd];
+            for (int r = 0; r < PPT / 2; ++r)
+                xv[r] = make_float2(xs[pg * PPT + 2 * r][dd], xs[pg * PPT + 2 * r + 1][dd]);
 #pragma unroll
-            for (int i = 0; i < KI; ++i) cv[i] = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : 0.f;
+            for (int i = 0; i < KI; ++i) cv[i] = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int r = 0; r < PPT; ++r)
+            for (int r = 0; r < PPT / 2; ++r)
 #pragma unroll
                 for (int i = 0; i < KI; ++i) {
-                    const float df = xv[r] - cv[i];
-                    acc[r][i] = fmaf(df, df, acc[r][i]);
+                    const float2 df = __fadd2_rn(xv[r], cv[i]);
+                    acc[r][i] = __ffma2_rn(df, df, acc[r][i]);
                 }
         }
     }
     const float it = 1.0f / tau;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) {
+        float dr[KI];
+#pragma unroll
+        for (int i = 0; i < KI; ++i) dr[i] = (r & 1) ? acc[r >> 1][i].y : acc[r >> 1][i].x;
         float dmin = FLT_MAX;
 #pragma unroll
         for (int i = 0; i < KI; ++i)
-            if (cl + 16 * i < k) dmin = fminf(dmin, acc[r][i]);
+            if (cl + 16 * i < k) dmin = fminf(dmin, dr[i]);
 #pragma unroll
         for (int o = 1; o < 16; o <<= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
         float s = 0.f;
 #pragma unroll
         for (int i = 0; i < KI; ++i) {
-            const float e = cl + 16 * i < k ? expf((dmin - acc[r][i]) * it) : 0.f;
-            acc[r][i] = e;
+            const float e = cl + 16 * i < k ? expf((dmin - dr[i]) * it) : 0.f;
+            dr[i] = e;
             s += e;
         }
 #pragma unroll
         for (int o = 1; o < 16; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         const float inv = 1.0f / s;
 #pragma unroll
-        for (int i = 0; i < KI; ++i) pr[r][i] = acc[r][i] * inv;
+        for (int i = 0; i < KI; ++i) pr[r][i] = dr[i] * inv;
     }
 }
 
@@ -118,10 +127,10 @@ __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X
                                                      int D, const float *__restrict__ C, int k, float tau,
                                                      float *__restrict__ P)
 {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
-    float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PT * (DCH + 1));
-    float *ps = sm + (PT + 16 * KI) * (DCH + 1);             // [k][PT + 1]
+    float2 (*cs)[DCH + 1] = reinterpret_cast<float2 (*)[DCH + 1]>(sm + PT * (DCH + 1));
+    float *ps = sm + (PT + 32 * KI) * (DCH + 1);             // [k][PT + 1]
     const long long p0 = (long long)blockIdx.x * PT;
     float pr[PPT][KI];
     tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
@@ -141,22 +150,40 @@ __global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X
 
 constexpr int SEG = 8;             // consecutive outputs per thread in the box passes
 
-// Row sums of width w: RW[row][x] = sum_{dx < w} P[row][x + dx], x <= W - w.  Thread: SEG
-// consecutive x, the first window summed directly, the next ones by sliding it.
-__global__ void row_box_kernel(const float *__restrict__ P, int W, int w, float *__restrict__ RW)
+// Row sums of width w: RW[row][x] = sum_{dx < w} P[row][x + dx], x <= W - w.  A block of 128
+// threads covers RBX = 128 SEG outputs of one row: the inputs it needs are staged in shared
+// memory with coalesced loads, thread t forms outputs SEG t .. SEG t + SEG - 1 (the first summed
+// directly, the next ones by sliding it), and the outputs leave through shared memory as
+// coalesced stores.  The shared arrays are skewed by one word per 32 so that the threads'
+// stride-SEG reads fall in distinct banks.
+constexpr int RBX = 128 * SEG;
+__device__ __forceinline__ int skew32(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr size_t row_box_smem(int w) { return sizeof(float) * ((RBX + w + (RBX + w) / 32 + 1) + (RBX + RBX / 32 + 1)); }
+__global__ void __launch_bounds__(128) row_box_kernel(const float *__restrict__ P, int W, int w, float *__restrict__ RW)
 {
+    extern __shared__ float rb[];
     const long long row = blockIdx.x;                          // rows in grid.x (> 65535 of them)
-    const int x0 = (blockIdx.y * blockDim.x + threadIdx.x) * SEG;
-    if (x0 > W - w) return;
-    const float *src = P + row * W;
-    float s = 0.f;
-    for (int dx = 0; dx < w; ++dx) s += src[x0 + dx];
-    const int xe = min(x0 + SEG, W - w + 1);
-    RW[row * W + x0] = s;
-    for (int x = x0 + 1; x < xe; ++x) {
-        s += src[x + w - 1] - src[x - 1];
-        RW[row * W + x] = s;
+    const int x0 = blockIdx.y * RBX, xm = W - w;
+    if (x0 > xm) return;                                       // uniform over the block
+    const int nout = min(RBX, xm - x0 + 1), nin = nout + w - 1;  // inputs x0 .. x0 + nin - 1 <= W - 1
+    float *ins = rb, *outs = rb + (RBX + w + (RBX + w) / 32 + 1);
+    const float *src = P + row * W + x0;
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) ins[skew32(i)] = src[i];
+    __syncthreads();
+    const int o0 = SEG * threadIdx.x;
+    if (o0 < nout) {
+        float s = 0.f;
+        for (int dx = 0; dx < w; ++dx) s += ins[skew32(o0 + dx)];
+        outs[skew32(o0)] = s;
+        const int oe = min(o0 + SEG, nout);
+        for (int o = o0 + 1; o < oe; ++o) {
+            s += ins[skew32(o + w - 1)] - ins[skew32(o - 1)];
+            outs[skew32(o)] = s;
+        }
     }
+    __syncthreads();
+    float *dst = RW + row * W + x0;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) dst[i] = outs[skew32(i)];
 }
 
 // Column sums of height h: BX[plane][y][x] = sum_{dy < h} RW[plane][y + dy][x], y <= H - h,
@@ -251,34 +278,35 @@ __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__r
     }
 }
 
-// Size class s (cells of height h, width w), one block per (plane b k + j, GROWS rows y' <= H - h):
-//   Z[x'] = sum over cells f of class s with window (y' - y0_f, x' - x0_f) valid of
-//           m_fj = -(w_f / A_f) dheat sign(Q_fj - T_fj), Q_fj(window) = BX[y'][x'], x' <= W - w,
+// Size class s (cells of height h, width w), one block per (item b, J consecutive planes j,
+// GR consecutive rows y' <= H - h):
+//   Z_j[x'] = sum over cells f of class s with window (y' - y0_f, x' - x0_f) valid of
+//             m_fj = -(w_f / A_f) dheat sign(Q_fj - T_fj), Q_fj(window) = BX_j[y'][x'], x' <= W - w,
 // kept in shared memory, then the row pass of the adjoint box sum
-//   R2[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z[x']
-// as a difference of two prefix sums of Z (a warp scan per 32 entries; two warps per row).
-// Prefix sums are safe here although the forward avoids them: these are gradient entries with
-// a tolerance relative to the largest one, and the prefix of a row of ~W terms rounds at
-// ~W * 2^-24 of its own magnitude.  Also dT_fj += -m_fj (block sums, then one atomic per block
-// and filter).  The class's cells (at most G * G) are staged in shared memory first, with a
-// row pointer into dheat per cell, so the per-pixel loop has uniform guards and no division.
-constexpr int GROWS = 4;           // rows per block of the gradient gather (two warps per row)
-template <int MC>                  // MC >= number of cells in class s
+//   R2_j[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z_j[x']
+// as a difference of two prefix sums of Z_j (a warp scan per 32 entries, one warp per row).
+// The window weights -(w_f / A_f) dheat do not depend on j: each thread loads them once per
+// pixel and applies them to its J planes.  Prefix sums are safe here although the forward
+// avoids them: these are gradient entries with a tolerance relative to the largest one, and the
+// prefix of a row of ~W terms rounds at ~W * 2^-24 of its own magnitude.  Also dT_fj += -m_fj
+// (block sums, then one atomic per block, filter and plane).  The class's cells (at most G * G)
+// are staged in shared memory first, so the per-pixel loop has uniform guards.
+constexpr int GR = 2;              // rows per block of the gradient gather
+template <int MC, int J>           // MC >= number of cells in class s; J planes per block
 __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
                                                           const float *__restrict__ T, const float *__restrict__ wf,
                                                           int H, int W, int k, int HO, int WO, SoftGrid sg, int s,
                                                           float *__restrict__ R2, float *__restrict__ dT)
 {
-    extern __shared__ float zrow[];                           // [GROWS][W]: Z, then its prefix sums
+    extern __shared__ float zrow[];                           // [J][GR][W]: Z, then its prefix sums
     __shared__ int c_y0[MC], c_x0[MC], c_f[MC];
-    __shared__ float c_t[MC], c_coef[MC];
+    __shared__ float c_t[MC][J], c_coef[MC];
     __shared__ int n_cell;
-    __shared__ float red[MC][8];
-    __shared__ float half_tot[GROWS];
+    __shared__ float red[MC * J][8];
     const int h = sg.hgt[sg.size_h[s]], w = sg.wid[sg.size_w[s]];
-    const int nrow = H - h + 1, nrb = (nrow + GROWS - 1) / GROWS;
-    const long long bj = blockIdx.x / nrb;
-    const int yb = (int)(blockIdx.x % nrb) * GROWS, b = (int)(bj / k), j = (int)(bj % k);
+    const int nrow = H - h + 1, nrb = (nrow + GR - 1) / GR, njg = (k + J - 1) / J;
+    const int rb = (int)(blockIdx.x % nrb), jg = (int)((blockIdx.x / nrb) % njg), b = (int)(blockIdx.x / nrb / njg);
+    const int yb = rb * GR, j0 = jg * J, nj = min(J, k - j0);
     if (threadIdx.x == 0) {
         int n = 0;
         for (int f = 0; f < sg.F && n < MC; ++f) {
@@ -287,7 +315,7 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
             c_y0[n] = c.y0;
             c_x0[n] = c.x0;
             c_f[n] = f;
-            c_t[n] = T[f * k + j];
+            for (int jj = 0; jj < J; ++jj) c_t[n][jj] = jj < nj ? T[f * k + j0 + jj] : 0.f;
             c_coef[n] = -(wf[f] / (float)((c.y1 - c.y0) * (c.x1 - c.x0)));
             ++n;
         }
@@ -295,84 +323,95 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
     }
     __syncthreads();
     const int nc = n_cell;
-    float dt[MC];
+    float dt[MC][J];
 #pragma unroll
-    for (int c = 0; c < MC; ++c) dt[c] = 0.f;
+    for (int c = 0; c < MC; ++c)
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) dt[c][jj] = 0.f;
     const int xm = W - w;
-    const int nr = min(GROWS, nrow - yb);
-    const float *bxp = BX + ((size_t)(b * sg.ns + s) * k + j) * H * W;
-    for (int r = 0; r < nr; ++r) {
+    const int nr = min(GR, nrow - yb);
+    const size_t plane = (size_t)H * W;
+    const float *bxp = BX + ((size_t)(b * sg.ns + s) * k + j0) * plane + (size_t)yb * W;
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+        if (r >= nr) break;                                   // uniform
         const int y = yb + r;
-        const float *brow = bxp + (size_t)y * W;
-        float *zr = zrow + r * W;
         for (int x = threadIdx.x; x <= xm; x += blockDim.x) {
-            const float q = brow[x];
-            float z = 0.f;
+            float q[J];
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) q[jj] = jj < nj ? bxp[jj * plane + (size_t)r * W + x] : 0.f;
+            float mc[MC];
 #pragma unroll
             for (int c = 0; c < MC; ++c) {
-                if (c >= nc) break;                           // uniform
+                mc[c] = 0.f;
+                if (c >= nc) continue;                        // uniform
                 const int wy = y - c_y0[c], wx = x - c_x0[c];
                 const bool ok = wy >= 0 && wy < HO && wx >= 0 && wx < WO;
-                const float d = ok ? dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
-                const float t = c_t[c];
-                const float sgn = q > t ? 1.f : (q < t ? -1.f : 0.f);
-                const float m = c_coef[c] * d * sgn;
-                z += m;
-                dt[c] -= m;
+                mc[c] = ok ? c_coef[c] * dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
             }
-            zr[x] = z;
-        }
-    }
-    __syncthreads();
-    // inclusive prefix sums of Z[0 .. xm] per row: warp 2r + hf scans half hf of row r
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int len = xm + 1, mid = ((len + 63) >> 6) << 5;    // first half: a multiple of 32 entries
-    {
-        const int r = wp >> 1, hf = wp & 1;
-        const int x_lo = hf ? mid : 0, x_hi = hf ? len : min(mid, len);
-        float carry = 0.f;
-        if (r < nr) {
-            float *zr = zrow + r * W;
-            for (int x0 = x_lo; x0 < x_hi; x0 += 32) {
-                const int x = x0 + lane;
-                float v = x < x_hi ? zr[x] : 0.f;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float u = __shfl_up_sync(0xffffffffu, v, o);
-                    if (lane >= o) v += u;
+            for (int jj = 0; jj < J; ++jj) {
+                float z = 0.f;
+#pragma unroll
+                for (int c = 0; c < MC; ++c) {
+                    if (c >= nc) break;                       // uniform
+                    const float t = c_t[c][jj];
+                    const float m = q[jj] > t ? mc[c] : (q[jj] < t ? -mc[c] : 0.f);
+                    z += m;
+                    dt[c][jj] -= m;
                 }
-                v += carry;
-                if (x < x_hi) zr[x] = v;
-                carry = __shfl_sync(0xffffffffu, v, 31);
+                zrow[(jj * GR + r) * W + x] = z;
             }
-            if (hf == 0 && lane == 0) half_tot[r] = carry;
         }
     }
     __syncthreads();
-    for (int r = 0; r < nr; ++r) {
-        const float *zr = zrow + r * W;
-        const float off = half_tot[r];
-        float *out = R2 + ((size_t)bj * H + yb + r) * W;
+    // inclusive prefix sums of Z[0 .. xm] per (plane, row): one warp per row
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int len = xm + 1;
+    for (int rr = wp; rr < nj * GR; rr += 8) {
+        if ((rr % GR) >= nr) continue;                        // uniform over the warp
+        float *zr = zrow + rr * W;
+        float carry = 0.f;
+        for (int x0 = 0; x0 < len; x0 += 32) {
+            const int x = x0 + lane;
+            float v = x < len ? zr[x] : 0.f;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
+            if (x < len) zr[x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nj * GR; ++rr) {
+        const int jj = rr / GR, r = rr % GR;
+        if (r >= nr) continue;                                // uniform
+        const float *zr = zrow + rr * W;
+        float *out = R2 + (((size_t)b * k + j0 + jj) * H + yb + r) * W;
         for (int ux = threadIdx.x; ux < W; ux += blockDim.x) {
             const int a = min(ux, xm), l = ux - w;
-            const float sa = zr[a] + (a >= mid ? off : 0.f);
-            const float sl = l >= 0 ? zr[l] + (l >= mid ? off : 0.f) : 0.f;
-            out[ux] = sa - sl;
+            out[ux] = zr[a] - (l >= 0 ? zr[l] : 0.f);
         }
     }
 #pragma unroll
     for (int c = 0; c < MC; ++c) {
         if (c >= nc) break;                                   // uniform
-        float v = dt[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[c][wp] = v;
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) {
+            float v = dt[c][jj];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[c * J + jj][wp] = v;
+        }
     }
     __syncthreads();
-    if (threadIdx.x < nc) {
-        const int c = threadIdx.x;
+    if ((int)threadIdx.x < nc * J) {
+        const int c = threadIdx.x / J, jj = threadIdx.x % J;
         float v = 0.f;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[c][q];
-        if (v != 0.f) atomicAdd(&dT[c_f[c] * k + j], v);
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[c * J + jj][q];
+        if (jj < nj && v != 0.f) atomicAdd(&dT[c_f[c] * k + j0 + jj], v);
     }
 }
 
@@ -606,7 +645,7 @@ template <int KI>
 cudaError_t launch_soft_p_ki(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
                              float *P, cudaStream_t s)
 {
-    const size_t sm = sizeof(float) * ((PT + 16 * KI) * (DCH + 1) + 16 * KI * (PT + 1));
+    const size_t sm = sizeof(float) * ((PT + 32 * KI) * (DCH + 1) + 16 * KI * (PT + 1));
     cudaError_t e = cudaFuncSetAttribute(soft_p_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     soft_p_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, P);
@@ -640,14 +679,31 @@ cudaError_t launch_soft_back(const float *X, long long n, long long npi, int D, 
     return launch_soft_back_ki<8>(X, n, npi, D, C, k, tau, P, Gp, A, dX, s);
 }
 
-template <int MC>
-cudaError_t launch_gather(dim3 grid, size_t zs, const SoftWs &w, const float *dheat, const float *wf, int H, int W,
-                          int k, int HO, int WO, const SoftGrid &sg, int is, cudaStream_t s)
+template <int MC, int J>
+cudaError_t launch_gather_j(const SoftWs &w, const float *dheat, const float *wf, int B, int H, int W, int k, int HO,
+                            int WO, const SoftGrid &sg, int is, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(soft_gather_kernel<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
+    const int h = sg.hgt[sg.size_h[is]];
+    const size_t zs = sizeof(float) * J * GR * W;             // up to 192 KB
+    cudaError_t e = cudaFuncSetAttribute(soft_gather_kernel<MC, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
     if (e != cudaSuccess) return e;
-    soft_gather_kernel<MC><<<grid, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2, w.dT);
+    const long long nblk = (long long)B * ((k + J - 1) / J) * ((H - h + GR) / GR);
+    soft_gather_kernel<MC, J><<<(unsigned)nblk, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2,
+                                                              w.dT);
     return cudaGetLastError();
+}
+
+// Planes per block: the register budget (MC x J accumulators) and shared memory (J GR W floats).
+template <int MC, int JMAX>
+cudaError_t launch_gather(const SoftWs &w, const float *dheat, const float *wf, int B, int H, int W, int k, int HO,
+                          int WO, const SoftGrid &sg, int is, cudaStream_t s)
+{
+    const long long room = 196608 / ((long long)sizeof(float) * GR * W);   // planes that fit
+    if constexpr (JMAX >= 8)
+        if (room >= 8) return launch_gather_j<MC, 8>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
+    if constexpr (JMAX >= 4)
+        if (room >= 4) return launch_gather_j<MC, 4>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
+    return launch_gather_j<MC, 2>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
 }
 
 }  // namespace
@@ -725,8 +781,12 @@ cudaError_t soft_forward(const float *Qf, int B, int H, int W, const float *Tf, 
     if (e != cudaSuccess) return e;
     const long long planes = (long long)B * k;
     for (int iw = 0; iw < sg.nw; ++iw) {
-        dim3 g((unsigned)(planes * H), (W + 128 * SEG - 1) / (128 * SEG));
-        row_box_kernel<<<g, 128, 0, s>>>(w.P, W, sg.wid[iw], w.RW + (size_t)iw * planes * H * W);
+        const int wd = sg.wid[iw];
+        const size_t rs = row_box_smem(wd);                   // up to ~56 KB (W <= 12288)
+        e = cudaFuncSetAttribute(row_box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+        if (e != cudaSuccess) return e;
+        dim3 g((unsigned)(planes * H), (W - wd + RBX) / RBX);
+        row_box_kernel<<<g, 128, rs, s>>>(w.P, W, wd, w.RW + (size_t)iw * planes * H * W);
     }
     for (int is = 0; is < sg.ns; ++is) {
         const int iw = sg.size_w[is];
@@ -760,11 +820,9 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
         const int h = sg.hgt[sg.size_h[is]];
         int ncell = 0;
         for (int f = 0; f < sg.F; ++f) ncell += sg.cell[f].s == is;
-        const dim3 gg((unsigned)(planes * ((H - h + GROWS) / GROWS)));
-        const size_t zs = sizeof(float) * GROWS * W;          // up to 192 KB (W <= 12288)
-        e = ncell <= 4 ? launch_gather<4>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s)
-            : ncell <= 9 ? launch_gather<9>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s)
-                         : launch_gather<kSoftMaxG * kSoftMaxG>(gg, zs, w, dheat, wf, H, W, k, HO, WO, sg, is, s);
+        e = ncell <= 4 ? launch_gather<4, 8>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s)
+            : ncell <= 9 ? launch_gather<9, 4>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s)
+                         : launch_gather<kSoftMaxG * kSoftMaxG, 2>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
         if (e != cudaSuccess) return e;
         dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
         adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
