@@ -10,9 +10,15 @@ occluded, noisy resample of the query), F = 10 (full window + 3 x 3 sub-windows)
 Inputs are generated on the device from fixed seeds and stay resident (8 GiB of features,
 larger than L2, so no flush is needed between steps).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp32|fp8] [--impl reference]
                   [--query-size S] [--no-compare] [--no-e2e] [--no-cpu-baseline] [--cpu-budget SEC]
                   [--no-paper-bank] [--no-soft] [--soft-batch B] [--no-batch] [--batch-eager] [--no-small]
+                  [--shard replicas|bands]
+
+With N > 1 ranks (torchrun), ``--shard replicas`` (default) gives every rank its own query
+(weak scaling); ``--shard bands`` splits the one query's window rows into N row bands, each rank
+scoring its band from its label rows plus a th - 1 row halo, the argmax combined by one MAX
+all-reduce (strong scaling; main leg only).
 
 ``--query-size`` shrinks the query to S x S (for profiler captures of the same kernels on a
 smaller case); the bench line itself is quoted on the default 2048.
@@ -240,6 +246,18 @@ def run_gpu(args, rank, world):
         cfg["H"] = cfg["W"] = args.query_size
     q, T, info, bank = make_workload(dev, cfg)
     X = q.X
+    L = cfg["H"] * cfg["W"]
+    band = None
+    if args.shard == "bands":
+        # row-band sharding of the one query: rank r scores the window rows of band r, reading
+        # its label rows plus the th - 1 row halo; the template side is recomputed from the same
+        # seed on every rank (identical codebook); the argmax is one MAX all-reduce afterwards
+        from paper_2306_15010_gb300 import bands as _bands
+        band = _bands.band_rows(cfg["H"] - cfg["th"] + 1, world)[rank]
+        if band[1] == band[0]:
+            raise SystemExit("more ranks than window rows")
+        cfg = dict(cfg, H=band[1] - band[0] + cfg["th"] - 1)
+        X = X[band[0]:band[1] + cfg["th"] - 1]
     s = torch.cuda.Stream(device=dev)
     pipe = Pipeline(vq, X, T, cfg, bank, args.prec, s)
     clk = Clocks(local).__enter__()
@@ -302,6 +320,12 @@ def run_gpu(args, rank, world):
     kern = np.array([[kv[0].elapsed_time(kv[1]), kv[2].elapsed_time(kv[3])] for kv in kevs]).mean(0)
     stats = pipe.stats.cpu().tolist()
     am = pipe.am.cpu().tolist()
+    if band is not None:
+        by, bx = am
+        hv = float(pipe.heat[by, bx].item())
+        WO = cfg["W"] - cfg["tw"] + 1
+        am = list(_bands.allreduce_argmax(hv, by + band[0], bx, WO, device=dev) if world > 1
+                  else (by + band[0], bx))
     clocks = clk.summary(t_on, t_off)
 
     # the other precisions on the same inputs, same GPU: the BF16-vs-FP32 comparison and the
@@ -363,8 +387,7 @@ def run_gpu(args, rank, world):
 
     if rank != 0:
         return None
-    L = cfg["H"] * cfg["W"]
-    value = job_value(ms, world, L)
+    value = job_value(ms, world, L) if band is None else L / (ms * 1e-3) / 1e6
     peaks, peak_src = _peaks()
     roof = roofline(cfg, args.prec, kern[0], peaks, peak_src)
     roof_score = roofline_score(cfg, kern[1], peaks)
@@ -373,16 +396,18 @@ def run_gpu(args, rank, world):
         "steps": K, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "execution": {"timed": "CUDA graph replay of one whole step per iteration",
                       "ms_per_step_call_by_call": round(ms_calls, 4)},
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "weak" if band is None else "strong", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp8": "fp8e4m3", "fp32": "f32"}[args.prec], "data": "synthetic",
         "config": {"workload": f"{cfg['H']}x{cfg['W']} query, D=512, k=128, 128x128 template, F=10 "
                                "(full + 3x3), 10 Lloyd steps; whole hot path per step",
                    "prec": args.prec, "query_px": L, "l2": "inputs larger than L2 (8 GiB features)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}" if band is None else
+                   f"row bands x{world} (rank 0: window rows {band[0]}..{band[1] - 1} + {cfg['th'] - 1}-row halo)"},
         "segments_ms": {"template_side": round(seg[0], 4), "query_assign": round(seg[1], 4),
                         "query_score": round(seg[2], 4)},
         "kernels_ms": {"query_contraction": round(float(kern[0]), 4), "score": round(float(kern[1]), 4)},
-        "query_only": {"value": round(world * L / ((seg[1] + seg[2]) * 1e-3) / 1e6, 3), "unit": "Mpix/s",
+        "query_only": {"value": round((world * L if band is None else L) / ((seg[1] + seg[2]) * 1e-3) / 1e6, 3),
+                       "unit": "Mpix/s",
                        "note": "query assign + integral image + score per query, template side amortised"},
         "assign_stats": {"n_flagged": stats[0], "n_candidates": stats[1], "n_deep": stats[2]},
         "argmax_yx": am, "planted_top_left": list(info["top_left"]),
@@ -823,7 +848,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(1, args.steps), 1),
             "ms_per_step_basis": "wall time of the sampled step that ran (not the whole workload)",
             "full_step_ms_estimate": round(1e3 * full_s, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak" if band is None else "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
                                    "(full + 3x3), 10 Lloyd steps; whole hot path per step",
@@ -858,7 +883,13 @@ def main():
                     help="skip the small latency-bound workload (256^2, D=64, k=16)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other precision on the same inputs")
+    ap.add_argument("--shard", choices=["replicas", "bands"], default="replicas",
+                    help="N > 1: one query per rank (replicas, weak scaling) or the one query's window "
+                         "rows split into N row bands (strong scaling); bands runs the main leg only")
     args = ap.parse_args()
+    if args.shard == "bands":
+        args.no_compare = args.no_e2e = args.no_cpu_baseline = args.no_paper_bank = True
+        args.no_soft = args.no_batch = args.no_small = True
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     if args.warmup < 3 and args.impl == "gpu":
