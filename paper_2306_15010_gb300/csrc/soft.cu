@@ -282,23 +282,24 @@ __global__ void soft_dw_kernel(const float *__restrict__ dheat, const float *__r
 // GR consecutive rows y' <= H - h):
 //   Z_j[x'] = sum over cells f of class s with window (y' - y0_f, x' - x0_f) valid of
 //             m_fj = -(w_f / A_f) dheat sign(Q_fj - T_fj), Q_fj(window) = BX_j[y'][x'], x' <= W - w,
-// kept in shared memory, then the row pass of the adjoint box sum
+// kept in shared memory (rows skewed by one word per 32, so that the threads' stride-SG reads
+// fall in distinct banks), then the row pass of the adjoint box sum
 //   R2_j[y'][ux] = sum over x' in [ux - w + 1, ux] within [0, W - w] of Z_j[x']
-// as a difference of two prefix sums of Z_j (a warp scan per 32 entries, one warp per row).
-// The window weights -(w_f / A_f) dheat do not depend on j: each thread loads them once per
-// pixel and applies them to its J planes.  Prefix sums are safe here although the forward
-// avoids them: these are gradient entries with a tolerance relative to the largest one, and the
-// prefix of a row of ~W terms rounds at ~W * 2^-24 of its own magnitude.  Also dT_fj += -m_fj
+// by sliding sums over segments of SG outputs per thread.  The window weights
+// -(w_f / A_f) dheat do not depend on j: each thread loads them once per pixel and applies them
+// to its J planes.  Also dT_fj += -m_fj
 // (block sums, then one atomic per block, filter and plane).  The class's cells (at most G * G)
 // are staged in shared memory first, so the per-pixel loop has uniform guards.
 constexpr int GR = 2;              // rows per block of the gradient gather
+constexpr int SG = 32;             // outputs per thread segment of its row pass
+__host__ __device__ constexpr int gather_pitch(int W) { return W + W / 32 + 1; }   // skewed row
 template <int MC, int J>           // MC >= number of cells in class s; J planes per block
 __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
                                                           const float *__restrict__ T, const float *__restrict__ wf,
                                                           int H, int W, int k, int HO, int WO, SoftGrid sg, int s,
                                                           float *__restrict__ R2, float *__restrict__ dT)
 {
-    extern __shared__ float zrow[];                           // [J][GR][W]: Z, then its prefix sums
+    extern __shared__ float zrow[];                           // [J][GR][WS]: Z (skewed rows)
     __shared__ int c_y0[MC], c_x0[MC], c_f[MC];
     __shared__ float c_t[MC][J], c_coef[MC];
     __shared__ int n_cell;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
     for (int c = 0; c < MC; ++c)
 #pragma unroll
         for (int jj = 0; jj < J; ++jj) dt[c][jj] = 0.f;
-    const int xm = W - w;
+    const int xm = W - w, WS = gather_pitch(W);
     const int nr = min(GR, nrow - yb);
     const size_t plane = (size_t)H * W;
     const float *bxp = BX + ((size_t)(b * sg.ns + s) * k + j0) * plane + (size_t)yb * W;
@@ -360,40 +361,44 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
                     z += m;
                     dt[c][jj] -= m;
                 }
-                zrow[(jj * GR + r) * W + x] = z;
+                zrow[(jj * GR + r) * WS + skew32(x)] = z;
             }
         }
     }
     __syncthreads();
-    // inclusive prefix sums of Z[0 .. xm] per (plane, row): one warp per row
+    // row pass: thread segments of SG consecutive outputs, the first summed directly and the
+    // next ones by sliding it; the outputs leave from registers as 16-byte stores
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int len = xm + 1;
-    for (int rr = wp; rr < nj * GR; rr += 8) {
-        if ((rr % GR) >= nr) continue;                        // uniform over the warp
-        float *zr = zrow + rr * W;
-        float carry = 0.f;
-        for (int x0 = 0; x0 < len; x0 += 32) {
-            const int x = x0 + lane;
-            float v = x < len ? zr[x] : 0.f;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const float u = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += u;
-            }
-            v += carry;
-            if (x < len) zr[x] = v;
-            carry = __shfl_sync(0xffffffffu, v, 31);
-        }
-    }
-    __syncthreads();
-    for (int rr = 0; rr < nj * GR; ++rr) {
+    const int nseg = (W + SG - 1) / SG;
+    const bool vec = (W & 3) == 0;
+    for (int e = threadIdx.x; e < nj * GR * nseg; e += blockDim.x) {
+        const int rr = e / nseg, u0 = (e - rr * nseg) * SG;
         const int jj = rr / GR, r = rr % GR;
-        if (r >= nr) continue;                                // uniform
-        const float *zr = zrow + rr * W;
-        float *out = R2 + (((size_t)b * k + j0 + jj) * H + yb + r) * W;
-        for (int ux = threadIdx.x; ux < W; ux += blockDim.x) {
-            const int a = min(ux, xm), l = ux - w;
-            out[ux] = zr[a] - (l >= 0 ? zr[l] : 0.f);
+        if (r >= nr) continue;
+        const float *zr = zrow + rr * WS;
+        const int n = min(SG, W - u0);
+        float o[SG];
+        float acc = 0.f;
+        for (int x = max(0, u0 - w + 1); x <= min(u0, xm); ++x) acc += zr[skew32(x)];
+        o[0] = acc;
+#pragma unroll
+        for (int i = 1; i < SG; ++i) {
+            const int ux = u0 + i;
+            if (i < n) {
+                if (ux <= xm) acc += zr[skew32(ux)];
+                if (ux - w >= 0) acc -= zr[skew32(ux - w)];
+            }
+            o[i] = acc;
+        }
+        float *out = R2 + (((size_t)b * k + j0 + jj) * H + yb + r) * W + u0;
+        if (vec && n == SG) {
+#pragma unroll
+            for (int i = 0; i < SG; i += 4)
+                *reinterpret_cast<float4 *>(out + i) = make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < SG; ++i)
+                if (i < n) out[i] = o[i];
         }
     }
 #pragma unroll
@@ -684,7 +689,7 @@ cudaError_t launch_gather_j(const SoftWs &w, const float *dheat, const float *wf
                             int WO, const SoftGrid &sg, int is, cudaStream_t s)
 {
     const int h = sg.hgt[sg.size_h[is]];
-    const size_t zs = sizeof(float) * J * GR * W;             // up to 192 KB
+    const size_t zs = sizeof(float) * J * GR * gather_pitch(W);   // up to ~198 KB
     cudaError_t e = cudaFuncSetAttribute(soft_gather_kernel<MC, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
     if (e != cudaSuccess) return e;
     const long long nblk = (long long)B * ((k + J - 1) / J) * ((H - h + GR) / GR);
@@ -698,7 +703,7 @@ template <int MC, int JMAX>
 cudaError_t launch_gather(const SoftWs &w, const float *dheat, const float *wf, int B, int H, int W, int k, int HO,
                           int WO, const SoftGrid &sg, int is, cudaStream_t s)
 {
-    const long long room = 196608 / ((long long)sizeof(float) * GR * W);   // planes that fit
+    const long long room = 200704 / ((long long)sizeof(float) * GR * gather_pitch(W));   // planes that fit
     if constexpr (JMAX >= 8)
         if (room >= 8) return launch_gather_j<MC, 8>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
     if constexpr (JMAX >= 4)
