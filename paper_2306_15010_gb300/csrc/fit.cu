@@ -114,7 +114,34 @@ __global__ void __launch_bounds__(1024) stable_sort_kernel(const uint8_t *__rest
 // positions apart.  A (cluster, dimension) pair that fails this, holds a value outside the
 // range, or whose sums could exceed 128 bits is summed in FP64 in pixel order by its lane.
 // Both branches therefore equal the in-order FP64 sum bit for bit.
+//
+// The common case takes a narrower route first: values with 2^-17 <= |x| < 2^5 (and zero) are
+// integers below 2^45 in units of 2^-40, so with fewer than 2^18 members their signed sum and
+// the sum of |x| are exact in 64 bits, at a quarter of the 128-bit route's instructions.  A
+// block with any value outside that range (or a larger cluster) repeats the members in 128 bits.
 constexpr int UW = 16;       // warps per (cluster, 32 dimensions)
+
+struct Fixed64 {
+    long long sum;                     // signed sum, units 2^-40
+    unsigned long long mag;            // sum of |x|
+    int low;                           // lowest set bit position over the values
+    bool bad;                          // a value outside [2^-17, 2^5)
+};
+
+__device__ __forceinline__ void fixed64_add(Fixed64 &f, float x)
+{
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t E = (b >> 23) & 0xFFu;
+    const uint32_t frac = b & 0x7FFFFFu;
+    if (E == 0u && frac == 0u) return;                     // +-0 adds nothing
+    if (E < 110u || E > 131u) { f.bad = true; return; }     // |x| < 2^-17 or >= 2^5 (inf, nan)
+    const uint32_t M = frac | 0x800000u;
+    const int sh = (int)E - 110;                          // x = M * 2^(sh - 40), M 2^sh < 2^45
+    const unsigned long long X = (unsigned long long)M << sh;
+    f.sum += (b >> 31) ? -(long long)X : (long long)X;
+    f.mag += X;
+    f.low = min(f.low, sh + __ffs((int)M) - 1);
+}
 
 struct Fixed {
     unsigned __int128 pos, neg, mag;   // sums of the positive and negative parts, of |x|
@@ -168,26 +195,49 @@ __global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restr
     if (c == 0) return;                                  // uniform over the block
     const int *m = members + off[j];
     const int ic = i < D ? i : D - 1;                    // clamped column (every address in bounds)
-    Fixed f;
-    f.pos = f.neg = f.mag = 0;
-    f.low = 1 << 30;
-    f.hish = 0;
-    f.bad = false;
+    Fixed64 f6;
+    f6.sum = 0;
+    f6.mag = 0;
+    f6.low = 1 << 30;
+    f6.bad = false;
     int q = w;
     for (; q + 7 * UW < c; q += 8 * UW) {                // eight member rows in flight per warp
         float x[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) x[u] = __ldg(T + (size_t)m[q + u * UW] * D + ic);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) fixed_add(f, x[u]);
+        for (int u = 0; u < 8; ++u) fixed64_add(f6, x[u]);
     }
-    for (; q < c; q += UW) fixed_add(f, __ldg(T + (size_t)m[q] * D + ic));
-    spos[w][lane] = f.pos;
-    sneg[w][lane] = f.neg;
-    smag[w][lane] = f.mag;
-    slow[w][lane] = f.low;
-    shish[w][lane] = f.hish;
-    sbad[w][lane] = f.bad ? 1 : 0;
+    for (; q < c; q += UW) fixed64_add(f6, __ldg(T + (size_t)m[q] * D + ic));
+    // uniform over the block: the 128-bit route when a value is outside the 64-bit range
+    const bool wide = __syncthreads_or(f6.bad || c >= (1 << 18));
+    long long (*s64)[32] = reinterpret_cast<long long (*)[32]>(&sacc[0][0][0]);
+    unsigned long long (*m64)[32] = reinterpret_cast<unsigned long long (*)[32]>(&sacc[1][0][0]);
+    if (!wide) {
+        s64[w][lane] = f6.sum;
+        m64[w][lane] = f6.mag;
+        slow[w][lane] = f6.low;
+    } else {
+        Fixed f;
+        f.pos = f.neg = f.mag = 0;
+        f.low = 1 << 30;
+        f.hish = 0;
+        f.bad = false;
+        for (q = w; q + 7 * UW < c; q += 8 * UW) {
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(T + (size_t)m[q + u * UW] * D + ic);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) fixed_add(f, x[u]);
+        }
+        for (; q < c; q += UW) fixed_add(f, __ldg(T + (size_t)m[q] * D + ic));
+        spos[w][lane] = f.pos;
+        sneg[w][lane] = f.neg;
+        smag[w][lane] = f.mag;
+        slow[w][lane] = f.low;
+        shish[w][lane] = f.hish;
+        sbad[w][lane] = f.bad ? 1 : 0;
+    }
     __syncthreads();
     // small clusters: warp 0 alone finishes (the other warps leave now, so the next block can
     // start); large clusters keep every warp for a staged in-order FP64 route
@@ -195,7 +245,27 @@ __global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restr
     if (!coop && w != 0) return;
     double s = 0.0;
     bool need = false;                                  // this lane's column takes the FP64 route
-    if (w == 0) {
+    if (w == 0 && !wide) {
+        long long sum = 0;
+        unsigned long long mag = 0;
+        int low = 1 << 30;
+#pragma unroll 4
+        for (int u = 0; u < UW; ++u) {
+            sum += s64[u][lane];
+            mag += m64[u][lane];
+            low = min(low, slow[u][lane]);
+        }
+        if (mag == 0) {
+            s = 0.0;                                     // only zeros: the FP64 sum is +0
+        } else if (63 - __clzll((long long)mag) - low <= 52) {
+            // exact: |sum| >> low has at most 53 significant bits
+            const unsigned long long a = sum < 0 ? (unsigned long long)(-sum) : (unsigned long long)sum;
+            const double v = (double)(a >> low);
+            s = ldexp(sum < 0 ? -v : v, low - 40);
+        } else {
+            need = true;                                 // a rounding could occur in order
+        }
+    } else if (w == 0) {
         unsigned __int128 pos = 0, neg = 0, mag = 0;
         int low = 1 << 30, hish = 0;
         bool bad = false;
@@ -224,6 +294,8 @@ __global__ void __launch_bounds__(32 * UW, 3) update_kernel(const float *__restr
         } else {
             need = true;                                 // a rounding could occur in order
         }
+    }
+    if (w == 0) {
         const unsigned nm = __ballot_sync(0xffffffffu, need && i < D);
         if (lane == 0) s_need = nm;
         if (!coop && need) {                             // the in-order FP64 sum, lane by lane
