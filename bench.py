@@ -47,11 +47,11 @@ OP_ASSIGN, OP_SCORE = 1, 3
 
 # DRAM traffic of one launch of the BF16 contraction kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), from the ncu capture summarised in
-# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,862,784 + 5,067,520 bytes),
+# profiles/assign_tc_kernel_query1024.md (1024 x 1024 query: 2,147,861,248 + 4,904,960 bytes),
 # scaled by the pixel count (traffic is proportional to it).  Valid only for the kernel source
 # it was taken on: the SHA-256 of assign_tc.cu below; any other source reports null.
-TC_TRAFFIC_PER_PX = (2147862784 + 5067520) / (1024 * 1024)
-TC_TRAFFIC_SRC_SHA256 = "b4ab6b74f3123c4ec705890da47c9d6f21dfa07067a9867f0d6cef30517b5ac2"
+TC_TRAFFIC_PER_PX = (2147861248 + 4904960) / (1024 * 1024)
+TC_TRAFFIC_SRC_SHA256 = "191d4f541bad2ed706a4d3b51baf91a22bee137e456ad990249fa00d01510926"
 
 
 

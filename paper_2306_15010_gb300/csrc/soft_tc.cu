@@ -14,11 +14,14 @@
 //   1. form a for the tile (thread: one pixel, half of the centroids) and store it twice in
 //      shared memory, as A [pixel][centroid] and A^T [centroid][pixel] (K-major, 128-byte
 //      swizzle, hi and lo planes), and reduce it over the tile's pixels per centroid (S_j);
-//   2. per 128-wide feature chunk m: load the chunk of X (thread: one feature, 64 pixels, kept
-//      in registers), store X^T [feature][pixel] hi/lo; one thread issues
+//   2. per 128-wide feature chunk m: store the chunk of X (thread: one feature, 64 pixels,
+//      loaded into registers during the previous chunk) as X^T [feature][pixel] hi/lo; one
+//      thread issues
 //        GEMM 1  acc1[d][u]   = C^T_m (128 features x kp)  . A^T      (kp = k rounded up to 16)
 //        GEMM 2  acc2_m[d][j] += X^T_m (128 features x 128 px) . (A^T)^T
-//      and the threads read acc1 back for dX = 2 (s_u x_u - acc1) (tensor-memory lane = feature).
+//      and while they run the threads load the next chunk's features; then they read acc1 back
+//      for dX = 2 (s_u x_u - acc1) (tensor-memory lane = feature), x_u = hi + lo from the
+//      planes (within 2^-17 relative of x_u).
 // C^T (hi and lo, every chunk) is loaded once per CTA from an image built by ct_image_kernel.
 // acc2 stays in tensor memory across the CTA's tiles and is written out once at the end.
 #include <cuda_bf16.h>
@@ -120,6 +123,18 @@ __global__ void __launch_bounds__(UNT, 1) soft_grad_tc_kernel(const __grid_const
     const int q4 = warp & 3, pxh = warp >> 2;                   // step 2: lane quadrant, pixel half
     const int dl = 32 * q4 + lane;                              // feature row within a chunk
     const uint32_t id1 = ptx::bf16_idesc(128, UP), id2 = ptx::bf16_idesc(128, KP);
+    // this thread's 64 pixels of feature column 128 m + dl of the tile at pixel p0n
+    float xv[64];
+    auto load_x = [&](long long p0n, int mn) {
+        const int dc = 128 * mn + dl;
+        const bool dvn = dc < g.D;
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+            const long long u = p0n + 64 * pxh + q;
+            xv[q] = (dvn && u < g.n) ? g.X[u * g.D + dc] : 0.f;
+        }
+    };
+    if (ok && (int)blockIdx.x < g.ntiles) load_x((long long)blockIdx.x * UP, 0);
     uint32_t phase = 0;
     float sacc = 0.f;                                           // S_j, j = hf KH + lane (lane < KH)
     bool first = true;
@@ -206,16 +221,10 @@ __global__ void __launch_bounds__(UNT, 1) soft_grad_tc_kernel(const __grid_const
             }
             sacc += v[0];
         }
-        // ---- 2. feature chunks
+        // ---- 2. feature chunks (this chunk's features were loaded during the previous one)
         for (int m = 0; m < nd; ++m) {
             const int dcol = 128 * m + dl;
             const bool dv = dcol < g.D;
-            float xv[64];
-#pragma unroll
-            for (int q = 0; q < 64; ++q) {
-                const long long u = p0 + 64 * pxh + q;
-                xv[q] = (dv && u < g.n) ? g.X[u * g.D + dcol] : 0.f;
-            }
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 uint4 h4, l4;
@@ -265,6 +274,10 @@ __global__ void __launch_bounds__(UNT, 1) soft_grad_tc_kernel(const __grid_const
                 }
                 ptx::tc_commit(&bar[1]);
             }
+            // the next chunk's features (of this tile, else of the CTA's next tile) are loaded
+            // while the MMAs run; the epilogue below takes x from the hi and lo planes
+            if (m + 1 < nd) load_x(p0, m + 1);
+            else if (tile + (int)gridDim.x < g.ntiles) load_x(p0 + (long long)gridDim.x * UP, 0);
             const bool w_ok = wait_bounded(&bar[1], phase);
             phase ^= 1;
             if (__syncthreads_or(!w_ok)) {
@@ -278,11 +291,21 @@ __global__ void __launch_bounds__(UNT, 1) soft_grad_tc_kernel(const __grid_const
                     float acc[32];
                     ptx::tc_ld32(tmem + ((uint32_t)(32 * q4) << 16) + 64 * pxh + 32 * hh, acc);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int px = 64 * pxh + 32 * hh + q;
-                        const long long u = p0 + px;
-                        if (dv && u < g.n)
-                            g.dX[u * g.D + dcol] = 2.0f * ((sas[px] + sas[UP + px]) * xv[32 * hh + q] - acc[q]);
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t o = (uint32_t)pxh * ATOM + sw_off(dl, 32 * hh + 8 * c);
+                        const uint4 h4 = *reinterpret_cast<const uint4 *>(sXT + o);
+                        const uint4 l4 = *reinterpret_cast<const uint4 *>(sXT + 2 * ATOM + o);
+                        const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w}, lw[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t hb = e & 1 ? hw[e >> 1] & 0xFFFF0000u : hw[e >> 1] << 16;
+                            const uint32_t lb = e & 1 ? lw[e >> 1] & 0xFFFF0000u : lw[e >> 1] << 16;
+                            const float x = __uint_as_float(hb) + __uint_as_float(lb);   // hi + lo
+                            const int px = 64 * pxh + 32 * hh + 8 * c + e;
+                            const long long u = p0 + px;
+                            if (dv && u < g.n)
+                                g.dX[u * g.D + dcol] = 2.0f * ((sas[px] + sas[UP + px]) * x - acc[8 * c + e]);
+                        }
                     }
                 }
             }
