@@ -63,19 +63,38 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
     for (int r = 0; r < PPT / 2; ++r)
 #pragma unroll
         for (int i = 0; i < KI; ++i) acc[r][i] = make_float2(0.f, 0.f);
-    for (int d0 = 0; d0 < D; d0 += DCH) {
-        __syncthreads();
-        for (int e = t; e < PT * DCH; e += blockDim.x) {
-            const int pp = e / DCH, dd = e % DCH;
+    // the next chunk's features and centroids are loaded into registers while the current one
+    // is consumed (256 threads: XE and CE elements each)
+    constexpr int XE = PT * DCH / 256, CE = 16 * KI * DCH / 256;
+    float xr[XE], cr[CE];
+    auto fetch = [&](int d0) {
+#pragma unroll
+        for (int q = 0; q < XE; ++q) {
+            const int e = t + 256 * q, pp = e / DCH, dd = e % DCH;
             const long long g = p0 + pp;
-            xs[pp][dd] = (g < n && d0 + dd < D) ? X[g * D + d0 + dd] : 0.f;
+            xr[q] = (g < n && d0 + dd < D) ? X[g * D + d0 + dd] : 0.f;
         }
-        for (int e = t; e < k * DCH; e += blockDim.x) {
-            const int j = e / DCH, dd = e % DCH;
-            const float c = d0 + dd < D ? -C[(size_t)j * D + d0 + dd] : 0.f;
-            cs[j][dd] = make_float2(c, c);
+#pragma unroll
+        for (int q = 0; q < CE; ++q) {
+            const int e = t + 256 * q, j = e / DCH, dd = e % DCH;
+            cr[q] = (j < k && d0 + dd < D) ? -C[(size_t)j * D + d0 + dd] : 0.f;
+        }
+    };
+    fetch(0);
+    for (int d0 = 0; d0 < D; d0 += DCH) {
+        __syncthreads();                                       // the previous chunk is consumed
+#pragma unroll
+        for (int q = 0; q < XE; ++q) {
+            const int e = t + 256 * q;
+            xs[e / DCH][e % DCH] = xr[q];
+        }
+#pragma unroll
+        for (int q = 0; q < CE; ++q) {
+            const int e = t + 256 * q;
+            cs[e / DCH][e % DCH] = make_float2(cr[q], cr[q]);
         }
         __syncthreads();
+        if (d0 + DCH < D) fetch(d0 + DCH);
 #pragma unroll 2
         for (int dd = 0; dd < DCH; ++dd) {
             float2 xv[PPT / 2], cv[KI];
@@ -123,7 +142,7 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
 // p planar: P[(item * k + j) * npi + pixel], written through a shared-memory transpose so that
 // consecutive threads store consecutive pixels of one plane.
 template <int KI>
-__global__ void __launch_bounds__(256) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
+__global__ void __launch_bounds__(256, KI == 8 ? 2 : 3) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
                                                      int D, const float *__restrict__ C, int k, float tau,
                                                      float *__restrict__ P)
 {
