@@ -489,10 +489,17 @@ def roofline_score(cfg, kernel_ms, peaks):
     ops = float(V) * k * ops_per
     ach = ops / (kernel_ms * 1e-3) / 1e12
     peak = 152 * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    # the same launch against HBM: the 16-bit integral image read once, the heatmap written
+    tbytes = (cfg["H"] + 1) * (cfg["W"] + 1) * k * 2 + V * 4
+    hbm = tbytes / (kernel_ms * 1e-3) / 1e9
     return {"bound": "alu", "achieved": round(ach, 2), "peak": round(peak, 2), "unit": "Tops/s",
             "frac": round(ach / peak, 4), "traffic": None, "kernel": "score_grid_kernel",
             "kernel_ms": round(float(kernel_ms), 4), "algorithmic_ops_per_window_cluster": ops_per,
-            "peak_source": "derived: 152 SMs x 128 INT32/FP32 lanes x max SM clock"}
+            "peak_source": "derived issue-rate bound: 152 SMs x 128 lanes x max SM clock, one operation "
+                           "(integer add or compare, or a shared-memory corner load) per lane and cycle",
+            "hbm": {"achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(hbm / peaks["hbm_gbs"], 4), "bytes_per_launch": tbytes,
+                    "note": "16-bit integral image read once + heatmap written"}}
 
 
 def run_paper_bank(vq, pipe, cfg, s, dev, reps=5):
