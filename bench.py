@@ -714,15 +714,17 @@ def run_e2e(vq, pipe, X, T, cfg, args, s, dev, am_ref=None):
 
     one_step()                                # warm-up
     torch.cuda.synchronize()
-    # the floor: the step's host-to-device bytes alone, one copy
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(s):
-        c0.record(s)
-        pipe.X.copy_(hX, non_blocking=True)
-        pipe.T.copy_(hT, non_blocking=True)
-        c1.record(s)
-    torch.cuda.synchronize()
-    copy_ms = c0.elapsed_time(c1)
+    # the floor: the step's host-to-device bytes alone (the fastest of three copies)
+    copy_ms = float("inf")
+    for _ in range(3):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            c0.record(s)
+            pipe.X.copy_(hX, non_blocking=True)
+            pipe.T.copy_(hT, non_blocking=True)
+            c1.record(s)
+        torch.cuda.synchronize()
+        copy_ms = min(copy_ms, c0.elapsed_time(c1))
     n = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(n):
