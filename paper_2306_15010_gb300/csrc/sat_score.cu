@@ -337,7 +337,7 @@ __device__ __forceinline__ void issue_chunk(T *dst, const T *__restrict__ S, int
 }
 
 template <typename T, int G, bool FULL, int NCOLP>
-__global__ void __launch_bounds__(STH, 6) score_grid_kernel(const T *__restrict__ S, int P, int k,
+__global__ void __launch_bounds__(STH, G <= 3 ? 8 : 6) score_grid_kernel(const T *__restrict__ S, int P, int k,
                                                          int HO, int WO, GridSpec gs,
                                                          const int32_t *__restrict__ tcounts,
                                                          float *__restrict__ heat,
