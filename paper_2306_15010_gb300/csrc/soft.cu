@@ -313,7 +313,7 @@ constexpr int GR = 2;              // rows per block of the gradient gather
 constexpr int SG = 32;             // outputs per thread segment of its row pass
 __host__ __device__ constexpr int gather_pitch(int W) { return W + W / 32 + 1; }   // skewed row
 template <int MC, int J>           // MC >= number of cells in class s; J planes per block
-__global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
+__global__ void __launch_bounds__(256, MC <= 4 ? 2 : 1) soft_gather_kernel(const float *__restrict__ BX, const float *__restrict__ dheat,
                                                           const float *__restrict__ T, const float *__restrict__ wf,
                                                           int H, int W, int k, int HO, int WO, SoftGrid sg, int s,
                                                           float *__restrict__ R2, float *__restrict__ dT)
@@ -352,23 +352,40 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
     const int nr = min(GR, nrow - yb);
     const size_t plane = (size_t)H * W;
     const float *bxp = BX + ((size_t)(b * sg.ns + s) * k + j0) * plane + (size_t)yb * W;
+    // per row: the planes' row pointers, and per cell a dheat row pointer with the valid x
+    // range [xlo, xhi) of its windows; loads outside that range are clamped into the row (and
+    // their value dropped), so every address formed stays inside the buffers
 #pragma unroll
     for (int r = 0; r < GR; ++r) {
         if (r >= nr) break;                                   // uniform
         const int y = yb + r;
+        const float *bq[J];
+#pragma unroll
+        for (int jj = 0; jj < J; ++jj) bq[jj] = bxp + (size_t)(jj < nj ? jj : 0) * plane + (size_t)r * W;
+        const float *dp[MC];
+        int xlo[MC], xhi[MC];
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+            const int wy = c < nc ? y - c_y0[c] : -1;
+            const bool rowok = wy >= 0 && wy < HO;
+            const int x0c = c < nc ? c_x0[c] : 0;
+            dp[c] = dheat + ((size_t)b * HO + (rowok ? wy : 0)) * WO;
+            xlo[c] = rowok ? x0c : 1 << 30;
+            xhi[c] = rowok ? x0c + WO : 0;
+        }
+        float *zr = zrow + r * WS;
         for (int x = threadIdx.x; x <= xm; x += blockDim.x) {
             float q[J];
 #pragma unroll
-            for (int jj = 0; jj < J; ++jj) q[jj] = jj < nj ? bxp[jj * plane + (size_t)r * W + x] : 0.f;
+            for (int jj = 0; jj < J; ++jj) q[jj] = jj < nj ? bq[jj][x] : 0.f;
             float mc[MC];
 #pragma unroll
             for (int c = 0; c < MC; ++c) {
-                mc[c] = 0.f;
-                if (c >= nc) continue;                        // uniform
-                const int wy = y - c_y0[c], wx = x - c_x0[c];
-                const bool ok = wy >= 0 && wy < HO && wx >= 0 && wx < WO;
-                mc[c] = ok ? c_coef[c] * dheat[((size_t)b * HO + wy) * WO + wx] : 0.f;
+                const bool ok = x >= xlo[c] && x < xhi[c];
+                const float d = dp[c][ok ? x - xlo[c] : 0];
+                mc[c] = ok ? c_coef[c] * d : 0.f;
             }
+            const int sx = skew32(x);
 #pragma unroll
             for (int jj = 0; jj < J; ++jj) {
                 float z = 0.f;
@@ -380,13 +397,14 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
                     z += m;
                     dt[c][jj] -= m;
                 }
-                zrow[(jj * GR + r) * WS + skew32(x)] = z;
+                zr[jj * GR * WS + sx] = z;
             }
         }
     }
     __syncthreads();
     // row pass: thread segments of SG consecutive outputs, the first summed directly and the
-    // next ones by sliding it; the outputs leave from registers as 16-byte stores
+    // next ones by sliding it; the outputs leave from registers as 16-byte stores.  Segments
+    // whose adds and subtractions all fall inside [0, W - w] take an unguarded loop.
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int nseg = (W + SG - 1) / SG;
     const bool vec = (W & 3) == 0;
@@ -400,14 +418,23 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
         float acc = 0.f;
         for (int x = max(0, u0 - w + 1); x <= min(u0, xm); ++x) acc += zr[skew32(x)];
         o[0] = acc;
+        if (n == SG && u0 + SG - 1 <= xm && u0 + 1 - w >= 0) {
 #pragma unroll
-        for (int i = 1; i < SG; ++i) {
-            const int ux = u0 + i;
-            if (i < n) {
-                if (ux <= xm) acc += zr[skew32(ux)];
-                if (ux - w >= 0) acc -= zr[skew32(ux - w)];
+            for (int i = 1; i < SG; ++i) {
+                acc += zr[skew32(u0 + i)];
+                acc -= zr[skew32(u0 + i - w)];
+                o[i] = acc;
             }
-            o[i] = acc;
+        } else {
+#pragma unroll
+            for (int i = 1; i < SG; ++i) {
+                const int ux = u0 + i;
+                if (i < n) {
+                    if (ux <= xm) acc += zr[skew32(ux)];
+                    if (ux - w >= 0) acc -= zr[skew32(ux - w)];
+                }
+                o[i] = acc;
+            }
         }
         float *out = R2 + (((size_t)b * k + j0 + jj) * H + yb + r) * W + u0;
         if (vec && n == SG) {
@@ -420,14 +447,33 @@ __global__ void __launch_bounds__(256) soft_gather_kernel(const float *__restric
                 if (i < n) out[i] = o[i];
         }
     }
+    if constexpr (MC * J <= 32) {
+        // the warp's sums of all MC J values at once: a reduce-scatter over the lanes (31
+        // exchanges), after which lane l holds the warp's sum of value l = c J + jj
+        float v[32];
 #pragma unroll
-    for (int c = 0; c < MC; ++c) {
-        if (c >= nc) break;                                   // uniform
+        for (int i = 0; i < 32; ++i) v[i] = i < MC * J ? dt[i / J][i % J] : 0.f;
 #pragma unroll
-        for (int jj = 0; jj < J; ++jj) {
-            float v = dt[c][jj];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[c * J + jj][wp] = v;
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+            const bool up = lane & sh;
+#pragma unroll
+            for (int i = 0; i < sh; ++i) {
+                const float send = up ? v[i] : v[i + sh];
+                const float keep = up ? v[i + sh] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, sh);
+            }
+        }
+        if (lane < MC * J) red[lane][wp] = v[0];
+    } else {
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+            if (c >= nc) break;                               // uniform
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+                float v = dt[c][jj];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) red[c * J + jj][wp] = v;
+            }
         }
     }
     __syncthreads();
