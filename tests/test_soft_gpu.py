@@ -78,7 +78,7 @@ def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
     (1, 150, 140, 48, 40, 40, 44, 3, 0.1),   # 165 pixel tiles: more tiles than CTAs
     (1, 30, 32, 384, 64, 18, 20, 1, 0.3),    # three 64-centroid chunks exceed shared memory: SIMT path
     (1, 30, 32, 40, 100, 20, 22, 1, 0.2),    # k > 64: SIMT path
-    (1, 18, 3300, 8, 6, 10, 2900, 2, 0.3),   # wide rows: large staged row blocks, 4 planes per gather block
+    (1, 18, 3300, 8, 6, 10, 60, 2, 0.3),     # wide rows: four row blocks per row, 4 planes per gather block
 ])
 def test_soft_contraction_paths(vq, B, H, W, D, k, th, tw, G, tau):
     # features scaled so that the logit gaps (d_other - d_own) / tau are ~3-5: soft assignments
