@@ -10,6 +10,7 @@
 // so a query's features are read from HBM once per group instead of once per template.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -21,6 +22,39 @@ using namespace vqnnf;
 namespace {
 
 constexpr int kGroupRows = kMaxK;            // rows of one group codebook, at most
+constexpr int kLanes = 4;                    // pairs of one query in flight at once (streams)
+
+// The library's own streams and events for the pair lanes, created once per device on first
+// use (outside any stream capture in the intended use: the first call is a warm-up) and kept
+// for the process.  Lane 0 is the caller's stream.  If they cannot be created the pairs run
+// one after another on the caller's stream.
+struct LanePool {
+    bool ok = false;
+    cudaStream_t st[kLanes];
+    cudaEvent_t fork, join[kLanes];
+};
+
+bool lane_pool(LanePool *&out)
+{
+    static std::mutex mu;
+    static LanePool pools[64];
+    static bool tried[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    LanePool &p = pools[dev];
+    if (!tried[dev]) {
+        tried[dev] = true;
+        bool ok = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int l = 1; l < kLanes && ok; ++l)
+            ok = cudaStreamCreateWithFlags(&p.st[l], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&p.join[l], cudaEventDisableTiming) == cudaSuccess;
+        p.ok = ok;
+        if (!ok) cudaGetLastError();                 // clear the failed creation's error
+    }
+    out = &p;
+    return p.ok;
+}
 
 struct GroupSrc {
     int nseg;
@@ -60,9 +94,9 @@ struct BatchWs {
     FlagList fl[kMaxSegStat];
     float *sC;                                // stationary codebooks, every launch's groups in a row
     CodebookPrep sprep;                       // their prepared planes (one common centring mean)
-    FitWs fit;
-    char *score_base;                         // integral-image workspace of one pair
-    float *heat_scratch;                      // heatmap of one pair when the caller wants maxima only
+    FitWs fit[kLanes];                        // per lane: the k-means and template-NNF workspace
+    char *score_base[kLanes];                 // integral-image workspace of one pair per lane
+    float *heat_scratch[kLanes];              // heatmap of one pair when the caller wants maxima only
 };
 
 int bank_size(int G) { return 1 + G * G; }
@@ -124,7 +158,7 @@ BatchWs carve_batch(WsCursor &c, const vqnnf_image *q, int nq, const vqnnf_batch
     w.sprep.a = c.take<float>(srows);
     w.sprep.v = c.take<float>(srows);
     w.sprep.b = c.take<float>(srows);
-    w.fit = carve_fit(c, l_max, D, k_max);
+    for (int l = 0; l < kLanes; ++l) w.fit[l] = carve_fit(c, l_max, D, k_max);
     // the largest integral-image layout over the templates (its size depends on the template)
     size_t sbytes = 0;
     for (int j = 0; j < nt; ++j) {
@@ -132,8 +166,10 @@ BatchWs carve_batch(WsCursor &c, const vqnnf_image *q, int nq, const vqnnf_batch
         carve_score(z, H_max, W_max, k_max, t[j].h, t[j].w);
         sbytes = std::max(sbytes, z.off);
     }
-    w.score_base = c.take<char>(sbytes);
-    w.heat_scratch = c.take<float>((size_t)hw_max);
+    for (int l = 0; l < kLanes; ++l) {
+        w.score_base[l] = c.take<char>(sbytes);
+        w.heat_scratch[l] = c.take<float>((size_t)hw_max);
+    }
     return w;
 }
 
@@ -369,16 +405,34 @@ vqnnf_status compile_banks(const vqnnf_batch_template *t, int nt, int G, Banks &
 }
 
 // Template side: codebook, NNF and filter responses of every template.
+// Template sides in up to kLanes lanes at once (template j in lane j % nl, each lane with its
+// own fit workspace): one template's Lloyd steps are a chain of small dependent launches that
+// leave most of the GPU idle.  The lanes fork from s and join it again before returning.
 vqnnf_status fit_templates(const vqnnf_batch_template *t, int nt, int D, int iters, uint64_t seed, const Banks &b,
                            BatchWs &w, cudaStream_t s)
 {
+    LanePool *lp = nullptr;
+    const int nl = lane_pool(lp) ? std::min(kLanes, nt) : 1;
+    cudaError_t e = cudaSuccess;
+    if (nl > 1) {
+        e = cudaEventRecord(lp->fork, s);
+        for (int l = 1; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lp->st[l], lp->fork, 0);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     for (int j = 0; j < nt; ++j) {
-        const long long l = (long long)t[j].h * t[j].w;
-        vqnnf_status st = run_fit(t[j].T, l, D, t[j].k, iters, seed + (uint64_t)j, VQNNF_PREC_BF16, w.C[j], w.fit, s);
+        const int l = j % nl;
+        const cudaStream_t ls = l ? lp->st[l] : s;
+        const long long n = (long long)t[j].h * t[j].w;
+        vqnnf_status st = run_fit(t[j].T, n, D, t[j].k, iters, seed + (uint64_t)j, VQNNF_PREC_BF16, w.C[j], w.fit[l], ls);
         if (st != VQNNF_OK) return st;
-        st = run_assign(t[j].T, l, D, w.C[j], t[j].k, VQNNF_PREC_BF16, w.tlab[j], nullptr, w.fit.as, s);
+        st = run_assign(t[j].T, n, D, w.C[j], t[j].k, VQNNF_PREC_BF16, w.tlab[j], nullptr, w.fit[l].as, ls);
         if (st != VQNNF_OK) return st;
-        cudaError_t e = launch_filter_responses(w.tlab[j], t[j].h, t[j].w, t[j].k, b.bs[j], w.tcnt[j], s);
+        e = launch_filter_responses(w.tlab[j], t[j].h, t[j].w, t[j].k, b.bs[j], w.tcnt[j], ls);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    for (int l = 1; l < nl; ++l) {
+        e = cudaEventRecord(lp->join[l], lp->st[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lp->join[l], 0);
         if (e != cudaSuccess) return from_cuda(e);
     }
     return VQNNF_OK;
@@ -491,18 +545,37 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
     }
     WGridSpec no_wgrid;
     memset(&no_wgrid, 0, sizeof(no_wgrid));
+    // per query, its pairs' integral images and scores run in kLanes lanes at once (pair j in
+    // lane j % kLanes, each lane with its own integral-image workspace): small pairs leave most
+    // of the GPU idle one at a time.  The lanes fork from the caller's stream after the query's
+    // assignment and join it before the next query's assignment rewrites the labels.
+    LanePool *lp = nullptr;
+    const int nl = lane_pool(lp) ? std::min(kLanes, nt) : 1;
     for (int i = 0; i < nq; ++i) {
         st = stat ? assign_query_stat(q[i], splan, t, D, w, s) : assign_query(q[i], groups, t, D, p, w, s);
         if (st != VQNNF_OK) return st;
+        cudaError_t e = cudaSuccess;
+        if (nl > 1) {
+            e = cudaEventRecord(lp->fork, s);
+            for (int l = 1; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lp->st[l], lp->fork, 0);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
         for (int j = 0; j < nt; ++j) {
-            WsCursor sc{w.score_base, 0};
+            const int l = j % nl;
+            const cudaStream_t ls = l ? lp->st[l] : s;
+            WsCursor sc{w.score_base[l], 0};
             ScoreWs sw = carve_score(sc, q[i].H, q[i].W, t[j].k, t[j].h, t[j].w);
-            cudaError_t e = launch_sat(w.qlab[j], q[i].H, q[i].W, t[j].k, sw.u16, sw.carry, sw.bandsum, sw.S, s);
+            e = launch_sat(w.qlab[j], q[i].H, q[i].W, t[j].k, sw.u16, sw.carry, sw.bandsum, sw.S, ls);
             if (e != cudaSuccess) return from_cuda(e);
             const int HO = q[i].H - t[j].h + 1, WO = q[i].W - t[j].w + 1;
-            float *hp = heat ? heat[(size_t)i * nt + j] : w.heat_scratch;
+            float *hp = heat ? heat[(size_t)i * nt + j] : w.heat_scratch[l];
             e = launch_score(sw.S, sw.u16, q[i].W, t[j].k, HO, WO, banks.bs[j], banks.gs[j], no_wgrid, w.tcnt[j], hp,
-                             sw.amax, argmax_yx + 2 * ((size_t)i * nt + j), s);
+                             sw.amax, argmax_yx + 2 * ((size_t)i * nt + j), ls);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        for (int l = 1; l < nl; ++l) {
+            e = cudaEventRecord(lp->join[l], lp->st[l]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lp->join[l], 0);
             if (e != cudaSuccess) return from_cuda(e);
         }
     }
