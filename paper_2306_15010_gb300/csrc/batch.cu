@@ -22,7 +22,7 @@ using namespace vqnnf;
 namespace {
 
 constexpr int kGroupRows = kMaxK;            // rows of one group codebook, at most
-constexpr int kLanes = 4;                    // pairs of one query in flight at once (streams)
+constexpr int kLanes = 8;                    // pairs of one query in flight at once (streams)
 
 // The library's own streams and events for the pair lanes, created once per device on first
 // use (outside any stream capture in the intended use: the first call is a warm-up) and kept
