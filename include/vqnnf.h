@@ -307,7 +307,14 @@ vqnnf_status vqnnf_match_host(const float *X_host, int H, int W, int D, const fl
  *           [2 (i * nt + j)]
  *   ws      device workspace of vqnnf_batch_workspace_bytes(q, nq, t, nt, D, G) bytes,
  *           256-byte aligned
- * The call only enqueues work (graph-capturable).  Limits: nq * nt <= 65536, n = H W < 2^31
+ * The call only enqueues work (graph-capturable).  Inside it the template sides, and each
+ * query's pairs, run in eight lanes at once: `stream` and seven streams that the library
+ * creates on its first call on a device (with the events that fork and join them) and keeps
+ * for the process.  Every lane starts after the work enqueued on `stream` before the call,
+ * and `stream` waits for every lane before the call returns, so ordering on `stream` is as if
+ * all work ran on it.  Make the first call on a device outside stream capture (it creates the
+ * streams; if that fails every lane runs on `stream`); a device reset invalidates them.  The
+ * workspace holds an integral-image area per lane.  Limits: nq * nt <= 65536, n = H W < 2^31
  * (else VQNNF_EUNSUPPORTED). */
 typedef struct vqnnf_image {
     const float *X;
