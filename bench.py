@@ -173,6 +173,12 @@ class Pipeline:
         dev = X.device
         self.ws_fit = vq.Workspace(vq.vqnnf_workspace_bytes(0, th, tw, D, k, prec=prec), dev)
         self.ws_a = vq.Workspace(vq.vqnnf_workspace_bytes(1, H, W, D, k, prec=prec), dev)
+        self.ws_t = vq.Workspace(vq.vqnnf_workspace_bytes(1, th, tw, D, k, prec=prec), dev)
+        # the template's NNF and responses run on a second stream beside the query's NNF (both
+        # need only the codebook; the score needs both)
+        self.s2 = torch.cuda.Stream(device=dev)
+        self.ev_fit = torch.cuda.Event()
+        self.ev_tpl = torch.cuda.Event()
         self.ws_s = vq.Workspace(vq.vqnnf_workspace_bytes(3, H, W, 0, k, th, tw, self.bank.F), dev)
         self.C = torch.empty((k, D), device=dev)
         self.tl = torch.empty((th, tw), dtype=torch.uint8, device=dev)
@@ -183,16 +189,20 @@ class Pipeline:
         self.stats = torch.zeros(4, dtype=torch.int64, device=dev)
 
     def step(self, ev=None, kev=None):
-        """One pass of the hot path.  ev: 4 events marking the segment boundaries; kev: 4 events
-        recorded by the library immediately around the query's contraction kernel and the
-        score kernel (vqnnf_set_kernel_events)."""
+        """One pass of the hot path.  ev: 4 events marking the segment boundaries (the template
+        segment is the codebook fit; the template's NNF and responses overlap the query's NNF
+        on the second stream); kev: 4 events recorded by the library immediately around the
+        query's contraction kernel and the score kernel (vqnnf_set_kernel_events)."""
         vq, c, s = self.vq, self.cfg, self.s
         if ev is not None:
             ev[0].record(s)
         vq.vqnnf_fit_codebook(self.T, c["k"], c["iters"], c["fit_seed"], self.prec, C=self.C,
                               ws=self.ws_fit, stream=s)
-        vq.vqnnf_assign(self.T, self.C, self.prec, labels=self.tl, ws=self.ws_a, stream=s)
-        vq.vqnnf_filter_responses(self.tl, c["k"], self.bank, counts=self.tc, stream=s)
+        self.ev_fit.record(s)
+        self.s2.wait_event(self.ev_fit)
+        vq.vqnnf_assign(self.T, self.C, self.prec, labels=self.tl, ws=self.ws_t, stream=self.s2)
+        vq.vqnnf_filter_responses(self.tl, c["k"], self.bank, counts=self.tc, stream=self.s2)
+        self.ev_tpl.record(self.s2)
         if ev is not None:
             ev[1].record(s)
         if kev is not None:
@@ -203,6 +213,7 @@ class Pipeline:
             vq.vqnnf_set_kernel_events(OP_ASSIGN, None, None)
         if ev is not None:
             ev[2].record(s)
+        s.wait_event(self.ev_tpl)
         if kev is not None:
             vq.vqnnf_set_kernel_events(OP_SCORE, kev[2], kev[3])
         vq.vqnnf_score(self.ql, c["k"], c["th"], c["tw"], self.bank, self.tc, heatmap=self.heat,
