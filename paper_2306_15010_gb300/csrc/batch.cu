@@ -24,14 +24,13 @@ namespace {
 constexpr int kGroupRows = kMaxK;            // rows of one group codebook, at most
 constexpr int kLanes = 8;                    // pairs of one query in flight at once (streams)
 
-// The library's own streams and events for the pair lanes, created once per device on first
-// use (outside any stream capture in the intended use: the first call is a warm-up) and kept
-// for the process.  Lane 0 is the caller's stream.  If they cannot be created the pairs run
-// one after another on the caller's stream.
+// The library's own streams and events for the lanes, created once per device on first use
+// (outside any stream capture in the intended use: the first call is a warm-up) and kept for
+// the process.  If they cannot be created, everything runs on the caller's stream.
 struct LanePool {
     bool ok = false;
     cudaStream_t st[kLanes];
-    cudaEvent_t fork, join[kLanes];
+    cudaEvent_t fork, join[kLanes][2];
 };
 
 bool lane_pool(LanePool *&out)
@@ -46,9 +45,10 @@ bool lane_pool(LanePool *&out)
     if (!tried[dev]) {
         tried[dev] = true;
         bool ok = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) == cudaSuccess;
-        for (int l = 1; l < kLanes && ok; ++l)
+        for (int l = 0; l < kLanes && ok; ++l)
             ok = cudaStreamCreateWithFlags(&p.st[l], cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&p.join[l], cudaEventDisableTiming) == cudaSuccess;
+                 cudaEventCreateWithFlags(&p.join[l][0], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&p.join[l][1], cudaEventDisableTiming) == cudaSuccess;
         p.ok = ok;
         if (!ok) cudaGetLastError();                 // clear the failed creation's error
     }
@@ -89,7 +89,8 @@ struct BatchWs {
     std::vector<int32_t *> tcnt;              // per template: responses F x k
     std::vector<float *> gC;                  // per group slot: group codebook
     std::vector<CodebookPrep> gprep;          // per group slot: its prepared planes
-    std::vector<uint8_t *> qlab;              // per template: the current query's NNF
+    std::vector<uint8_t *> qlab;              // per template: the current query's NNF (one of qset)
+    std::vector<uint8_t *> qset[2];           // two sets, alternating between queries
     unsigned *flcount;                        // kMaxSegStat x 64 (counters and stats, one memset)
     FlagList fl[kMaxSegStat];
     float *sC;                                // stationary codebooks, every launch's groups in a row
@@ -138,7 +139,9 @@ BatchWs carve_batch(WsCursor &c, const vqnnf_image *q, int nq, const vqnnf_batch
         p.b = c.take<float>(kGroupRows);
         w.gprep.push_back(p);
     }
-    for (int j = 0; j < nt; ++j) w.qlab.push_back(c.take<uint8_t>((size_t)n_max));
+    for (int b = 0; b < 2; ++b)
+        for (int j = 0; j < nt; ++j) w.qset[b].push_back(c.take<uint8_t>((size_t)n_max));
+    w.qlab = w.qset[0];
     w.flcount = c.take<unsigned>((size_t)kMaxSegStat * 64);
     for (int s = 0; s < kMaxSegStat; ++s) {
         FlagList &f = w.fl[s];
@@ -431,8 +434,8 @@ vqnnf_status fit_templates(const vqnnf_batch_template *t, int nt, int D, int ite
         if (e != cudaSuccess) return from_cuda(e);
     }
     for (int l = 1; l < nl; ++l) {
-        e = cudaEventRecord(lp->join[l], lp->st[l]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lp->join[l], 0);
+        e = cudaEventRecord(lp->join[l][0], lp->st[l]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lp->join[l][0], 0);
         if (e != cudaSuccess) return from_cuda(e);
     }
     return VQNNF_OK;
@@ -545,24 +548,31 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
     }
     WGridSpec no_wgrid;
     memset(&no_wgrid, 0, sizeof(no_wgrid));
-    // per query, its pairs' integral images and scores run in kLanes lanes at once (pair j in
-    // lane j % kLanes, each lane with its own integral-image workspace): small pairs leave most
-    // of the GPU idle one at a time.  The lanes fork from the caller's stream after the query's
-    // assignment and join it before the next query's assignment rewrites the labels.
+    // Each query's pairs (integral image + score) run in kLanes lanes at once, pair j in lane
+    // j % kLanes with the lane's own integral-image workspace: small pairs leave most of the GPU
+    // idle one at a time.  The lanes are library streams; the caller's stream runs the query
+    // assignments.  The labels alternate between two sets, so query i + 1's assignment runs
+    // beside query i's pairs and only waits for query i - 1's pairs, the last readers of its
+    // set.  Everything joins the caller's stream before the call returns.
     LanePool *lp = nullptr;
-    const int nl = lane_pool(lp) ? std::min(kLanes, nt) : 1;
+    const int nl = lane_pool(lp) ? std::min(kLanes, nt) : 0;
+    cudaError_t e = cudaSuccess;
     for (int i = 0; i < nq; ++i) {
+        const int par = i & 1;
+        w.qlab = w.qset[par];
+        if (nl && i >= 2)
+            for (int l = 0; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(s, lp->join[l][par], 0);
+        if (e != cudaSuccess) return from_cuda(e);
         st = stat ? assign_query_stat(q[i], splan, t, D, w, s) : assign_query(q[i], groups, t, D, p, w, s);
         if (st != VQNNF_OK) return st;
-        cudaError_t e = cudaSuccess;
-        if (nl > 1) {
+        if (nl) {
             e = cudaEventRecord(lp->fork, s);
-            for (int l = 1; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lp->st[l], lp->fork, 0);
+            for (int l = 0; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(lp->st[l], lp->fork, 0);
             if (e != cudaSuccess) return from_cuda(e);
         }
         for (int j = 0; j < nt; ++j) {
-            const int l = j % nl;
-            const cudaStream_t ls = l ? lp->st[l] : s;
+            const int l = nl ? j % nl : 0;
+            const cudaStream_t ls = nl ? lp->st[l] : s;
             WsCursor sc{w.score_base[l], 0};
             ScoreWs sw = carve_score(sc, q[i].H, q[i].W, t[j].k, t[j].h, t[j].w);
             e = launch_sat(w.qlab[j], q[i].H, q[i].W, t[j].k, sw.u16, sw.carry, sw.bandsum, sw.S, ls);
@@ -573,13 +583,12 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
                              sw.amax, argmax_yx + 2 * ((size_t)i * nt + j), ls);
             if (e != cudaSuccess) return from_cuda(e);
         }
-        for (int l = 1; l < nl; ++l) {
-            e = cudaEventRecord(lp->join[l], lp->st[l]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, lp->join[l], 0);
-            if (e != cudaSuccess) return from_cuda(e);
-        }
+        for (int l = 0; l < nl && e == cudaSuccess; ++l) e = cudaEventRecord(lp->join[l][par], lp->st[l]);
+        if (e != cudaSuccess) return from_cuda(e);
     }
-    return VQNNF_OK;
+    // join: each lane's last record follows all of its work
+    for (int l = 0; l < nl && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(s, lp->join[l][(nq - 1) & 1], 0);
+    return from_cuda(e);
 }
 
 vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_template *t, int nt, int D,
