@@ -314,8 +314,9 @@ vqnnf_status vqnnf_match_host(const float *X_host, int H, int W, int D, const fl
  * and `stream` waits for every lane before the call returns, so ordering on `stream` is as if
  * all work ran on it.  Make the first call on a device outside stream capture (it creates the
  * streams; if that fails every lane runs on `stream`); a device reset invalidates them.  The
- * workspace holds an integral-image area per lane.  Limits: nq * nt <= 65536, n = H W < 2^31
- * (else VQNNF_EUNSUPPORTED). */
+ * workspace holds an integral-image area per lane and two sets of query labels, so that a
+ * query's assignment runs beside the previous query's pairs.  Limits: nq * nt <= 65536,
+ * n = H W < 2^31 (else VQNNF_EUNSUPPORTED). */
 typedef struct vqnnf_image {
     const float *X;
     int32_t H, W;
