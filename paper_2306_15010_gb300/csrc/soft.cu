@@ -45,8 +45,17 @@ __device__ __forceinline__ long long planar_index(long long it0, long long of0, 
     return (it * k + j) * npi + of;
 }
 
-// Distances of a 64-pixel tile to all k centroids and the softmax over each pixel's k logits.
-// Thread t = 16 pg + cl owns pixels 4 pg .. 4 pg + 3 and centroids cl, cl + 16, ...; the 16
+// Tile of the soft-assignment kernel: 16 pixel groups of PPT pixels.
+template <int KI>
+struct SoftTile {
+    static constexpr int PPT = KI <= 4 ? 8 : 4;
+    static constexpr int PT = 16 * PPT;
+};
+
+// Distances of a tile of 16 PPT pixels to all k centroids and the softmax over each pixel's k
+// logits.  Thread t = 16 pg + cl owns pixels PPT pg .. PPT pg + PPT - 1 and centroids cl,
+// cl + 16, ... (PPT = 8 pixels for k <= 64, else 4, so that the register tile stays within
+// budget; the larger tile halves the shared-memory loads per (pixel, centroid) pair); the 16
 // threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.  The
 // direct differences run on packed pairs of pixels (two FP32 lanes per instruction, each
 // rounded as the scalar subtraction and FMA would be): the centroid chunk is staged negated
@@ -57,15 +66,16 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
                                              const float *__restrict__ C, int k, float tau, float (*xs)[DCH + 1],
                                              float2 (*cs)[DCH + 1], float (*pr)[KI])
 {
+    constexpr int PPTK = SoftTile<KI>::PPT, PTK = SoftTile<KI>::PT;
     const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
-    float2 acc[PPT / 2][KI];
+    float2 acc[PPTK / 2][KI];
 #pragma unroll
-    for (int r = 0; r < PPT / 2; ++r)
+    for (int r = 0; r < PPTK / 2; ++r)
 #pragma unroll
         for (int i = 0; i < KI; ++i) acc[r][i] = make_float2(0.f, 0.f);
     // the next chunk's features and centroids are loaded into registers while the current one
     // is consumed (256 threads: XE and CE elements each)
-    constexpr int XE = PT * DCH / 256, CE = 16 * KI * DCH / 256;
+    constexpr int XE = PTK * DCH / 256, CE = 16 * KI * DCH / 256;
     float xr[XE], cr[CE];
     auto fetch = [&](int d0) {
 #pragma unroll
@@ -97,14 +107,14 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
         if (d0 + DCH < D) fetch(d0 + DCH);
 #pragma unroll 2
         for (int dd = 0; dd < DCH; ++dd) {
-            float2 xv[PPT / 2], cv[KI];
+            float2 xv[PPTK / 2], cv[KI];
 #pragma unroll
-            for (int r = 0; r < PPT / 2; ++r)
-                xv[r] = make_float2(xs[pg * PPT + 2 * r][dd], xs[pg * PPT + 2 * r + 1][dd]);
+            for (int r = 0; r < PPTK / 2; ++r)
+                xv[r] = make_float2(xs[pg * PPTK + 2 * r][dd], xs[pg * PPTK + 2 * r + 1][dd]);
 #pragma unroll
             for (int i = 0; i < KI; ++i) cv[i] = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int r = 0; r < PPT / 2; ++r)
+            for (int r = 0; r < PPTK / 2; ++r)
 #pragma unroll
                 for (int i = 0; i < KI; ++i) {
                     const float2 df = __fadd2_rn(xv[r], cv[i]);
@@ -114,7 +124,7 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
     }
     const float it = 1.0f / tau;
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) {
+    for (int r = 0; r < PPTK; ++r) {
         float dr[KI];
 #pragma unroll
         for (int i = 0; i < KI; ++i) dr[i] = (r & 1) ? acc[r >> 1][i].y : acc[r >> 1][i].x;
@@ -142,28 +152,29 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
 // p planar: P[(item * k + j) * npi + pixel], written through a shared-memory transpose so that
 // consecutive threads store consecutive pixels of one plane.
 template <int KI>
-__global__ void __launch_bounds__(256, KI == 8 ? 2 : 3) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
+__global__ void __launch_bounds__(256, KI == 2 ? 3 : 2) soft_p_kernel(const float *__restrict__ X, long long n, long long npi,
                                                      int D, const float *__restrict__ C, int k, float tau,
                                                      float *__restrict__ P)
 {
+    constexpr int PPTK = SoftTile<KI>::PPT, PTK = SoftTile<KI>::PT;
     extern __shared__ __align__(16) float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
-    float2 (*cs)[DCH + 1] = reinterpret_cast<float2 (*)[DCH + 1]>(sm + PT * (DCH + 1));
-    float *ps = sm + (PT + 32 * KI) * (DCH + 1);             // [k][PT + 1]
-    const long long p0 = (long long)blockIdx.x * PT;
-    float pr[PPT][KI];
+    float2 (*cs)[DCH + 1] = reinterpret_cast<float2 (*)[DCH + 1]>(sm + PTK * (DCH + 1));
+    float *ps = sm + (PTK + 32 * KI) * (DCH + 1);             // [k][PTK + 1]
+    const long long p0 = (long long)blockIdx.x * PTK;
+    float pr[PPTK][KI];
     tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
     const int pg = threadIdx.x >> 4, cl = threadIdx.x & 15;
 #pragma unroll
-    for (int r = 0; r < PPT; ++r)
+    for (int r = 0; r < PPTK; ++r)
 #pragma unroll
         for (int i = 0; i < KI; ++i)
-            if (cl + 16 * i < k) ps[(cl + 16 * i) * (PT + 1) + pg * PPT + r] = pr[r][i];
+            if (cl + 16 * i < k) ps[(cl + 16 * i) * (PTK + 1) + pg * PPTK + r] = pr[r][i];
     __syncthreads();
     const long long it0 = p0 / npi, of0 = p0 - it0 * npi;
-    for (int e = threadIdx.x; e < k * PT; e += blockDim.x) {
-        const int j = e / PT, pp = e % PT;
-        if (p0 + pp < n) P[planar_index(it0, of0, pp, j, k, npi)] = ps[j * (PT + 1) + pp];
+    for (int e = threadIdx.x; e < k * PTK; e += blockDim.x) {
+        const int j = e / PTK, pp = e % PTK;
+        if (p0 + pp < n) P[planar_index(it0, of0, pp, j, k, npi)] = ps[j * (PTK + 1) + pp];
     }
 }
 
@@ -715,10 +726,11 @@ template <int KI>
 cudaError_t launch_soft_p_ki(const float *X, long long n, long long npi, int D, const float *C, int k, float tau,
                              float *P, cudaStream_t s)
 {
-    const size_t sm = sizeof(float) * ((PT + 32 * KI) * (DCH + 1) + 16 * KI * (PT + 1));
+    constexpr int PTK = SoftTile<KI>::PT;
+    const size_t sm = sizeof(float) * ((PTK + 32 * KI) * (DCH + 1) + 16 * KI * (PTK + 1));
     cudaError_t e = cudaFuncSetAttribute(soft_p_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    soft_p_kernel<KI><<<(unsigned)((n + PT - 1) / PT), 256, sm, s>>>(X, n, npi, D, C, k, tau, P);
+    soft_p_kernel<KI><<<(unsigned)((n + PTK - 1) / PTK), 256, sm, s>>>(X, n, npi, D, C, k, tau, P);
     return cudaGetLastError();
 }
 
