@@ -58,13 +58,13 @@ struct SoftTile {
 // budget; the larger tile halves the shared-memory loads per (pixel, centroid) pair); the 16
 // threads of a pixel group are consecutive lanes (half a warp).  X rows are pixels.  The
 // direct differences run on packed pairs of pixels (two FP32 lanes per instruction, each
-// rounded as the scalar subtraction and FMA would be): the centroid chunk is staged negated
-// and duplicated, cs[j][dd] = (-c, -c), so one add and one FMA cover two (pixel, centroid)
-// pairs.
+// rounded as the scalar subtraction and FMA would be): the centroid chunk is staged negated,
+// cs[j][dd] = -c, and paired as (-c, -c) in registers, so one add and one FMA cover two
+// (pixel, centroid) pairs.
 template <int KI>
 __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long long n, long long p0, int D,
                                              const float *__restrict__ C, int k, float tau, float (*xs)[DCH + 1],
-                                             float2 (*cs)[DCH + 1], float (*pr)[KI])
+                                             float (*cs)[DCH + 1], float (*pr)[KI])
 {
     constexpr int PPTK = SoftTile<KI>::PPT, PTK = SoftTile<KI>::PT;
     const int t = threadIdx.x, pg = t >> 4, cl = t & 15;
@@ -101,7 +101,7 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
 #pragma unroll
         for (int q = 0; q < CE; ++q) {
             const int e = t + 256 * q;
-            cs[e / DCH][e % DCH] = make_float2(cr[q], cr[q]);
+            cs[e / DCH][e % DCH] = cr[q];
         }
         __syncthreads();
         if (d0 + DCH < D) fetch(d0 + DCH);
@@ -112,7 +112,10 @@ __device__ __forceinline__ void tile_softmax(const float *__restrict__ X, long l
             for (int r = 0; r < PPTK / 2; ++r)
                 xv[r] = make_float2(xs[pg * PPTK + 2 * r][dd], xs[pg * PPTK + 2 * r + 1][dd]);
 #pragma unroll
-            for (int i = 0; i < KI; ++i) cv[i] = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : make_float2(0.f, 0.f);
+            for (int i = 0; i < KI; ++i) {
+                const float c = (cl + 16 * i < k) ? cs[cl + 16 * i][dd] : 0.f;
+                cv[i] = make_float2(c, c);
+            }
 #pragma unroll
             for (int r = 0; r < PPTK / 2; ++r)
 #pragma unroll
@@ -159,8 +162,8 @@ __global__ void __launch_bounds__(256, KI == 2 ? 3 : 2) soft_p_kernel(const floa
     constexpr int PPTK = SoftTile<KI>::PPT, PTK = SoftTile<KI>::PT;
     extern __shared__ __align__(16) float sm[];
     float (*xs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm);
-    float2 (*cs)[DCH + 1] = reinterpret_cast<float2 (*)[DCH + 1]>(sm + PTK * (DCH + 1));
-    float *ps = sm + (PTK + 32 * KI) * (DCH + 1);             // [k][PTK + 1]
+    float (*cs)[DCH + 1] = reinterpret_cast<float (*)[DCH + 1]>(sm + PTK * (DCH + 1));
+    float *ps = sm + (PTK + 16 * KI) * (DCH + 1);             // [k][PTK + 1]
     const long long p0 = (long long)blockIdx.x * PTK;
     float pr[PPTK][KI];
     tile_softmax<KI>(X, n, p0, D, C, k, tau, xs, cs, pr);
@@ -727,7 +730,7 @@ cudaError_t launch_soft_p_ki(const float *X, long long n, long long npi, int D, 
                              float *P, cudaStream_t s)
 {
     constexpr int PTK = SoftTile<KI>::PT;
-    const size_t sm = sizeof(float) * ((PTK + 32 * KI) * (DCH + 1) + 16 * KI * (PTK + 1));
+    const size_t sm = sizeof(float) * ((PTK + 16 * KI) * (DCH + 1) + 16 * KI * (PTK + 1));
     cudaError_t e = cudaFuncSetAttribute(soft_p_kernel<KI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     soft_p_kernel<KI><<<(unsigned)((n + PTK - 1) / PTK), 256, sm, s>>>(X, n, npi, D, C, k, tau, P);
