@@ -29,9 +29,11 @@
  *            VQNNF_ETIMEOUT in a device error word that vqnnf_last_device_error() reads.
  *            No call aborts the process or traps on the device.
  * Threads.   Calls from several host threads on different streams are independent, with
- *            two exceptions, both process-wide: the profiling events of
- *            vqnnf_set_kernel_events (set under a lock), and the one device scratch area
- *            of vqnnf_assign_noalloc, which overlapping calls must not share.
+ *            three exceptions, all process-wide: the profiling events of
+ *            vqnnf_set_kernel_events (set under a lock), the one device scratch area of
+ *            vqnnf_assign_noalloc, which overlapping calls must not share, and the lanes of
+ *            the batch calls (library streams shared per device: concurrent batch calls
+ *            enqueue one at a time under a lock, and their work shares the lanes).
  * Ties.      Nearest-neighbour ties go to the lowest centroid index; the heatmap maximum
  *            goes to the lowest row-major (y, then x) window.
  */

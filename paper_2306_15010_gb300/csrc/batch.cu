@@ -33,6 +33,10 @@ struct LanePool {
     cudaEvent_t fork, join[kLanes][2];
 };
 
+// The lanes and their events are shared by every call on a device, so the batch calls of
+// several host threads take this lock while they enqueue (the work itself still overlaps).
+std::recursive_mutex g_lane_mu;
+
 bool lane_pool(LanePool *&out)
 {
     static std::mutex mu;
@@ -533,6 +537,7 @@ vqnnf_status vqnnf_match_batch(const vqnnf_image *q, int nq, const vqnnf_batch_t
     Banks banks;
     if ((st = compile_banks(t, nt, G, banks)) != VQNNF_OK) return st;
     cudaStream_t s = as_stream(stream);
+    std::lock_guard<std::recursive_mutex> lane_lock(g_lane_mu);
     WsCursor c{static_cast<char *>(ws), 0};
     BatchWs w = carve_batch(c, q, nq, t, nt, D, G);
     if ((st = fit_templates(t, nt, D, iters, seed, banks, w, s)) != VQNNF_OK) return st;
@@ -602,6 +607,7 @@ vqnnf_status vqnnf_batch_tune(const vqnnf_image *q, int nq, const vqnnf_batch_te
     Banks banks;
     if ((st = compile_banks(t, nt, G, banks)) != VQNNF_OK) return st;
     cudaStream_t s = as_stream(stream);
+    std::lock_guard<std::recursive_mutex> lane_lock(g_lane_mu);
     WsCursor c{static_cast<char *>(ws), 0};
     BatchWs w = carve_batch(c, q, nq, t, nt, D, G);
     if ((st = fit_templates(t, nt, D, iters, seed, banks, w, s)) != VQNNF_OK) return st;
