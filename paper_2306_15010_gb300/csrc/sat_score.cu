@@ -80,10 +80,20 @@ __global__ void __launch_bounds__(256) band_sum_kernel(const uint8_t *__restrict
     const int x0 = s * SW, y0 = b * BH, y1 = min(H, y0 + BH);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < SW * k; q += blockDim.x) cc[q] = 0;
-    // the band's carry sums, cluster-major (consecutive threads read consecutive clusters)
+    // the band's carry sums, cluster-major (consecutive threads read consecutive clusters),
+    // sixteen rows' loads in flight at a time (integer sums: any order is exact)
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        int cs = 0;
-        for (int y = y0; y < y1; ++y) cs += carry[((size_t)y * nS + s) * k + j];
+        const int *cp = carry + ((size_t)y0 * nS + s) * k + j;
+        const size_t rs = (size_t)nS * k;                // one row further
+        int cs = 0, y = y0;
+        for (; y + 16 <= y1; y += 16, cp += 16 * rs) {
+            int v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = cp[u * rs];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) cs += v[u];
+        }
+        for (; y < y1; ++y, cp += rs) cs += *cp;
         csum_s[j] = cs;
     }
     __syncthreads();
