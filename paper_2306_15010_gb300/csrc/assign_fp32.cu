@@ -20,6 +20,8 @@
 
 #include <cfloat>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -622,8 +624,11 @@ cudaError_t launch_rescore(const float *X, long long n, int D, const float *C, i
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one warp per flagged pixel at a time; at most n pixels can be flagged, so small calls
+    // (the Lloyd steps' template assignments) launch fewer blocks
+    const long long blocks = std::min<long long>((long long)sms * 8, std::max<long long>(sms, (n + 63) / 64));
     {
-        const cudaError_t le_ = launch_pdl(rescore_kernel, dim3(sms * 8), dim3(256), 0, s, X, D, C, k, labels, fl, (unsigned)n);
+        const cudaError_t le_ = launch_pdl(rescore_kernel, dim3((unsigned)blocks), dim3(256), 0, s, X, D, C, k, labels, fl, (unsigned)n);
         if (le_ != cudaSuccess) return le_;
     }
     return cudaGetLastError();

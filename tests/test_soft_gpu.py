@@ -76,6 +76,7 @@ def test_soft_forward_backward(vq, B, H, W, D, k, th, tw, G, tau):
 @pytest.mark.parametrize("B,H,W,D,k,th,tw,G,tau", [
     (2, 34, 36, 200, 20, 20, 18, 2, 0.2),    # two feature chunks, the second ragged (200 = 128 + 72)
     (1, 150, 140, 48, 40, 40, 44, 3, 0.1),   # 165 pixel tiles: more tiles than CTAs
+    (1, 30, 32, 300, 40, 18, 20, 1, 0.3),    # three feature chunks with 48 centroid columns (largest shared-memory use)
     (1, 30, 32, 384, 64, 18, 20, 1, 0.3),    # three 64-centroid chunks exceed shared memory: SIMT path
     (1, 30, 32, 40, 100, 20, 22, 1, 0.2),    # k > 64: SIMT path
     (1, 18, 3300, 8, 6, 10, 60, 2, 0.3),     # wide rows: four row blocks per row, 4 planes per gather block
