@@ -499,26 +499,42 @@ __global__ void __launch_bounds__(256, MC <= 4 ? 2 : 1) soft_gather_kernel(const
     }
 }
 
-// G[plane][uy][ux] (+)= sum over y' in [uy - h + 1, uy] within [0, H - h] of R2[plane][y'][ux];
-// thread: SEG consecutive uy, sliding window.
-__global__ void adj_col_kernel(const float *__restrict__ R2, int H, int W, int h, bool first, float *__restrict__ Gp)
+// G[plane][uy][ux] = sum over size classes s of the sum over y' in [uy - h_s + 1, uy] within
+// [0, H - h_s] of R2_s[plane][y'][ux] (the column pass of every class's adjoint box sum, so G is
+// written once); thread: SEG consecutive uy, one sliding window per class.
+struct AdjCols {
+    int ns;
+    int h[4];
+};
+__global__ void adj_col_kernel(const float *__restrict__ R2, long long cls_stride, int H, int W, AdjCols ac,
+                               float *__restrict__ Gp)
 {
     const int ux = blockIdx.x * blockDim.x + threadIdx.x, v0 = blockIdx.y * SEG;
     const long long plane = blockIdx.z;
     if (ux >= W || v0 >= H) return;
-    const float *src = R2 + plane * H * W + ux;
-    const int ym = H - h;
-    float s = 0.f;
-    for (int yp = max(0, v0 - h + 1); yp <= min(v0, ym); ++yp) s += src[(size_t)yp * W];
     const int ve = min(v0 + SEG, H);
-    for (int uy = v0; uy < ve; ++uy) {
-        if (uy > v0) {
-            if (uy <= ym) s += src[(size_t)uy * W];
-            if (uy - h >= 0 && uy - h <= ym) s -= src[(size_t)(uy - h) * W];
+    float out[SEG];
+#pragma unroll
+    for (int i = 0; i < SEG; ++i) out[i] = 0.f;
+    for (int is = 0; is < ac.ns; ++is) {
+        const float *src = R2 + is * cls_stride + plane * H * W + ux;
+        const int h = ac.h[is], ym = H - h;
+        float s = 0.f;
+        for (int yp = max(0, v0 - h + 1); yp <= min(v0, ym); ++yp) s += src[(size_t)yp * W];
+        out[0] += s;
+#pragma unroll
+        for (int i = 1; i < SEG; ++i) {
+            const int uy = v0 + i;
+            if (uy < ve) {
+                if (uy <= ym) s += src[(size_t)uy * W];
+                if (uy - h >= 0 && uy - h <= ym) s -= src[(size_t)(uy - h) * W];
+            }
+            out[i] += s;
         }
-        const size_t o = (plane * H + uy) * W + ux;
-        Gp[o] = first ? s : Gp[o] + s;
     }
+#pragma unroll
+    for (int i = 0; i < SEG; ++i)
+        if (v0 + i < ve) Gp[(plane * H + v0 + i) * W + ux] = out[i];
 }
 
 // Template pixel gradients: Gt[j][v] = sum over cells f containing v of dT_fj.
@@ -773,7 +789,8 @@ cudaError_t launch_gather_j(const SoftWs &w, const float *dheat, const float *wf
     cudaError_t e = cudaFuncSetAttribute(soft_gather_kernel<MC, J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zs);
     if (e != cudaSuccess) return e;
     const long long nblk = (long long)B * ((k + J - 1) / J) * ((H - h + GR) / GR);
-    soft_gather_kernel<MC, J><<<(unsigned)nblk, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is, w.R2,
+    soft_gather_kernel<MC, J><<<(unsigned)nblk, 256, zs, s>>>(w.BX, dheat, w.T, wf, H, W, k, HO, WO, sg, is,
+                                                              w.R2 + (size_t)is * B * k * H * W,
                                                               w.dT);
     return cudaGetLastError();
 }
@@ -845,7 +862,7 @@ SoftWs carve_soft(WsCursor &c, int B, int H, int W, int D, int k, int th, int tw
     w.Pt = c.take<float>((size_t)k * th * tw);
     w.T = c.take<float>((size_t)sg.F * k);
     w.L1 = c.take<float>((size_t)B * sg.F * (H - th + 1) * (W - tw + 1));
-    w.R2 = c.take<float>((size_t)B * k * plane);
+    w.R2 = c.take<float>((size_t)sg.ns * B * k * plane);    // one area per size class
     w.G = c.take<float>((size_t)B * k * plane);
     w.A = c.take<float>((size_t)B * k * plane);
     w.At = c.take<float>((size_t)k * th * tw);
@@ -901,6 +918,7 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
     e = cudaMemsetAsync(w.dT, 0, sizeof(float) * sg.F * k, s);
     if (e != cudaSuccess) return e;
     const long long planes = (long long)B * k;
+    AdjCols ac{sg.ns, {0, 0, 0, 0}};
     for (int is = 0; is < sg.ns; ++is) {
         const int h = sg.hgt[sg.size_h[is]];
         int ncell = 0;
@@ -909,9 +927,10 @@ cudaError_t soft_backward(const float *Qf, int B, int H, int W, const float *Tf,
             : ncell <= 9 ? launch_gather<9, 4>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s)
                          : launch_gather<kSoftMaxG * kSoftMaxG, 2>(w, dheat, wf, B, H, W, k, HO, WO, sg, is, s);
         if (e != cudaSuccess) return e;
-        dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
-        adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, H, W, h, is == 0, w.G);
+        ac.h[is] = h;
     }
+    dim3 g3((W + 127) / 128, (H + SEG - 1) / SEG, (unsigned)planes);
+    adj_col_kernel<<<g3, 128, 0, s>>>(w.R2, planes * H * W, H, W, ac, w.G);
     const size_t kDk = (size_t)k * D + k;
     if (soft_tc_supported(D, k)) {                            // tensor-core contractions
         int nqs = 0, nts = 0;

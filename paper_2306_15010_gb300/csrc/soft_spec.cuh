@@ -33,7 +33,7 @@ struct SoftWs {
     float *Pt;     // k x th x tw       template soft assignment, kept for the backward
     float *T;      // F x k             template soft counts
     float *L1;     // B x F x HO x WO   per-filter L1 distances
-    float *R2;     // B x k x H x W     gradient gather + adjoint row pass of one cell size
+    float *R2;     // ns x B x k x H x W gradient gather + adjoint row pass of each cell size
     float *G;      // B x k x H x W     dL/dp of the query pixels (planar)
     float *A;      // B x H x W x k     dL/dd of the query pixels (pixel-major)
     float *At;     // th x tw x k       dL/dd of the template pixels
