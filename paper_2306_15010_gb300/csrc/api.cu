@@ -52,9 +52,15 @@ FitWs carve_fit(WsCursor &c, long long l, int D, int k, int prec)
     FitWs w;
     w.as = carve_assign(c, l, D, k, prec);
     w.lab = c.take<uint8_t>((size_t)l);
-    w.cnt = c.take<int>((size_t)k);
-    w.off = c.take<int>((size_t)k + 1);
-    w.members = c.take<int>((size_t)l);
+    w.lw.cnt = c.take<int>((size_t)k);
+    w.lw.off = c.take<int>((size_t)k + 1);
+    w.lw.members = c.take<int>((size_t)l);
+    w.lw.ordered = c.take<int>((size_t)l);
+    const long long mc = lloyd_max_chunks(l, k);
+    w.lw.chunks = c.take<int4>((size_t)mc);
+    w.lw.bh = c.take<int>((size_t)kLloydSortBlocks * k);
+    w.lw.done = c.take<int>((size_t)k * ((D + 31) / 32));
+    w.lw.part = c.take<LloydPart>((size_t)mc * D);
     return w;
 }
 
@@ -144,9 +150,9 @@ namespace vqnnf {
 
 // Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).
 vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
-                        uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s)
+                        uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s, bool keep_mean)
 {
-    cudaError_t e = launch_prep_codebook(C, k, D, prec, w.prep, s, w.fl.count);
+    cudaError_t e = launch_prep_codebook(C, k, D, prec, w.prep, s, w.fl.count, keep_mean);
     if (e == cudaSuccess) {
         e = record_kernel_event(VQNNF_OP_ASSIGN, 0, s);
         if (e == cudaSuccess)
@@ -199,7 +205,9 @@ void kmeans_init_indices(long long l, int k, uint64_t seed, int32_t *out)
     }
 }
 
-// Seeded initial centroids, then `iters` Lloyd steps (assignment + exact centroid means).
+// Seeded initial centroids, then `iters` Lloyd steps (assignment + exact centroid means).  The
+// reference point of the assignment bound is the mean of the initial centroids, kept for every
+// step (the bound holds for any fixed point; the labels are exact either way).
 vqnnf_status run_fit(const float *T, long long l, int D, int k, int iters, uint64_t seed, int prec,
                      float *C, FitWs &fw, cudaStream_t s)
 {
@@ -209,9 +217,9 @@ vqnnf_status run_fit(const float *T, long long l, int D, int k, int iters, uint6
     cudaError_t e = launch_gather_init(T, D, k, ii, C, s);
     if (e != cudaSuccess) return from_cuda(e);
     for (int it = 0; it < iters; ++it) {
-        vqnnf_status st = run_assign(T, l, D, C, k, prec, fw.lab, nullptr, fw.as, s);
+        vqnnf_status st = run_assign(T, l, D, C, k, prec, fw.lab, nullptr, fw.as, s, it > 0);
         if (st != VQNNF_OK) return st;
-        e = launch_lloyd_update(T, (int)l, D, k, fw.lab, fw.cnt, fw.off, fw.members, C, s);
+        e = launch_lloyd_update(T, (int)l, D, k, fw.lab, fw.lw, C, s);
         if (e != cudaSuccess) return from_cuda(e);
     }
     return VQNNF_OK;

@@ -103,9 +103,10 @@ __device__ __forceinline__ float pow2_scale(float amax)
 // and upper bounds of the other norms (sums of squares inflated by their summation bound).
 // The block reduction has a fixed tree order (deterministic).
 __global__ void __launch_bounds__(256) prep_centroid_kernel(const float *__restrict__ C, int k,
-                                                            int D, int prec, CodebookPrep p)
+                                                            int D, int prec, CodebookPrep p, unsigned *zero64)
 {
     ptx::pdl_enter();
+    if (zero64 && blockIdx.x == 0 && threadIdx.x < 64) zero64[threadIdx.x] = 0u;   // see prep_mean_kernel
     const int j = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __shared__ float red[8][8];
@@ -470,7 +471,7 @@ __device__ __forceinline__ void df_warp_sum(float &hi, float &lo)
 
 constexpr int RS_MAXC = 16;        // 32-feature chunks of a pixel held in registers by the re-scoring
 
-__global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ X, int D,
+__global__ void __launch_bounds__(256, 2) rescore_kernel(const float *__restrict__ X, int D,
                                                       const float *__restrict__ C, int k,
                                                       uint8_t *__restrict__ labels, FlagList fl,
                                                       unsigned cap)
@@ -499,37 +500,70 @@ __global__ void __launch_bounds__(256) rescore_kernel(const float *__restrict__ 
             const int i = 32 * t + lane;
             xv[t] = inreg && i < D ? x[i] : 0.f;
         }
-        for (int w = 0; w < kMaskWords; ++w) {
-            unsigned bits = __shfl_sync(0xffffffffu, mw, w);
-            while (bits) {
-                const int j = w * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
+        auto keep = [&](float r, int j) {
+            ++nc;
+            if (r < r1) { r2 = r1; r1 = r; a = j; }
+            else if (r < r2) { r2 = r; }
+        };
+        if (inreg) {
+            // candidates in increasing index order, the next one's centroid loaded while the
+            // current one is summed
+            int cw = 0;
+            unsigned cb = __shfl_sync(0xffffffffu, mw, 0);
+            auto next = [&]() -> int {                       // uniform over the warp
+                while (cb == 0u) {
+                    if (++cw >= kMaskWords) return -1;
+                    cb = __shfl_sync(0xffffffffu, mw, cw);
+                }
+                const int j = cw * 32 + __ffs(cb) - 1;
+                cb &= cb - 1;
+                return j;
+            };
+            auto load_c = [&](int j, float (&cv)[RS_MAXC]) {
                 const float *c = C + (size_t)j * D;
+#pragma unroll
+                for (int t = 0; t < RS_MAXC; ++t) {
+                    const int i = 32 * t + lane;
+                    cv[t] = i < D ? c[i] : 0.f;
+                }
+            };
+            auto sum_c = [&](const float (&cv)[RS_MAXC], int j) {
                 float acc = 0.f;
-                if (inreg) {
-                    float cv[RS_MAXC];
 #pragma unroll
-                    for (int t = 0; t < RS_MAXC; ++t) {
-                        const int i = 32 * t + lane;
-                        cv[t] = i < D ? c[i] : 0.f;
-                    }
-#pragma unroll
-                    for (int t = 0; t < RS_MAXC; ++t) {
-                        const float d = xv[t] - cv[t];
-                        if (32 * t + lane < D) acc = fmaf(d, d, acc);
-                    }
-                } else {
+                for (int t = 0; t < RS_MAXC; ++t) {
+                    const float d = xv[t] - cv[t];
+                    if (32 * t + lane < D) acc = fmaf(d, d, acc);
+                }
+                keep(warp_sum(acc), j);
+            };
+            float ca[RS_MAXC], cb2[RS_MAXC];                 // two buffers, used in turn
+            int ja = next();
+            if (ja >= 0) load_c(ja, ca);
+            while (ja >= 0) {
+                const int jb = next();
+                if (jb >= 0) load_c(jb, cb2);
+                sum_c(ca, ja);
+                if (jb < 0) break;
+                ja = next();
+                if (ja >= 0) load_c(ja, ca);
+                sum_c(cb2, jb);
+            }
+        } else {
+            for (int w = 0; w < kMaskWords; ++w) {
+                unsigned bits = __shfl_sync(0xffffffffu, mw, w);
+                while (bits) {
+                    const int j = w * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const float *c = C + (size_t)j * D;
+                    float acc = 0.f;
                     for (int i0 = 0; i0 < D; i0 += 32) {
                         const bool ok = i0 + lane < D;
                         const int i = ok ? i0 + lane : D - 1;
                         const float d = x[i] - c[i];
                         acc = ok ? fmaf(d, d, acc) : acc;
                     }
+                    keep(warp_sum(acc), j);
                 }
-                const float r = warp_sum(acc);
-                ++nc;
-                if (r < r1) { r2 = r1; r1 = r; a = j; }
-                else if (r < r2) { r2 = r; }
             }
         }
         const bool decided = r2 * (1.0f - rho) > r1 * (1.0f + rho);
@@ -584,14 +618,15 @@ __global__ void finish_stats_kernel(FlagList fl, vqnnf_assign_stats *out)
 }  // namespace
 
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
-                                 cudaStream_t s, unsigned *zero64)
+                                 cudaStream_t s, unsigned *zero64, bool keep_mean)
 {
-    {
+    if (!keep_mean) {
         const cudaError_t le_ = launch_pdl(prep_mean_kernel, dim3((D + 31) / 32), dim3(256), 0, s, C, k, D, p.mean, zero64);
         if (le_ != cudaSuccess) return le_;
     }
     {
-        const cudaError_t le_ = launch_pdl(prep_centroid_kernel, dim3(k), dim3(256), 0, s, C, k, D, prec, p);
+        const cudaError_t le_ = launch_pdl(prep_centroid_kernel, dim3(k), dim3(256), 0, s, C, k, D, prec, p,
+                                           keep_mean ? zero64 : nullptr);
         if (le_ != cudaSuccess) return le_;
     }
     return cudaGetLastError();

@@ -54,8 +54,10 @@ struct TcSeg {
 
 // Host-side launchers (defined in the .cu files).
 // zero64: if not null, 64 words zeroed by the first kernel (a flag list's counter and statistics).
+// keep_mean: the reference point p.mean is left as it is (set by an earlier call on the same
+// workspace) instead of recomputed as the codebook mean; any fixed m keeps the bound valid.
 cudaError_t launch_prep_codebook(const float *C, int k, int D, int prec, CodebookPrep p,
-                                 cudaStream_t s, unsigned *zero64 = nullptr);
+                                 cudaStream_t s, unsigned *zero64 = nullptr, bool keep_mean = false);
 cudaError_t launch_assign_fp32(const float *X, long long n, int D, int k,
                                const CodebookPrep &p, uint8_t *labels, FlagList fl,
                                cudaStream_t s);
@@ -118,8 +120,26 @@ struct InitIdx {
 };
 cudaError_t launch_gather_init(const float *T, int D, int k, const InitIdx &ii, float *C,
                                cudaStream_t s);
-cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8_t *lab, int *cnt,
-                                int *off, int *members, float *C, cudaStream_t s);
+// Lloyd update workspace (fit.cu).  The members of each cluster are cut into
+// chunks of kLloydRows rows; a cluster of more than one chunk combines its chunks' exact partial
+// sums (one LloydPart per chunk and dimension) in the block that finishes last.
+constexpr int kLloydRows = 128;
+constexpr int kLloydSortBlocks = 32;  // most blocks of the counting sort
+struct __align__(16) LloydPart {
+    unsigned __int128 pos, neg, mag;   // sums of the positive parts, negative parts; a bound of sum |x|
+    int low, hish, bad, pad;           // lowest set bit, largest shift, a value outside the range
+};
+struct LloydWs {
+    int *cnt, *off, *members;          // cluster sizes, first slots, member pixels (any order)
+    int *ordered;                      // member pixels in pixel order (the in-order FP64 route only)
+    int4 *chunks;                      // (first member slot, rows | cluster << 8, first chunk, size)
+    int *bh;                           // per sort block and cluster: label counts
+    int *done;                         // per (cluster, 32 dimensions): chunks finished
+    LloydPart *part;                   // per (chunk, dimension) partial sums
+};
+inline long long lloyd_max_chunks(long long l, int k) { return (l + kLloydRows - 1) / kLloydRows + k; }
+cudaError_t launch_lloyd_update(const float *T, int l, int D, int k, const uint8_t *lab, const LloydWs &lw,
+                                float *C, cudaStream_t s);
 
 }  // namespace vqnnf
 

@@ -17,7 +17,7 @@ struct AssignWs {
 struct FitWs {
     AssignWs as;
     uint8_t *lab;
-    int *cnt, *off, *members;
+    LloydWs lw;
 };
 
 struct ScoreWs {
@@ -39,8 +39,10 @@ FitWs carve_fit(WsCursor &c, long long l, int D, int k, int prec = VQNNF_PREC_FP
 ScoreWs carve_score(WsCursor &c, int H, int W, int k, int th, int tw);
 
 // Enqueue the full assignment of n pixels (prep, contraction, re-scoring, stats).
+// keep_mean: reuse the reference point of the previous call on w (the Lloyd steps after the first).
 vqnnf_status run_assign(const float *X, long long n, int D, const float *C, int k, int prec,
-                        uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s);
+                        uint8_t *labels, vqnnf_assign_stats *stats, AssignWs &w, cudaStream_t s,
+                        bool keep_mean = false);
 // Seeded initial centroids, then `iters` Lloyd steps.
 vqnnf_status run_fit(const float *T, long long l, int D, int k, int iters, uint64_t seed, int prec,
                      float *C, FitWs &fw, cudaStream_t s);

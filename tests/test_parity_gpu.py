@@ -167,8 +167,8 @@ def test_fit_codebook_exact_sum_edge_values(vq, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_fit_codebook_large_clusters_exact(vq, prec):
-    """Clusters of more than a thousand members (the block-wide staged route of the in-order
-    FP64 sums) with values that force that route: bit-identical to the oracle."""
+    """Clusters of more than a thousand members (many chunks, and the block-wide staged route
+    of the in-order FP64 sums) with values that force that route: bit-identical to the oracle."""
     r = np.random.default_rng(11)
     l, D, k = 3600, 32, 2
     T = np.abs(r.normal(0.5, 0.3, (l, D))).astype(np.float32)
@@ -178,6 +178,22 @@ def test_fit_codebook_large_clusters_exact(vq, prec):
     T = T.reshape(60, 60, D)
     C = vq.vqnnf_fit_codebook(_dev(T), k, 3, 21, prec)
     C_ref = oracle.fit_codebook(T, k, 3, 21)
+    assert np.array_equal(C.cpu().numpy().view(np.uint32), C_ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fit_codebook_mixed_routes_across_chunks(vq, prec):
+    """Clusters of many 128-member chunks where a few chunks hold values of 32 or more (outside
+    the 64-bit fixed-point range, inside the 128-bit one) and the rest do not: the chunks'
+    partial sums come from both routes and are combined; bit-identical to the oracle."""
+    r = np.random.default_rng(17)
+    l, D, k = 2000, 48, 3
+    T = np.abs(r.normal(0.5, 0.3, (l, D))).astype(np.float32)
+    big = r.random((l, D)) < 0.0002
+    T[big] = r.uniform(32.0, 64.0, big.sum()).astype(np.float32)
+    T = T.reshape(40, 50, D)
+    C = vq.vqnnf_fit_codebook(_dev(T), k, 3, 5, prec)
+    C_ref = oracle.fit_codebook(T, k, 3, 5)
     assert np.array_equal(C.cpu().numpy().view(np.uint32), C_ref.view(np.uint32))
 
 
