@@ -59,6 +59,7 @@ FitWs carve_fit(WsCursor &c, long long l, int D, int k, int prec)
     const long long mc = lloyd_max_chunks(l, k);
     w.lw.chunks = c.take<int4>((size_t)mc);
     w.lw.bh = c.take<int>((size_t)kLloydSortBlocks * k);
+    w.lw.rcp = c.take<double>((size_t)k);
     w.lw.done = c.take<int>((size_t)k * ((D + 31) / 32));
     w.lw.part = c.take<LloydPart>((size_t)mc * D);
     return w;

@@ -134,6 +134,7 @@ struct LloydWs {
     int *ordered;                      // member pixels in pixel order (the in-order FP64 route only)
     int4 *chunks;                      // (first member slot, rows | cluster << 8, first chunk, size)
     int *bh;                           // per sort block and cluster: label counts
+    double *rcp;                       // per cluster: 1 / size, correctly rounded
     int *done;                         // per (cluster, 32 dimensions): chunks finished
     LloydPart *part;                   // per (chunk, dimension) partial sums
 };

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const uint8_
         if (t < k) {
             lw.cnt[t] = c;
             lw.off[t] = first;
+            lw.rcp[t] = c > 0 ? 1.0 / (double)c : 0.0;
             // chunk entries (first slot, rows | cluster << 8, cluster's first chunk, cluster size)
             for (int r = 0; r < nch; ++r)
                 lw.chunks[f + r] = make_int4(first + r * kLloydRows, min(kLloydRows, c - r * kLloydRows) | t << 8, f, c);
@@ -259,7 +260,19 @@ __device__ __forceinline__ int top_bit(unsigned __int128 v)
 
 constexpr int FCH = 44;      // member rows per staged chunk of the in-order FP64 route
 
-__global__ void __launch_bounds__(32 * UW, 4) update_kernel(const float *__restrict__ T, int l, int D,
+// RN(a / b) for finite a and b > 0 from y = RN(1 / b) (Markstein's theorem: if q is within one
+// ulp of a / b, r = a - b q is exact and RN(q + r y) is the correctly rounded quotient).  The
+// first correction brings q0 = RN(a y), within 1.5 ulp, to within one ulp.
+__device__ __forceinline__ double div_rn(double a, double b, double y)
+{
+    double q = a * y;
+    double r = fma(-q, b, a);
+    q = fma(r, y, q);
+    r = fma(-q, b, a);
+    return fma(r, y, q);
+}
+
+__global__ void __launch_bounds__(32 * UW, 5) update_kernel(const float *__restrict__ T, int l, int D,
                                                          const uint8_t *__restrict__ lab, LloydWs lw,
                                                          float *__restrict__ C)
 {
@@ -429,7 +442,8 @@ __global__ void __launch_bounds__(32 * UW, 4) update_kernel(const float *__restr
         const bool negative = neg > pos;
         const unsigned __int128 d = negative ? neg - pos : pos - neg;
         const double v = (double)(uint64_t)(d >> low);
-        s = ldexp(negative ? -v : v, low - 80);
+        // times 2^(low - 80), a normal power of two (low - 80 lies in [-80, 45])
+        s = (negative ? -v : v) * __longlong_as_double((long long)(low - 80 + 1023) << 52);
     }
     if (nm) {
         // the in-order FP64 sum of the flagged columns over all c members: the members are
@@ -457,7 +471,7 @@ __global__ void __launch_bounds__(32 * UW, 4) update_kernel(const float *__restr
         }
         if (mine) s = acc;
     }
-    if (w == 0 && i < D) C[(size_t)j * D + i] = (float)(s / (double)c);
+    if (w == 0 && i < D) C[(size_t)j * D + i] = (float)(isfinite(s) ? div_rn(s, (double)c, __ldg(lw.rcp + j)) : s / (double)c);
 }
 
 }  // namespace
