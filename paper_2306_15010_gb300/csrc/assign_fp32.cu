@@ -484,22 +484,34 @@ __global__ void __launch_bounds__(256, 2) rescore_kernel(const float *__restrict
     const float u = (float)kU32;
     const float rho = ((float)((D + 31) / 32) + 8.0f) * u * 1.01f + 4.0f * u;
     unsigned long long my_cand = 0, my_deep = 0;
-    for (unsigned e = wid; e < n_entries; e += nw) {
-        const unsigned pix = fl.pix[e];
-        const unsigned mw0 = fl.mask[(size_t)e * kMaskWords + (lane & (kMaskWords - 1))];
-        const unsigned mw = lane < kMaskWords ? mw0 : 0u;
-        const float *x = X + (size_t)pix * D;
-        float r1 = FLT_MAX, r2 = FLT_MAX;
-        int a = 0, nc = 0;
-        // D <= 32 RS_MAXC: the pixel's features stay in registers and every candidate's loads
-        // are issued together (the same per-lane order of additions as the general loop)
-        const bool inreg = D <= 32 * RS_MAXC;
-        float xv[RS_MAXC];
+    // D <= 32 RS_MAXC: a pixel's features stay in registers and every candidate's loads are
+    // issued together (the same per-lane order of additions as the general loop).  The warp's
+    // next entry (pixel, candidate mask word, features) is loaded while this one is scored.
+    const bool inreg = D <= 32 * RS_MAXC;
+    unsigned pix_n = 0u, mw_n = 0u;
+    float xn[RS_MAXC];
+    auto fetch = [&](unsigned e2) {
+        pix_n = fl.pix[e2];
+        const unsigned m0 = fl.mask[(size_t)e2 * kMaskWords + (lane & (kMaskWords - 1))];
+        mw_n = lane < kMaskWords ? m0 : 0u;
+        const float *x2 = X + (size_t)pix_n * D;
 #pragma unroll
         for (int t = 0; t < RS_MAXC; ++t) {
             const int i = 32 * t + lane;
-            xv[t] = inreg && i < D ? x[i] : 0.f;
+            xn[t] = inreg && i < D ? x2[i] : 0.f;
         }
+    };
+    if (wid < n_entries) fetch(wid);
+    for (unsigned e = wid; e < n_entries; e += nw) {
+        const unsigned pix = pix_n;
+        const unsigned mw = mw_n;
+        const float *x = X + (size_t)pix * D;
+        float r1 = FLT_MAX, r2 = FLT_MAX;
+        int a = 0, nc = 0;
+        float xv[RS_MAXC];
+#pragma unroll
+        for (int t = 0; t < RS_MAXC; ++t) xv[t] = xn[t];
+        if (e + nw < n_entries) fetch(e + nw);
         auto keep = [&](float r, int j) {
             ++nc;
             if (r < r1) { r2 = r1; r1 = r; a = j; }
