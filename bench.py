@@ -228,7 +228,9 @@ def kernels_per_step(cfg, prec):
     """Kernels of this library launched by one step (counted from the launch sequence)."""
     k = cfg["k"]
     assign = 2 + 1 + 1 + 1          # prep mean + prep centroids, contraction, rescore, stats
-    fit = 1 + cfg["iters"] * (assign - 1 + 2)   # gather; per step: assign (no stats) + sort + update
+    # gather; per Lloyd step: prep centroids, contraction, rescore, two sort kernels, update; the
+    # first step also forms the reference point (prep mean), which the later steps keep
+    fit = 1 + cfg["iters"] * (3 + 3) + (1 if cfg["iters"] > 0 else 0)
     tpl = (assign - 1) + 1          # template NNF, template responses
     score = 4 + 1 + 1               # row carries, band sums, band prefix, write pass; score; argmax
     return fit + tpl + assign + score
