@@ -73,10 +73,11 @@ def test_cpu_baseline_fields_on_a_small_workload():
 
 def test_launch_count_claim_matches_the_launch_sequence():
     """gpu_launches counts the library's kernels per step.  The headline launch list
-    (profiles/launches_bench_headline_2048.md) shows 77 per BF16 step:
-    - 12 each of prep mean, prep centroids, contraction and re-scoring;
-    - 10 each of stable sort and update;
+    (profiles/launches_bench_headline_2048.md) shows 78 per BF16 step:
+    - 12 each of prep centroids, contraction and re-scoring;
+    - 3 of prep mean (the fit's first Lloyd step, the template and the query assignment);
+    - 10 each of the two sort kernels and the update;
     - one each of gather, template responses, stats, row carries, band sums, band prefix,
       write pass, score and argmax."""
     import bench
-    assert bench.kernels_per_step(bench.HEADLINE, "bf16") == 12 * 4 + 10 * 2 + 9
+    assert bench.kernels_per_step(bench.HEADLINE, "bf16") == 12 * 3 + 3 + 10 * 3 + 9
