@@ -183,11 +183,11 @@ __device__ void ordered_members(const uint8_t *__restrict__ lab, int l, int j, i
 // holds a value outside the range, or whose sums could exceed 128 bits is summed in FP64 in
 // pixel order.  Both branches therefore equal the in-order FP64 sum bit for bit.
 //
-// The common case takes a narrower route first: values with 2^-17 <= |x| < 2^5 (and zero) are
-// integers below 2^45 in units of 2^-40, so the sums of the positive and of the negative
-// values' magnitudes over a chunk's rows are exact in 64 bits, at a fraction of the 128-bit
-// route's instructions (the sum of |x| is their sum, the signed sum their difference).  A
-// block with any value outside that range repeats its rows in 128 bits.
+// The common case takes a narrower route first (Split32 below): values with 2^-17 <= |x| < 2^5
+// (and zero) are multiples of 2^-40, summed exactly on the FP32 pipe at a fraction of the
+// 128-bit route's instructions.  Its exactness test uses bounds: rows x max |x| for sum |x|,
+// and the last mantissa bit of the smallest nonzero |x| for the lowest set bit.  A block with
+// any value outside that range repeats its rows in 128 bits.
 //
 // Work split: one block per (chunk of at most kLloydRows member rows, 32 dimensions), so a
 // large cluster is spread over many blocks.  A one-chunk cluster finishes in its block; the
