@@ -896,7 +896,7 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(1, args.steps), 1),
             "ms_per_step_basis": "wall time of the sampled step that ran (not the whole workload)",
             "full_step_ms_estimate": round(1e3 * full_s, 1),
-            "higher_is_better": True, "scaling": "weak" if band is None else "strong", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "2048x2048 query, D=512, k=128, 128x128 template, F=10 "
                                    "(full + 3x3), 10 Lloyd steps; whole hot path per step",

@@ -81,3 +81,31 @@ def test_launch_count_claim_matches_the_launch_sequence():
       write pass, score and argmax."""
     import bench
     assert bench.kernels_per_step(bench.HEADLINE, "bf16") == 12 * 3 + 3 + 10 * 3 + 9
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch):
+    """The reference arm's JSON line on rank 0 (the oracle's bounded sample stubbed out so the
+    test is quick): the base contract's keys, impl = reference, and its own e2e and
+    cpu_baseline objects."""
+    import json
+    import bench
+
+    def fake_workload(dev, cfg):
+        return None, None, {"top_left": (0, 0)}, None
+
+    def fake_baseline(q, T, cfg, bank, **kw):
+        return {"value": 0.25, "unit": "Mpix/s", "cores": 4, "kind": "oracle", "sample": "stub",
+                "step_s_estimate": 16.0, "phases_s": {}}
+
+    monkeypatch.setattr(bench, "make_workload", fake_workload)
+    monkeypatch.setattr(bench, "cpu_baseline", fake_baseline)
+    args = type("A", (), {"steps": 2, "warmup": 1})()
+    line = bench.run_reference(args, 0, 1)
+    json.dumps(line)                                      # one JSON line
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in line
+    assert line["impl"] == "reference" and line["value"] == 0.25 and line["steps"] == 2
+    assert line["e2e"]["value"] == 0.25 and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == 0.25
+
